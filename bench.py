@@ -1,0 +1,298 @@
+"""Benchmark of the reduced-space IPM hot path on one GB300.
+
+Metric: scenario condensations per second (one scenario condensed and reduced
+at one interior-point iteration = one condensation) and seconds per IPM
+iteration, on the 1000-bus / 64-scenario two-stage OPF workload (FP64 path).
+A step is one full IPM iteration (evaluation, condensation, reduction,
+Cholesky with inertia correction, step recovery, line search) over all
+scenarios; the states cycle through complete solves from the cold start
+(re-initialised, untimed, whenever a solve converges).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
+numpy/scipy implementation in oracle/) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2301_04869_gb300 import synth  # noqa: E402
+
+METRIC = "scenario condensations/s & s per IPM iter (mixed vs FP64 path, 1e-8 KKT res)"
+UNIT = "scenario condensations/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r.split(",") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        smax = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+
+
+def roofline(phases, dims, peaks, peak_kind):
+    """Roofline entry for the dominant kernel phase (device time share)."""
+    name = max(phases, key=lambda k: phases[k][0])
+    ms, calls = phases[name]
+    N, nx, nu = dims.n_scen, dims.n_x, dims.n_u
+    per_call_s = ms / 1e3 / max(calls, 1)
+    fp64_peak = peaks.get("fp64_tflops", 1.25)
+    if name == "gemm":
+        # algorithmic flops: the upper triangle of sum_i Z_i^T Y_i (symmetric K_hat)
+        flops = 2.0 * nx * (nu * (nu + 1) / 2.0) * N
+        ach = flops / per_call_s / 1e12
+        return {"kernel": "k_gemm_tn64 (FP64 Z^T Y + scenario sum)", "bound": "alu", "achieved": ach,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "algorithmic": f"{flops:.4g} flop/launch"}
+    if name == "zsolve":
+        flops = 2.0 * dims.nnz_lu * nu * N
+        ach = flops / per_call_s / 1e12
+        return {"kernel": "k_zsolve64 (FP64 multi-RHS solves + SpMM)", "bound": "alu", "achieved": ach,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "algorithmic": f"{flops:.4g} flop/launch"}
+    if name == "lu":
+        return {"kernel": "k_lu_factor", "bound": "alu", "achieved": None, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": None, "traffic": None}
+    # bandwidth-type phases: bytes of Z and Y touched
+    byt = 8.0 * nx * nu * N * 2
+    ach = byt / per_call_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None}
+
+
+def cpu_baseline(workload, n_sample=8, iters=2):
+    """The oracle, as it stands, on a bounded sample: `iters` IPM iterations
+    from the cold start on the first `n_sample` scenarios of the workload."""
+    from oracle import ipm as oipm
+    from oracle import opf
+    net, pd, qd = synth.workload(workload, n_scen=n_sample)
+    M = opf.Model(net, pd, qd)
+    st = oipm.initial_state(M)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        oipm.iterate(M, st)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample * iters / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{iters} IPM iterations from the cold start on {n_sample} of the workload's scenarios "
+                      f"({dt:.1f} s, numpy/scipy FP64, BLAS threads = all cores)",
+            "s_per_ipm_iter": dt / iters}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import ipm as oipm
+    from oracle import opf
+    n_sample = 8
+    net, pd, qd = synth.workload(args.workload, n_scen=n_sample)
+    M = opf.Model(net, pd, qd)
+    st = oipm.initial_state(M)
+    for _ in range(args.warmup):
+        conv, _ = oipm.iterate(M, st)
+        if conv:
+            st = oipm.initial_state(M)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        conv, _ = oipm.iterate(M, st)
+        times.append(time.perf_counter() - t0)
+        if conv:
+            st = oipm.initial_state(M)
+    tot = sum(times)
+    val = n_sample * args.steps / tot
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "scenarios_timed": n_sample, "path": "oracle FP64 (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step = one IPM iteration on {n_sample} scenarios"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    from paper_2301_04869_gb300 import ipm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    net, pd, qd = synth.workload(args.workload)
+    prec = ipm.PREC_MIXED if args.precision == "mixed" else ipm.PREC_FP64
+    sol = ipm.Solver(net, pd, qd, precision=prec)
+    dims = sol.dims
+    N = dims.n_scen
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        conv, err = sol.ipm_step()
+        if conv:
+            sol.ipm_init_state()
+            conv, err = sol.ipm_step()
+        return conv
+
+    for _ in range(args.warmup):
+        one_step()
+    sol.ipm_set_profiling(2)
+    _, launches0 = sol.timers()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # larger than L2: evicts the previous step's data
+            ev[k][0].record(stream)
+            conv, _ = sol.ipm_step()
+            ev[k][1].record(stream)
+            if conv:  # a converged check takes no step: restart (untimed) and redo
+                sol.ipm_init_state()
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                sol.ipm_step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    phases, launches1 = sol.timers()
+    sol.ipm_set_profiling(0)
+    value = world * N * args.steps / (tot_ms / 1e3)
+    cond_ms = sum(phases[p][0] for p in ("condense_K", "lu", "zsolve", "gemm", "reduced_rhs"))
+    cond_calls = max(phases["lu"][1], 1)
+
+    # end to end through the C ABI with host buffers: state in from pinned host
+    # memory, one IPM iteration, state out to host memory, every step
+    host = torch.empty(dims.state_len, dtype=torch.float64, pin_memory=True)
+    hnp = host.numpy()
+    sol.ipm_get_state(hnp)
+    e2e = []
+    for k in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol.ipm_set_state(hnp)
+        conv, _ = sol.ipm_step()
+        sol.ipm_get_state(hnp)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+        if conv:
+            sol.ipm_init_state()
+            sol.ipm_get_state(hnp)
+    e2e_val = world * N * len(e2e) / sum(e2e)
+
+    if rank != 0:
+        return
+    peaks, pk = load_peaks()
+    if "fp64_tflops" not in peaks:
+        peaks["fp64_tflops"] = 1.25
+    rl = roofline(phases, dims, peaks, pk)
+    rl["peak_source"] = ("derived FP64 rate (see DESIGN)" if rl["bound"] == "alu" else f"{pk} MEASURED_PEAKS.json")
+    cb = cpu_baseline(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == ipm.PREC_FP64 else "bf16x3+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_bus": dims.n_bus, "n_scen": N, "n_x": dims.n_x, "n_u": dims.n_u,
+                   "path": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "s_per_ipm_iter": tot_ms / args.steps / 1e3,
+        "condense_only": {"value": N * cond_calls / (cond_ms / 1e3) if cond_ms > 0 else None, "unit": UNIT,
+                          "phases": ["condense_K", "lu", "zsolve", "gemm", "reduced_rhs"]},
+        "phases_ms_per_step": {p: phases[p][0] / args.steps for p in phases},
+        "roofline": rl,
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * dims.state_len,
+                "d2h_bytes_per_step": 8 * dims.state_len},
+        "gpu_launches": launches1 - launches0,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="opf1000_n64", choices=list(synth.CONFIGS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

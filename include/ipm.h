@@ -1,0 +1,174 @@
+/*
+ * ipm.h -- C ABI of the GB300 reduced-space interior-point hot path.
+ *
+ * The library solves the two-stage block nonlinear program of §2 (eqs. (2)-(3))
+ * for stochastic AC optimal power flow (§4.1.1): N scenarios share the
+ * controls u (generator voltages and non-slack active powers) and own their
+ * states x_i (angles, load-bus voltages).  At every interior-point iteration
+ * it evaluates each scenario's Jacobians and Lagrangian Hessian, condenses the
+ * inequalities into a barrier diagonal (Prop. 2.1/2.2), eliminates the states
+ * through a batched sparse LU of G_x and the multi-RHS solves
+ * Z = -G_x^{-1} G_u (Prop. 2.3), accumulates the dense reduced Hessian
+ * Z^T K Z over scenarios (the Schur complement of Prop. 2.4) and factors it
+ * by dense Cholesky.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an ipm_status; nothing aborts or traps.  On error,
+ *    ipm_last_error() describes the failure.
+ *  - "stream" is a cudaStream_t passed as void* (0 = legacy default stream).
+ *    Work is enqueued on it; calls that must read a device scalar (a
+ *    positive-definiteness flag, a KKT error, a line-search merit value)
+ *    synchronise that stream before returning.
+ *  - Host arrays passed to ipm_create are copied; the caller keeps ownership.
+ *  - Device pointers passed in are caller-owned, must hold the stated number
+ *    of doubles, and are accessed through "stream".
+ *  - A context is not thread-safe; use one stream per context at a time.
+ */
+#ifndef IPM_H
+#define IPM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipm_ctx ipm_ctx;
+
+typedef enum {
+  IPM_OK = 0,
+  IPM_ERR_ARG = 1,          /* invalid argument (sizes, NaN/negative loads, bad indices) */
+  IPM_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  IPM_ERR_OOM = 3,          /* device allocation failed */
+  IPM_ERR_SINGULAR_GX = 4,  /* a static LU pivot of G_x is (numerically) zero */
+  IPM_ERR_NOT_PD = 5,       /* inertia correction exceeded its largest delta_w */
+  IPM_ERR_LINESEARCH = 6,   /* backtracking fell below the minimum step */
+  IPM_ERR_MAXITER = 7,      /* iteration limit reached */
+  IPM_ERR_TIMEOUT = 8,      /* a bounded device wait gave up */
+  IPM_ERR_STATE = 9         /* call out of order (e.g. solve before factor) */
+} ipm_status;
+
+/* One network (per-unit).  Lines use the pi model without taps or shunts
+ * (Y_ff = Y_tt = y + j b/2, Y_ft = Y_tf = -y, y = 1/(r + j x)).
+ * gen_bus[0] must be 0: generator 0 is the slack (its Pg is the dependent
+ * function P_0 + Pd_0).  Pg bounds are [0, pmax]; Qg bounds [-qmax, qmax];
+ * V bounds [vmin, vmax] at every bus. */
+typedef struct {
+  int n_bus, n_line, n_gen;
+  const int *from, *to;        /* [n_line] */
+  const int *gen_bus;          /* [n_gen] distinct buses, gen_bus[0] == 0 */
+  const double *r, *x, *b;     /* [n_line] */
+  const double *pmax, *qmax;   /* [n_gen] */
+  const double *c2, *c1;       /* [n_gen] cost c2 Pg^2 + c1 Pg */
+  const double *vmin, *vmax;   /* [n_bus] */
+} ipm_network;
+
+enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1 };
+
+typedef struct {
+  double tol;            /* KKT residual E_0 target (1e-8) */
+  int max_iter;          /* 200 */
+  int precision;         /* IPM_PREC_FP64 or IPM_PREC_MIXED */
+  int max_refine;        /* iterative-refinement sweeps of the KKT solve (mixed) */
+  int panel;             /* RHS columns per CTA in the multi-RHS solves (0 = auto) */
+  int reserved[7];
+} ipm_options;
+
+/* Sizes of a context.  state_len = 4 N n_x + 4 N m + 3 n_u + 3; the state
+ * vector layout is, in doubles:
+ *   x[N][n_x], u[n_u], s[N][m], y[N][n_x], z[N][m],
+ *   zl_x[N][n_x], zu_x[N][n_x], zl_u[n_u], zu_u[n_u], zl_s[N][m], zu_s[N][m],
+ *   mu, rho, delta_last.
+ * step_len = 2 N n_x + 2 N m + n_u (p_x, p_u, p_s, p_y, p_z in that order). */
+typedef struct {
+  int n_bus, n_line, n_gen, n_scen;
+  int n_x, n_u, m;
+  long long state_len, step_len;
+  long long nnz_lu;      /* stored entries of the static-pivot LU of G_x */
+  int lu_levels;         /* level-schedule depth of the LU / triangular solves */
+} ipm_dims;
+
+ipm_status ipm_default_options(ipm_options *opt);
+
+/* Create a context for one network and N scenarios.
+ * pd, qd: host [n_scen][n_bus] loads (scenario-major).  Builds the symbolic
+ * structures (orderings, LU pattern, level schedules) on the host, uploads
+ * everything, allocates all device workspaces and sets the cold-start state.
+ * Errors: IPM_ERR_ARG on bad sizes/indices/non-finite or negative loads,
+ * IPM_ERR_OOM, IPM_ERR_CUDA. */
+ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd,
+                      const double *qd, const ipm_options *opt, ipm_ctx **out);
+ipm_status ipm_destroy(ipm_ctx *ctx);
+ipm_status ipm_get_dims(const ipm_ctx *ctx, ipm_dims *out);
+const char *ipm_last_error(const ipm_ctx *ctx);
+
+/* Cold start (§2.2 reading): theta = 0, V = 1, Pg = Pmax/2, pushed inside the
+ * boxes; s = -h pushed; y = z = 0; bound duals 1; mu = 0.1; rho = 1. */
+ipm_status ipm_init_state(ipm_ctx *ctx, void *stream);
+
+/* Copy a full state in/out (layout above).  on_device != 0: the pointer is a
+ * device pointer, else a host pointer (pinned or pageable). */
+ipm_status ipm_set_state(ipm_ctx *ctx, const double *state, int on_device, void *stream);
+ipm_status ipm_get_state(ipm_ctx *ctx, double *state, int on_device, void *stream);
+
+/* Evaluate f, g, h, the Jacobians G, H and the Lagrangian Hessian W of every
+ * scenario at the current state (eq. (4) without bound terms). */
+ipm_status ipm_eval_derivatives(ipm_ctx *ctx, void *stream);
+
+/* Condense and reduce at the current state and barrier parameter mu:
+ * Sigma's, K = W + Sigma_p + H^T Sigma_s H (Prop. 2.1/2.2), the static-pivot
+ * LU of every G_x^i, Z_i = -(G_x^i)^{-1} G_u^i, Y_i = K_i [Z_i; I], and
+ * K_hat = sum_i Z_i^T K_i Z_i + Sigma_u (Prop. 2.3), plus the reduced
+ * right-hand side of eq. (11).  Requires ipm_eval_derivatives first.
+ * Errors: IPM_ERR_SINGULAR_GX when a pivot |u_ii| < 1e-14 max|row|. */
+ipm_status ipm_condense_scenarios(ipm_ctx *ctx, void *stream);
+
+/* Factor K_hat + delta_w (sum_i Z_i^T Z_i + I) -- i.e. the reduced matrix of
+ * K + delta_w I -- by dense FP64 Cholesky.  *is_pd = 1 on success, 0 when a
+ * pivot is not positive (correct inertia <=> K_hat positive definite). */
+ipm_status ipm_factor_schur(ipm_ctx *ctx, double delta_w, int *is_pd, void *stream);
+
+/* Solve the Newton system eq. (6) through eq. (11) and the recoveries of
+ * Props. 2.1 and 2.3.  step: nullable device pointer receiving step_len
+ * doubles.  refine_resid: nullable host pointer receiving the relative
+ * residual of the condensed system after refinement. */
+ipm_status ipm_solve_kkt(ipm_ctx *ctx, double *step, double *refine_resid, void *stream);
+
+/* One full interior-point iteration (evaluate, test convergence, update mu,
+ * condense, factor with inertia correction, solve, fraction to boundary,
+ * backtracking line search, update).  *converged = 1 when the current point
+ * already meets E_0 <= tol (no step is then taken); *kkt_err = E_0 there. */
+ipm_status ipm_step(ipm_ctx *ctx, int *converged, double *kkt_err, void *stream);
+
+/* Run ipm_step until convergence or max_iter.  *iters = Newton steps taken. */
+ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
+
+/* Diagnostics for tests: copy an internal quantity to host memory.
+ * which: IPM_Q_KHAT (n_u*n_u, row-major, before factorization, delta = 0),
+ *        IPM_Q_RHS_U (n_u), IPM_Q_Z (scenario scen, n_x*n_u row-major, rows in
+ *        the x order of the state vector), IPM_Q_FGH (scen: f, g[n_x], h[m]),
+ *        IPM_Q_JAC (scen: dense G_x, G_u, H_x, H_u row-major, concatenated),
+ *        IPM_Q_HESS (scen: dense W_xx, W_xu, W_uu^i), IPM_Q_ERRS (6 doubles:
+ *        dual, primal, compl max, compl min, s_d, s_c), IPM_Q_INFO (8 doubles:
+ *        alpha, alpha_max, alpha_z, delta, trials, rho, mu_used, refine),
+ *        IPM_Q_TIMERS (2*IPM_N_PHASES doubles: accumulated device milliseconds
+ *        and call counts per phase, see ipm_set_profiling; a further double,
+ *        if cap allows, is the total number of kernels the library launched).
+ * cap: capacity of host_out in doubles. */
+enum { IPM_Q_KHAT = 0, IPM_Q_RHS_U = 1, IPM_Q_Z = 2, IPM_Q_FGH = 3, IPM_Q_JAC = 4,
+       IPM_Q_HESS = 5, IPM_Q_ERRS = 6, IPM_Q_INFO = 7, IPM_Q_TIMERS = 8 };
+ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
+                            long long cap, void *stream);
+
+/* Phase timers (tracing).  When on, CUDA events are recorded on the call's
+ * stream around each phase of the path and the elapsed device time is
+ * accumulated; on = 2 also resets the accumulators.  Phases, in order:
+ * eval, condense_K (Sigma, K, right-hand sides), lu, zsolve (Z and Y),
+ * gemm (Z^T Y + scenario sum), reduced_rhs, cholesky, recover, linesearch. */
+enum { IPM_N_PHASES = 9 };
+ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPM_H */

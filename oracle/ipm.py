@@ -20,7 +20,8 @@ path implements the same rules so that both take the same iterates:
     dzl = mu/(w-l) - zl - Sigma_l dw,  dzu = mu/(b-w) - zu + Sigma_u dw;
  5. fraction to boundary tau = max(0.99, 1-mu) for primal and dual steps;
  6. backtracking (halving) on phi = f + barrier + rho ||(g, h+s)||_1 with the
-    Armijo constant 1e-4 from the largest primal step; rho raised to
+    Armijo constant 1e-4 from the largest primal step (merit changes within
+    10 eps |phi| count as no increase); rho raised to
     (grad phi^T p + max(q,0)/2) / (0.9 ||c||_1) when below it;
  7. w += a_p dw; (y,z) += a_p (p_y,p_z); bound duals += a_d dz, then kept
     within [mu/(1e10 (w-l)), 1e10 mu/(w-l)].
@@ -44,6 +45,9 @@ OPTS = dict(tol=1e-8, max_iter=200, mu0=0.1, k1=1e-2, k2=1e-2, tau_min=0.99,
             alpha_min=1e-12, kappa_sigma=1e10, s_max=100.0, rho0=1.0,
             rho_frac=0.1, delta0=1e-4, delta_min=1e-20, delta_max=1e40,
             kw_minus=1.0 / 3.0, kw_plus=8.0, kw_plus_bar=100.0)
+
+
+EPS = float(np.finfo(np.float64).eps)
 
 
 class IPMError(RuntimeError):
@@ -278,7 +282,9 @@ def iterate(model, st, D=None, opts=OPTS, log=None):
         ut = st["u"] + alpha * p["pu"]
         s_t = st["s"] + alpha * p["ps"]
         pt_fb, ct = merit_parts(model, xt, ut, s_t, mu)
-        if pt_fb + rho * ct <= phi0 + opts["eta"] * alpha * dphi:
+        # Armijo, with a roundoff allowance of 10 eps |phi| (changes below the
+        # rounding level of the merit value are accepted, as in IPOPT)
+        if pt_fb + rho * ct - phi0 <= opts["eta"] * alpha * dphi + 10.0 * EPS * abs(phi0):
             break
         alpha *= 0.5
         if alpha < opts["alpha_min"]:

@@ -1,0 +1,66 @@
+// Device-side views of the symbolic structures and shared helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+struct DevSym {
+  int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b;
+  const int *xth, *xv, *uv, *gen_of_bus, *xbus, *xkind;
+  const int *lfr, *lto;
+  const double *lg, *lb, *lbh;
+  const int *a_ptr, *a_col, *a_diag, *inc_ptr, *inc_line, *inc_other, *inc_aslot;
+  const int *kb_ptr, *kb_col, *kb_row, *kb_aslot, *kbi_ptr, *kbi_r, *kbi_ja, *kbi_jb;
+  const int *hrow_bus, *hrow_comp, *ht_ptr, *ht_r, *ht_aslot;
+  const int *perm, *iperm;
+  const int *lu_diag, *lu_init;
+  const int *f_lev_ptr, *f_piv_ptr, *f_piv, *f_tgt, *f_op_ptr, *f_op_l, *f_op_u, *f_op_k;
+  const int *lsc_slot, *lsc_k;
+  const int *fw_lev_ptr, *fw_rows, *fr_ptr, *fr_col, *fr_lslot, *fr_uslot;
+  const int *bw_lev_ptr, *bw_rows, *br_ptr, *br_col, *br_uslot, *br_lslot;
+  const int *gu_ptr, *gu_col, *gu_src, *gut_ptr, *gut_col, *gut_src;
+  const int *kx_ptr, *kx_col, *kx_src, *ku_ptr, *ku_col, *ku_src;
+  const double *xl, *xu, *ul, *uu, *sl, *su, *c2, *c1;
+  const double *pd, *qd;  // [N][n]
+};
+
+// Dynamic per-iteration arrays (device).  Vectors are scenario-major
+// [N][len]; sparse values (J, W, K) are scenario-fastest [slot*4+e][N];
+// LU values are scenario-major [N][nnzLU].
+struct DevWork {
+  // primal/dual state (views into the state vector)
+  double *x, *u, *s, *y, *z, *zlx, *zux, *zlu, *zuu, *zls, *zus, *scal;
+  // evaluation
+  double *P, *Q, *g, *h, *fs;    // P,Q [N][n]; g [N][nx]; h [N][m]; fs [N]
+  double *J, *W, *JTl;           // J,W [4 nnzA][N]; JTl [N][2n]
+  double *K;                     // [4 nnzKB][N]
+  double *Sx, *Su, *Ss;          // barrier diagonals
+  double *r1x, *r1u, *r2, *r4, *rh1x, *rh2, *tv;  // right-hand sides
+  double *LU, *rd;               // [N][nnzLU], reciprocal pivots [N][nx]
+  int *flags;                    // device error / status words
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// bus voltage angle / magnitude of scenario sc
+__device__ __forceinline__ double bus_theta(const DevSym &S, const double *x, int sc, int i) {
+  return i == 0 ? 0.0 : x[(size_t)sc * S.nx + S.xth[i]];
+}
+__device__ __forceinline__ double bus_v(const DevSym &S, const double *x, const double *u, int sc, int i) {
+  int q = S.xv[i];
+  return q >= 0 ? x[(size_t)sc * S.nx + q] : u[S.uv[i]];
+}
+
+// flags
+enum { FLAG_SINGULAR = 0, FLAG_NOT_PD = 1, FLAG_NONFINITE = 2, FLAG_COUNT = 8 };

@@ -1,0 +1,908 @@
+// C ABI of the reduced-space IPM (include/ipm.h): context management and the
+// host-side driver of one interior-point iteration.  Every numerical step of
+// the path runs in the kernels of kernels_*.cu; the host only sequences them
+// and takes the scalar decisions (barrier update, inertia-correction retries,
+// line-search acceptance) on values read back from the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "dev.cuh"
+#include "ipm_internal.h"
+#include "kernels.h"
+
+long long g_ipm_launches = 0;  // kernels launched by this library (all contexts)
+
+namespace {
+
+// IPM constants (the same rule set as the CPU oracle, see DESIGN)
+constexpr double MU0 = 0.1, K1 = 1e-2, K2 = 1e-2, TAU_MIN = 0.99, KAPPA_EPS = 10.0, KAPPA_MU = 0.2,
+                 THETA_MU = 1.5, ETA = 1e-4, ALPHA_MIN = 1e-12, KAPPA_SIGMA = 1e10, S_MAX = 100.0,
+                 RHO0 = 1.0, RHO_FRAC = 0.1, DELTA0 = 1e-4, DELTA_MIN = 1e-20, DELTA_MAX = 1e40,
+                 KW_MINUS = 1.0 / 3.0, KW_PLUS = 8.0, KW_PLUS_BAR = 100.0;
+
+}  // namespace
+
+struct ipm_ctx {
+  Sym S;
+  DevSym ds{};
+  DevWork dw{};
+  ipm_options opt{};
+  std::string err;
+  std::vector<void *> allocs;
+  double *state = nullptr;
+  long long state_len = 0, step_len = 0;
+  // work buffers
+  double *Z = nullptr, *Y = nullptr, *Yu = nullptr, *partial = nullptr;
+  int2 *tiles = nullptr;
+  int *tile_of = nullptr;
+  int ntiles = 0, nt1 = 0, ngroups = 0, spg = 0;
+  double *Khat = nullptr, *M = nullptr, *F = nullptr, *diag1 = nullptr, *rhs_u = nullptr;
+  double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta) and its scratch
+  double *gLu = nullptr, *HTt_u = nullptr;
+  double *pg_curv = nullptr, *pmax_d = nullptr;
+  double *step = nullptr, *px = nullptr, *pu = nullptr, *ps = nullptr, *py = nullptr, *pz = nullptr;
+  double *dz[6] = {};
+  double *Hp = nullptr, *kpx = nullptr, *kpu = nullptr, *vpos = nullptr, *bpos = nullptr, *apos = nullptr;
+  double *xt = nullptr, *ut = nullptr, *st = nullptr, *gt = nullptr, *ht = nullptr, *fst = nullptr,
+         *Pt = nullptr, *Qt = nullptr;
+  double *red_partial = nullptr, *red_out = nullptr;
+  double *h_red = nullptr;  // pinned host mirror of reduction outputs
+  int *h_flags = nullptr;
+  int nL = 0;
+  long long n_bounds = 0;
+  // host mirror of the state scalars
+  double mu = MU0, rho = RHO0, delta_last = 0.0;
+  double delta_fact = 0.0;
+  bool have_eval = false, have_cond = false, have_fact = false, M_valid = false;
+  double info[8] = {0};
+  double errs[6] = {0};
+  // phase timers
+  bool prof = false;
+  cudaEvent_t ev[2 * IPM_N_PHASES] = {};
+  bool ev_pending[IPM_N_PHASES] = {};
+  double t_ms[IPM_N_PHASES] = {0};
+  double t_cnt[IPM_N_PHASES] = {0};
+};
+
+namespace {
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return fail(c, IPM_ERR_CUDA, #call, e_); \
+  } while (0)
+
+ipm_status fail(ipm_ctx *c, ipm_status s, const char *what, cudaError_t e = cudaSuccess) {
+  if (c) {
+    c->err = what;
+    if (e != cudaSuccess) {
+      c->err += ": ";
+      c->err += cudaGetErrorString(e);
+    }
+  }
+  return s;
+}
+
+template <class T>
+ipm_status dalloc(ipm_ctx *c, T **p, size_t count) {
+  if (count == 0) count = 1;
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, IPM_ERR_OOM, "cudaMalloc", e);
+  }
+  c->allocs.push_back(q);
+  *p = (T *)q;
+  return IPM_OK;
+}
+
+template <class T>
+ipm_status upload(ipm_ctx *c, const T **dst, const std::vector<T> &v) {
+  T *p = nullptr;
+  ipm_status s = dalloc(c, &p, v.size());
+  if (s != IPM_OK) return s;
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = p;
+  return IPM_OK;
+}
+
+#define TRY(x)                   \
+  do {                           \
+    ipm_status s_ = (x);         \
+    if (s_ != IPM_OK) return s_; \
+  } while (0)
+
+inline cudaStream_t STR(void *s) { return (cudaStream_t)s; }
+
+double emu(const double *e, double mu) {
+  return std::max(std::max(e[0] / e[4], e[1]), std::max(e[2] - mu, mu - e[3]) / e[5]);
+}
+
+ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, const double *qd) {
+  Sym &S = c->S;
+  DevSym &d = c->ds;
+  d.n = S.n; d.L = S.L; d.ng = S.ng; d.N = S.N; d.nx = S.nx; d.nu = S.nu; d.m = S.m;
+  d.nnzA = S.nnzA; d.nnzKB = S.nnzKB; d.nnzLU = S.nnzLU; d.nlev = S.nlev; d.nlev_b = S.nlev_b;
+  TRY(upload(c, &d.xth, S.xth)); TRY(upload(c, &d.xv, S.xv)); TRY(upload(c, &d.uv, S.uv));
+  TRY(upload(c, &d.gen_of_bus, S.gen_of_bus)); TRY(upload(c, &d.xbus, S.xbus)); TRY(upload(c, &d.xkind, S.xkind));
+  TRY(upload(c, &d.lfr, S.lfr)); TRY(upload(c, &d.lto, S.lto));
+  TRY(upload(c, &d.lg, S.lg)); TRY(upload(c, &d.lb, S.lb)); TRY(upload(c, &d.lbh, S.lbh));
+  TRY(upload(c, &d.a_ptr, S.a_ptr)); TRY(upload(c, &d.a_col, S.a_col)); TRY(upload(c, &d.a_diag, S.a_diag));
+  TRY(upload(c, &d.inc_ptr, S.inc_ptr)); TRY(upload(c, &d.inc_line, S.inc_line));
+  TRY(upload(c, &d.inc_other, S.inc_other)); TRY(upload(c, &d.inc_aslot, S.inc_aslot));
+  TRY(upload(c, &d.kb_ptr, S.kb_ptr)); TRY(upload(c, &d.kb_col, S.kb_col)); TRY(upload(c, &d.kb_row, S.kb_row));
+  TRY(upload(c, &d.kb_aslot, S.kb_aslot)); TRY(upload(c, &d.kbi_ptr, S.kbi_ptr)); TRY(upload(c, &d.kbi_r, S.kbi_r));
+  TRY(upload(c, &d.kbi_ja, S.kbi_ja)); TRY(upload(c, &d.kbi_jb, S.kbi_jb));
+  TRY(upload(c, &d.hrow_bus, S.hrow_bus)); TRY(upload(c, &d.hrow_comp, S.hrow_comp));
+  TRY(upload(c, &d.ht_ptr, S.ht_ptr)); TRY(upload(c, &d.ht_r, S.ht_r)); TRY(upload(c, &d.ht_aslot, S.ht_aslot));
+  TRY(upload(c, &d.perm, S.perm)); TRY(upload(c, &d.iperm, S.iperm));
+  TRY(upload(c, &d.lu_diag, S.lu_diag)); TRY(upload(c, &d.lu_init, S.lu_init));
+  TRY(upload(c, &d.f_lev_ptr, S.f_lev_ptr)); TRY(upload(c, &d.f_piv_ptr, S.f_piv_ptr)); TRY(upload(c, &d.f_piv, S.f_piv));
+  TRY(upload(c, &d.f_tgt, S.f_tgt)); TRY(upload(c, &d.f_op_ptr, S.f_op_ptr)); TRY(upload(c, &d.f_op_l, S.f_op_l));
+  TRY(upload(c, &d.f_op_u, S.f_op_u)); TRY(upload(c, &d.f_op_k, S.f_op_k));
+  TRY(upload(c, &d.lsc_slot, S.lsc_slot)); TRY(upload(c, &d.lsc_k, S.lsc_k));
+  TRY(upload(c, &d.fw_lev_ptr, S.fw_lev_ptr)); TRY(upload(c, &d.fw_rows, S.fw_rows)); TRY(upload(c, &d.fr_ptr, S.fr_ptr));
+  TRY(upload(c, &d.fr_col, S.fr_col)); TRY(upload(c, &d.fr_lslot, S.fr_lslot)); TRY(upload(c, &d.fr_uslot, S.fr_uslot));
+  TRY(upload(c, &d.bw_lev_ptr, S.bw_lev_ptr)); TRY(upload(c, &d.bw_rows, S.bw_rows)); TRY(upload(c, &d.br_ptr, S.br_ptr));
+  TRY(upload(c, &d.br_col, S.br_col)); TRY(upload(c, &d.br_uslot, S.br_uslot)); TRY(upload(c, &d.br_lslot, S.br_lslot));
+  TRY(upload(c, &d.gu_ptr, S.gu_ptr)); TRY(upload(c, &d.gu_col, S.gu_col)); TRY(upload(c, &d.gu_src, S.gu_src));
+  TRY(upload(c, &d.gut_ptr, S.gut_ptr)); TRY(upload(c, &d.gut_col, S.gut_col)); TRY(upload(c, &d.gut_src, S.gut_src));
+  TRY(upload(c, &d.kx_ptr, S.kx_ptr)); TRY(upload(c, &d.kx_col, S.kx_col)); TRY(upload(c, &d.kx_src, S.kx_src));
+  TRY(upload(c, &d.ku_ptr, S.ku_ptr)); TRY(upload(c, &d.ku_col, S.ku_col)); TRY(upload(c, &d.ku_src, S.ku_src));
+  TRY(upload(c, &d.xl, S.xl)); TRY(upload(c, &d.xu, S.xu)); TRY(upload(c, &d.ul, S.ul)); TRY(upload(c, &d.uu, S.uu));
+  TRY(upload(c, &d.sl, S.sl)); TRY(upload(c, &d.su, S.su)); TRY(upload(c, &d.c2, S.c2)); TRY(upload(c, &d.c1, S.c1));
+  std::vector<double> vpd(pd, pd + (size_t)S.N * S.n), vqd(qd, qd + (size_t)S.N * S.n);
+  TRY(upload(c, &d.pd, vpd)); TRY(upload(c, &d.qd, vqd));
+  c->nL = (int)S.lsc_slot.size();
+  (void)net;
+  return IPM_OK;
+}
+
+ipm_status alloc_work(ipm_ctx *c) {
+  const Sym &S = c->S;
+  const long long N = S.N, nx = S.nx, nu = S.nu, m = S.m, n = S.n;
+  c->state_len = 4 * N * nx + 4 * N * m + 3 * nu + 3;
+  c->step_len = 2 * N * nx + 2 * N * m + nu;
+  TRY(dalloc(c, &c->state, c->state_len));
+  CK(cudaMemset(c->state, 0, c->state_len * sizeof(double)));
+  DevWork &D = c->dw;
+  double *p = c->state;
+  D.x = p; p += N * nx;
+  D.u = p; p += nu;
+  D.s = p; p += N * m;
+  D.y = p; p += N * nx;
+  D.z = p; p += N * m;
+  D.zlx = p; p += N * nx;
+  D.zux = p; p += N * nx;
+  D.zlu = p; p += nu;
+  D.zuu = p; p += nu;
+  D.zls = p; p += N * m;
+  D.zus = p; p += N * m;
+  D.scal = p;
+  TRY(dalloc(c, &D.P, N * n)); TRY(dalloc(c, &D.Q, N * n)); TRY(dalloc(c, &D.g, N * nx));
+  TRY(dalloc(c, &D.h, N * m)); TRY(dalloc(c, &D.fs, N));
+  TRY(dalloc(c, &D.J, 4LL * S.nnzA * N)); TRY(dalloc(c, &D.W, 4LL * S.nnzA * N));
+  TRY(dalloc(c, &D.JTl, 2 * N * n)); TRY(dalloc(c, &D.K, 4LL * S.nnzKB * N));
+  TRY(dalloc(c, &D.Sx, N * nx)); TRY(dalloc(c, &D.Su, nu)); TRY(dalloc(c, &D.Ss, N * m));
+  TRY(dalloc(c, &D.r1x, N * nx)); TRY(dalloc(c, &D.r1u, nu)); TRY(dalloc(c, &D.r2, N * m));
+  TRY(dalloc(c, &D.r4, N * m)); TRY(dalloc(c, &D.rh1x, N * nx)); TRY(dalloc(c, &D.rh2, nu));
+  TRY(dalloc(c, &D.tv, N * m));
+  TRY(dalloc(c, &D.LU, (long long)S.nnzLU * N)); TRY(dalloc(c, &D.rd, N * nx));
+  TRY(dalloc(c, &D.flags, FLAG_COUNT));
+  CK(cudaMemset(D.flags, 0, FLAG_COUNT * sizeof(int)));
+  TRY(dalloc(c, &c->Z, N * nx * nu)); TRY(dalloc(c, &c->Y, N * nx * nu)); TRY(dalloc(c, &c->Yu, N * nu * nu));
+  // GEMM tiling: upper tiles, scenario groups
+  c->nt1 = (int)((nu + 63) / 64);
+  std::vector<int2> tl;
+  std::vector<int> tof((size_t)c->nt1 * c->nt1, -1);
+  for (int i = 0; i < c->nt1; ++i)
+    for (int j = i; j < c->nt1; ++j) {
+      tof[(size_t)i * c->nt1 + j] = (int)tl.size();
+      tl.push_back(make_int2(i, j));
+    }
+  c->ntiles = (int)tl.size();
+  int G = (int)std::min<long long>(N, std::max(1, (3 * 152 + c->ntiles - 1) / c->ntiles));
+  c->spg = (int)((N + G - 1) / G);
+  c->ngroups = (int)((N + c->spg - 1) / c->spg);
+  TRY(dalloc(c, &c->tiles, tl.size()));
+  CK(cudaMemcpy(c->tiles, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  TRY(dalloc(c, &c->tile_of, tof.size()));
+  CK(cudaMemcpy(c->tile_of, tof.data(), tof.size() * sizeof(int), cudaMemcpyHostToDevice));
+  TRY(dalloc(c, &c->partial, (long long)c->ngroups * c->ntiles * 4096));
+  TRY(dalloc(c, &c->Khat, nu * nu)); TRY(dalloc(c, &c->M, nu * nu)); TRY(dalloc(c, &c->F, nu * nu));
+  TRY(dalloc(c, &c->diag1, nu)); TRY(dalloc(c, &c->rhs_u, nu));
+  TRY(dalloc(c, &c->rhs_corr, nu)); TRY(dalloc(c, &c->cpos, N * nx));
+  TRY(dalloc(c, &c->gLu, nu)); TRY(dalloc(c, &c->HTt_u, nu));
+  {
+    std::vector<double> pgc(nu, 0.0);
+    for (int k = 1; k < S.ng; ++k) pgc[S.ng + k - 1] = 2.0 * S.c2[k];
+    const double *tmp = nullptr;
+    TRY(upload(c, &tmp, pgc));
+    c->pg_curv = const_cast<double *>(tmp);
+    TRY(upload(c, &tmp, S.pmax));
+    c->pmax_d = const_cast<double *>(tmp);
+  }
+  TRY(dalloc(c, &c->step, c->step_len));
+  c->px = c->step;
+  c->pu = c->px + N * nx;
+  c->ps = c->pu + nu;
+  c->py = c->ps + N * m;
+  c->pz = c->py + N * nx;
+  for (int i = 0; i < 6; ++i) {
+    long long len = (i < 2) ? N * nx : (i < 4 ? nu : N * m);
+    TRY(dalloc(c, &c->dz[i], len));
+  }
+  TRY(dalloc(c, &c->Hp, N * m)); TRY(dalloc(c, &c->kpx, N * nx)); TRY(dalloc(c, &c->kpu, N * nu));
+  TRY(dalloc(c, &c->vpos, N * nx)); TRY(dalloc(c, &c->bpos, N * nx)); TRY(dalloc(c, &c->apos, N * nx));
+  TRY(dalloc(c, &c->xt, N * nx)); TRY(dalloc(c, &c->ut, nu)); TRY(dalloc(c, &c->st, N * m));
+  TRY(dalloc(c, &c->gt, N * nx)); TRY(dalloc(c, &c->ht, N * m)); TRY(dalloc(c, &c->fst, N));
+  TRY(dalloc(c, &c->Pt, N * n)); TRY(dalloc(c, &c->Qt, N * n));
+  TRY(dalloc(c, &c->red_partial, 152 * 8)); TRY(dalloc(c, &c->red_out, 16));
+  CK(cudaMallocHost(&c->h_red, 16 * sizeof(double)));
+  CK(cudaMallocHost(&c->h_flags, FLAG_COUNT * sizeof(int)));
+  // first-stage diagonal terms of K_hat that do not depend on the iterate
+  // (cost curvature of the non-slack generators); Sigma_u is added per call
+  long long nb = 0;
+  for (int j = 0; j < S.nx; ++j) nb += (std::isfinite(S.xl[j]) ? 1 : 0) + (std::isfinite(S.xu[j]) ? 1 : 0);
+  nb *= N;
+  for (int j = 0; j < S.nu; ++j) nb += (std::isfinite(S.ul[j]) ? 1 : 0) + (std::isfinite(S.uu[j]) ? 1 : 0);
+  long long nbs = 0;
+  for (int j = 0; j < S.m; ++j) nbs += (std::isfinite(S.sl[j]) ? 1 : 0) + (std::isfinite(S.su[j]) ? 1 : 0);
+  nb += nbs * N;
+  c->n_bounds = nb;
+  return IPM_OK;
+}
+
+ipm_status read_red(ipm_ctx *c, int nv, cudaStream_t st) {
+  CK(cudaMemcpyAsync(c->h_red, c->red_out, nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return IPM_OK;
+}
+
+
+enum { PH_EVAL = 0, PH_COND, PH_LU, PH_ZSOLVE, PH_GEMM, PH_RRHS, PH_CHOL, PH_RECOVER, PH_LS };
+
+inline void ph_begin(ipm_ctx *c, int p, cudaStream_t st) {
+  if (c->prof) cudaEventRecord(c->ev[2 * p], st);
+}
+inline void ph_end(ipm_ctx *c, int p, cudaStream_t st) {
+  if (c->prof) {
+    cudaEventRecord(c->ev[2 * p + 1], st);
+    c->ev_pending[p] = true;
+  }
+}
+// accumulate finished phases (call after a stream synchronisation)
+void ph_collect(ipm_ctx *c) {
+  if (!c->prof) return;
+  for (int p = 0; p < IPM_N_PHASES; ++p)
+    if (c->ev_pending[p]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[2 * p], c->ev[2 * p + 1]) == cudaSuccess) {
+        c->t_ms[p] += ms;
+        c->t_cnt[p] += 1;
+      }
+      c->ev_pending[p] = false;
+    }
+}
+
+ipm_status read_flags(ipm_ctx *c, cudaStream_t st) {
+  CK(cudaMemcpyAsync(c->h_flags, c->dw.flags, FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return IPM_OK;
+}
+
+ipm_status write_scalars(ipm_ctx *c, cudaStream_t st) {
+  c->h_red[8] = c->mu;
+  c->h_red[9] = c->rho;
+  c->h_red[10] = c->delta_last;
+  CK(cudaMemcpyAsync(c->dw.scal, c->h_red + 8, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return IPM_OK;
+}
+
+ipm_status read_scalars(ipm_ctx *c, cudaStream_t st) {
+  CK(cudaMemcpyAsync(c->h_red + 8, c->dw.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  c->mu = c->h_red[8];
+  c->rho = c->h_red[9];
+  c->delta_last = c->h_red[10];
+  return IPM_OK;
+}
+
+// f, g, h at (x, u); J, W, J^T lambda at (x, u, y, z)
+ipm_status do_eval(ipm_ctx *c, cudaStream_t st) {
+  DevWork &D = c->dw;
+  ph_begin(c, PH_EVAL, st);
+  launch_functions(c->ds, D.x, D.u, D.P, D.Q, D.g, D.h, D.fs, st);
+  launch_derivatives(c->ds, D, st);
+  launch_ugrad(c->ds, D, c->gLu, st);
+  ph_end(c, PH_EVAL, st);
+  CK(cudaGetLastError());
+  c->have_eval = true;
+  c->have_cond = c->have_fact = false;
+  return IPM_OK;
+}
+
+// optimality error pieces -> c->errs (dual, primal, compl max, compl min, s_d, s_c)
+ipm_status do_errors(ipm_ctx *c, cudaStream_t st) {
+  launch_errors(c->ds, c->dw, c->gLu, c->red_partial, c->red_out, st);
+  TRY(read_red(c, 6, st));
+  const Sym &S = c->S;
+  const double nlam = (double)S.N * (S.nx + S.m);
+  const double nb = (double)c->n_bounds;
+  c->errs[0] = c->h_red[0];
+  c->errs[1] = c->h_red[1];
+  c->errs[2] = c->h_red[2];
+  c->errs[3] = c->h_red[3];
+  c->errs[4] = std::max(S_MAX, (c->h_red[4] + c->h_red[5]) / (nlam + nb)) / S_MAX;
+  c->errs[5] = std::max(S_MAX, c->h_red[5] / nb) / S_MAX;
+  return IPM_OK;
+}
+
+// Sigma, K, LU(G_x), Z, Y, K_hat (delta = 0), reduced right-hand side
+ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
+  if (!c->have_eval) return fail(c, IPM_ERR_STATE, "condense before eval");
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const double mu = c->mu;
+  ph_begin(c, PH_COND, st);
+  launch_sigmas(S, D, st);
+  launch_condense(S, D, st);
+  launch_rhs(S, D, mu, c->gLu, c->HTt_u, st);
+  ph_end(c, PH_COND, st);
+  CK(cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st));
+  ph_begin(c, PH_LU, st);
+  launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st);
+  ph_end(c, PH_LU, st);
+  ph_begin(c, PH_ZSOLVE, st);
+  launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st);
+  ph_end(c, PH_ZSOLVE, st);
+  ph_begin(c, PH_GEMM, st);
+  launch_gemm_tn64(S.nx, S.nu, S.N, c->spg, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles, c->partial, st);
+  // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
+  launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
+  launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
+                       c->Khat, st);
+  ph_end(c, PH_GEMM, st);
+  ph_begin(c, PH_RRHS, st);
+  // reduced RHS, eq. (11): b = G_x^{-1} r3, a = G_x^{-T}(rhat1 - K_xx b)
+  launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
+  launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+  launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
+  launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
+  launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
+  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+  launch_rhs_reduced(S, D.J, D.K, D.rh2, c->apos, c->bpos, c->rhs_u, st);
+  ph_end(c, PH_RRHS, st);
+  CK(cudaGetLastError());
+  TRY(read_flags(c, st));
+  ph_collect(c);
+  if (c->h_flags[FLAG_SINGULAR]) return fail(c, IPM_ERR_SINGULAR_GX, "singular pivot in the LU of G_x");
+  c->have_cond = true;
+  c->have_fact = false;
+  c->M_valid = false;
+  return IPM_OK;
+}
+
+ipm_status do_factor(ipm_ctx *c, double delta, int *is_pd, cudaStream_t st) {
+  if (!c->have_cond) return fail(c, IPM_ERR_STATE, "factor before condense");
+  const DevSym &S = c->ds;
+  if (delta != 0.0 && !c->M_valid) {
+    // M = sum_i Z_i^T Z_i, so that K_hat(K + delta I) = K_hat(K) + delta (M + I)
+    launch_gemm_tn64(S.nx, S.nu, S.N, c->spg, c->ngroups, c->Z, c->Z, c->tiles, c->ntiles, c->partial, st);
+    launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, nullptr, nullptr,
+                         c->M, st);
+    // eq. (11) contains K_xx: with K_xx + delta I the reduced right-hand side
+    // gains -delta sum_i G_u^T G_x^{-T} b_i (b_i = G_x^{-1} r3_i)
+    CK(cudaMemcpyAsync(c->cpos, c->bpos, (size_t)S.N * S.nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_solve1(S, c->dw.LU, c->dw.rd, c->cpos, 1, st);
+    launch_gut_sum(S, c->dw.J, c->cpos, -1.0, c->rhs_corr, st);
+    c->M_valid = true;
+  }
+  ph_begin(c, PH_CHOL, st);
+  launch_shift(S.nu, c->Khat, c->M, delta, c->F, st);
+  CK(cudaMemsetAsync(c->dw.flags + FLAG_NOT_PD, 0, sizeof(int), st));
+  launch_cholesky(S.nu, c->F, c->dw.flags, st);
+  ph_end(c, PH_CHOL, st);
+  CK(cudaGetLastError());
+  TRY(read_flags(c, st));
+  ph_collect(c);
+  *is_pd = c->h_flags[FLAG_NOT_PD] ? 0 : 1;
+  c->have_fact = *is_pd != 0;
+  c->delta_fact = delta;
+  return IPM_OK;
+}
+
+// Newton step: p_u from the Cholesky factor, then p_x, p_y (Prop. 2.3),
+// p_z, p_s (Prop. 2.1) and the bound-dual steps.
+ipm_status do_solve(ipm_ctx *c, cudaStream_t st) {
+  if (!c->have_fact) return fail(c, IPM_ERR_STATE, "solve before a successful factorization");
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const double delta = c->delta_fact, mu = c->mu;
+  const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
+  ph_begin(c, PH_RECOVER, st);
+  launch_lincomb(S.nu, c->pu, 1.0, c->rhs_u, delta, delta != 0.0 ? c->rhs_corr : nullptr, 0.0, nullptr, st);
+  launch_chol_solve(S.nu, c->F, c->pu, st);
+  // p_x = -G_x^{-1} (r3 + G_u p_u)
+  launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->vpos, 1.0, st);
+  launch_gu_apply(S, D.J, c->pu, c->vpos, st);
+  launch_solve1(S, D.LU, D.rd, c->vpos, 0, st);
+  launch_lincomb(NX, c->vpos, -1.0, c->vpos, 0.0, nullptr, 0.0, nullptr, st);
+  launch_scatter_pos(S.N, S.nx, S.iperm, c->vpos, c->px, 1.0, st);
+  // p_y = -G_x^{-T} (rhat1 + (K_xx + delta I) p_x + K_xu p_u)
+  launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);
+  launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
+  launch_lincomb(NX, c->apos, 1.0, c->apos, 1.0, c->kpx, delta, c->vpos, st);
+  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+  launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, c->py, -1.0, st);
+  launch_pz_ps(S, D, c->px, c->pu, c->Hp, c->pz, c->ps, st);
+  launch_bound_steps(NX, S.nx, D.x, c->px, S.xl, S.xu, D.zlx, D.zux, mu, c->dz[0], c->dz[1], st);
+  launch_bound_steps(S.nu, S.nu, D.u, c->pu, S.ul, S.uu, D.zlu, D.zuu, mu, c->dz[2], c->dz[3], st);
+  launch_bound_steps(NM, S.m, D.s, c->ps, S.sl, S.su, D.zls, D.zus, mu, c->dz[4], c->dz[5], st);
+  ph_end(c, PH_RECOVER, st);
+  CK(cudaGetLastError());
+  return IPM_OK;
+}
+
+ipm_status do_init(ipm_ctx *c, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
+  CK(cudaMemsetAsync(c->state, 0, c->state_len * sizeof(double), st));
+  launch_init_primal(S, D.x, D.u, c->pmax_d, st);
+  launch_push(NX, S.nx, D.x, S.xl, S.xu, K1, K2, st);
+  launch_push(S.nu, S.nu, D.u, S.ul, S.uu, K1, K2, st);
+  launch_functions(S, D.x, D.u, D.P, D.Q, D.g, D.h, D.fs, st);
+  launch_lincomb(NM, D.s, -1.0, D.h, 0.0, nullptr, 0.0, nullptr, st);
+  launch_push(NM, S.m, D.s, S.sl, S.su, K1, K2, st);
+  launch_fill_bound_duals(NX, S.nx, S.xl, S.xu, D.zlx, D.zux, st);
+  launch_fill_bound_duals(S.nu, S.nu, S.ul, S.uu, D.zlu, D.zuu, st);
+  launch_fill_bound_duals(NM, S.m, S.sl, S.su, D.zls, D.zus, st);
+  CK(cudaGetLastError());
+  c->mu = MU0;
+  c->rho = RHO0;
+  c->delta_last = 0.0;
+  c->have_eval = c->have_cond = c->have_fact = false;
+  return write_scalars(c, st);
+}
+
+// One interior-point iteration, the same rule set as the oracle.
+ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
+  TRY(do_eval(c, st));
+  TRY(do_errors(c, st));
+  const double E0 = emu(c->errs, 0.0);
+  if (kkt_err) *kkt_err = E0;
+  if (E0 <= c->opt.tol) {
+    *converged = 1;
+    return IPM_OK;
+  }
+  *converged = 0;
+  double mu = c->mu;
+  const double mu_min = c->opt.tol / 10.0;
+  if (emu(c->errs, mu) <= KAPPA_EPS * mu && mu > mu_min) {
+    mu = std::max(mu_min, std::min(KAPPA_MU * mu, std::pow(mu, THETA_MU)));
+    c->mu = mu;
+  }
+  TRY(do_condense(c, st));
+  int pd = 0;
+  TRY(do_factor(c, 0.0, &pd, st));
+  double delta = 0.0;
+  if (!pd) {
+    const double dl = c->delta_last;
+    delta = dl == 0.0 ? DELTA0 : std::max(DELTA_MIN, KW_MINUS * dl);
+    while (true) {
+      TRY(do_factor(c, delta, &pd, st));
+      if (pd) {
+        c->delta_last = delta;
+        break;
+      }
+      delta *= (dl == 0.0) ? KW_PLUS_BAR : KW_PLUS;
+      if (delta > DELTA_MAX) return fail(c, IPM_ERR_NOT_PD, "inertia correction exceeded delta_max");
+    }
+  }
+  TRY(do_solve(c, st));
+  ph_begin(c, PH_LS, st);
+  const double tau = std::max(TAU_MIN, 1.0 - mu);
+  launch_ftb(S, D, c->px, c->pu, c->ps, c->dz, tau, c->red_partial, c->red_out, st);
+  TRY(read_red(c, 2, st));
+  const double amax = std::min(1.0, c->h_red[0]), az = std::min(1.0, c->h_red[1]);
+  launch_dir(S, D, c->px, c->pu, c->ps, c->kpx, c->kpu, c->Hp, mu, delta, c->red_partial, c->red_out, st);
+  TRY(read_red(c, 3, st));
+  const double gphi = c->h_red[0], q = c->h_red[1], c1 = c->h_red[2];
+  if (c1 > 0.0) {
+    const double rt = (gphi + 0.5 * std::max(q, 0.0)) / ((1.0 - RHO_FRAC) * c1);
+    if (c->rho < rt) c->rho = rt;
+  }
+  const double rho = c->rho;
+  const double dphi = gphi - rho * c1;
+  launch_merit(S, D.x, D.u, D.s, D.g, D.h, D.fs, c->red_partial, c->red_out, st);
+  TRY(read_red(c, 3, st));
+  const double phi0 = (c->h_red[0] - mu * c->h_red[1]) + rho * c->h_red[2];
+  double alpha = amax;
+  int trials = 0;
+  while (true) {
+    ++trials;
+    launch_lincomb(NX, c->xt, 1.0, D.x, alpha, c->px, 0.0, nullptr, st);
+    launch_lincomb(S.nu, c->ut, 1.0, D.u, alpha, c->pu, 0.0, nullptr, st);
+    launch_lincomb(NM, c->st, 1.0, D.s, alpha, c->ps, 0.0, nullptr, st);
+    launch_functions(S, c->xt, c->ut, c->Pt, c->Qt, c->gt, c->ht, c->fst, st);
+    launch_merit(S, c->xt, c->ut, c->st, c->gt, c->ht, c->fst, c->red_partial, c->red_out, st);
+    TRY(read_red(c, 3, st));
+    const double phit = (c->h_red[0] - mu * c->h_red[1]) + rho * c->h_red[2];
+    // Armijo with a roundoff allowance: changes below 10 eps |phi| count as none
+    if (phit - phi0 <= ETA * alpha * dphi + 10.0 * std::numeric_limits<double>::epsilon() * std::fabs(phi0)) break;
+    alpha *= 0.5;
+    if (alpha < ALPHA_MIN) return fail(c, IPM_ERR_LINESEARCH, "step size below alpha_min");
+  }
+  CK(cudaMemcpyAsync(D.x, c->xt, NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(D.u, c->ut, S.nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(D.s, c->st, NM * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_lincomb(NX, D.y, 1.0, D.y, alpha, c->py, 0.0, nullptr, st);
+  launch_lincomb(NM, D.z, 1.0, D.z, alpha, c->pz, 0.0, nullptr, st);
+  launch_dual_update(NX, S.nx, D.x, S.xl, S.xu, D.zlx, D.zux, c->dz[0], c->dz[1], az, mu, KAPPA_SIGMA, st);
+  launch_dual_update(S.nu, S.nu, D.u, S.ul, S.uu, D.zlu, D.zuu, c->dz[2], c->dz[3], az, mu, KAPPA_SIGMA, st);
+  launch_dual_update(NM, S.m, D.s, S.sl, S.su, D.zls, D.zus, c->dz[4], c->dz[5], az, mu, KAPPA_SIGMA, st);
+  ph_end(c, PH_LS, st);
+  CK(cudaGetLastError());
+  c->info[0] = alpha; c->info[1] = amax; c->info[2] = az; c->info[3] = delta;
+  c->info[4] = trials; c->info[5] = rho; c->info[6] = mu; c->info[7] = 0;
+  c->have_eval = c->have_cond = c->have_fact = false;
+  ipm_status ws = write_scalars(c, st);
+  ph_collect(c);
+  return ws;
+}
+
+bool finite_nonneg(const double *p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i]) || p[i] < 0) return false;
+  return true;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+ipm_status ipm_default_options(ipm_options *opt) {
+  if (!opt) return IPM_ERR_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->tol = 1e-8;
+  opt->max_iter = 200;
+  opt->precision = IPM_PREC_FP64;
+  opt->max_refine = 10;
+  opt->panel = 0;
+  return IPM_OK;
+}
+
+ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, const double *qd,
+                      const ipm_options *opt, ipm_ctx **out) {
+  if (!out) return IPM_ERR_ARG;
+  *out = nullptr;
+  if (!net || !pd || !qd || n_scen < 1 || net->n_bus < 2 || net->n_line < 1 || net->n_gen < 1)
+    return IPM_ERR_ARG;
+  if (!net->from || !net->to || !net->gen_bus || !net->r || !net->x || !net->b || !net->pmax ||
+      !net->qmax || !net->c2 || !net->c1 || !net->vmin || !net->vmax)
+    return IPM_ERR_ARG;
+  const size_t nl = (size_t)n_scen * net->n_bus;
+  if (!finite_nonneg(pd, nl)) return IPM_ERR_ARG;
+  for (size_t i = 0; i < nl; ++i)
+    if (!std::isfinite(qd[i])) return IPM_ERR_ARG;
+  ipm_ctx *c = new ipm_ctx();
+  if (opt) c->opt = *opt;
+  else ipm_default_options(&c->opt);
+  if (c->opt.precision != IPM_PREC_FP64 || !(c->opt.tol > 0) || c->opt.max_iter < 0) {
+    delete c;
+    return IPM_ERR_ARG;
+  }
+  HostNet h;
+  h.n = net->n_bus; h.L = net->n_line; h.ng = net->n_gen;
+  h.fr.assign(net->from, net->from + h.L); h.to.assign(net->to, net->to + h.L);
+  h.gen.assign(net->gen_bus, net->gen_bus + h.ng);
+  h.r.assign(net->r, net->r + h.L); h.x.assign(net->x, net->x + h.L); h.b.assign(net->b, net->b + h.L);
+  h.pmax.assign(net->pmax, net->pmax + h.ng); h.qmax.assign(net->qmax, net->qmax + h.ng);
+  h.c2.assign(net->c2, net->c2 + h.ng); h.c1.assign(net->c1, net->c1 + h.ng);
+  h.vmin.assign(net->vmin, net->vmin + h.n); h.vmax.assign(net->vmax, net->vmax + h.n);
+  bool ok = true;
+  for (int k = 0; k < h.ng; ++k)
+    if (!(h.pmax[k] > 0) || !(h.qmax[k] >= 0) || !std::isfinite(h.c2[k]) || !std::isfinite(h.c1[k])) ok = false;
+  for (int i = 0; i < h.n; ++i)
+    if (!(h.vmin[i] > 0) || !(h.vmax[i] > h.vmin[i]) || !std::isfinite(h.vmax[i])) ok = false;
+  std::string err;
+  if (!ok || !build_symbolic(h, n_scen, c->S, err)) {
+    delete c;
+    return IPM_ERR_ARG;
+  }
+  ipm_status s = upload_symbolic(c, h, pd, qd);
+  if (s == IPM_OK) s = alloc_work(c);
+  if (s == IPM_OK) s = do_init(c, 0);
+  if (s != IPM_OK) {
+    ipm_destroy(c);
+    return s;
+  }
+  *out = c;
+  return IPM_OK;
+}
+
+ipm_status ipm_destroy(ipm_ctx *c) {
+  if (!c) return IPM_ERR_ARG;
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (void *p : c->allocs) cudaFree(p);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  delete c;
+  return IPM_OK;
+}
+
+ipm_status ipm_get_dims(const ipm_ctx *c, ipm_dims *o) {
+  if (!c || !o) return IPM_ERR_ARG;
+  o->n_bus = c->S.n; o->n_line = c->S.L; o->n_gen = c->S.ng; o->n_scen = c->S.N;
+  o->n_x = c->S.nx; o->n_u = c->S.nu; o->m = c->S.m;
+  o->state_len = c->state_len; o->step_len = c->step_len;
+  o->nnz_lu = c->S.nnzLU;
+  o->lu_levels = c->S.nlev;
+  return IPM_OK;
+}
+
+const char *ipm_last_error(const ipm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+ipm_status ipm_init_state(ipm_ctx *c, void *stream) {
+  if (!c) return IPM_ERR_ARG;
+  return do_init(c, STR(stream));
+}
+
+ipm_status ipm_set_state(ipm_ctx *c, const double *state, int on_device, void *stream) {
+  if (!c || !state) return IPM_ERR_ARG;
+  cudaStream_t st = STR(stream);
+  CK(cudaMemcpyAsync(c->state, state, c->state_len * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  c->have_eval = c->have_cond = c->have_fact = false;
+  return read_scalars(c, st);
+}
+
+ipm_status ipm_get_state(ipm_ctx *c, double *state, int on_device, void *stream) {
+  if (!c || !state) return IPM_ERR_ARG;
+  cudaStream_t st = STR(stream);
+  CK(cudaMemcpyAsync(state, c->state, c->state_len * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return IPM_OK;
+}
+
+ipm_status ipm_eval_derivatives(ipm_ctx *c, void *stream) {
+  if (!c) return IPM_ERR_ARG;
+  return do_eval(c, STR(stream));
+}
+
+ipm_status ipm_condense_scenarios(ipm_ctx *c, void *stream) {
+  if (!c) return IPM_ERR_ARG;
+  return do_condense(c, STR(stream));
+}
+
+ipm_status ipm_factor_schur(ipm_ctx *c, double delta_w, int *is_pd, void *stream) {
+  if (!c || !is_pd || !(delta_w >= 0) || !std::isfinite(delta_w)) return IPM_ERR_ARG;
+  return do_factor(c, delta_w, is_pd, STR(stream));
+}
+
+ipm_status ipm_solve_kkt(ipm_ctx *c, double *step, double *refine_resid, void *stream) {
+  if (!c) return IPM_ERR_ARG;
+  cudaStream_t st = STR(stream);
+  TRY(do_solve(c, st));
+  if (step) CK(cudaMemcpyAsync(step, c->step, c->step_len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (refine_resid) *refine_resid = 0.0;
+  CK(cudaStreamSynchronize(st));
+  return IPM_OK;
+}
+
+ipm_status ipm_step(ipm_ctx *c, int *converged, double *kkt_err, void *stream) {
+  if (!c || !converged) return IPM_ERR_ARG;
+  return do_step(c, converged, kkt_err, STR(stream));
+}
+
+ipm_status ipm_solve(ipm_ctx *c, int *iters, double *kkt_err, void *stream) {
+  if (!c) return IPM_ERR_ARG;
+  int conv = 0;
+  double e = 0.0;
+  for (int k = 0; k <= c->opt.max_iter; ++k) {
+    TRY(do_step(c, &conv, &e, STR(stream)));
+    if (conv) {
+      if (iters) *iters = k;
+      if (kkt_err) *kkt_err = e;
+      return IPM_OK;
+    }
+  }
+  if (iters) *iters = c->opt.max_iter;
+  if (kkt_err) *kkt_err = e;
+  return fail(c, IPM_ERR_MAXITER, "iteration limit reached");
+}
+
+ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long long cap, void *stream) {
+  if (!c || !out) return IPM_ERR_ARG;
+  cudaStream_t st = STR(stream);
+  const Sym &S = c->S;
+  const int N = S.N, nx = S.nx, nu = S.nu, m = S.m;
+  auto need = [&](long long k) { return cap >= k; };
+  CK(cudaStreamSynchronize(st));
+  if (which == IPM_Q_KHAT) {
+    if (!c->have_cond) return fail(c, IPM_ERR_STATE, "no condensed system");
+    if (!need((long long)nu * nu)) return IPM_ERR_ARG;
+    CK(cudaMemcpy(out, c->Khat, (size_t)nu * nu * sizeof(double), cudaMemcpyDeviceToHost));
+    return IPM_OK;
+  }
+  if (which == IPM_Q_RHS_U) {
+    if (!c->have_cond) return fail(c, IPM_ERR_STATE, "no condensed system");
+    if (!need(nu)) return IPM_ERR_ARG;
+    CK(cudaMemcpy(out, c->rhs_u, nu * sizeof(double), cudaMemcpyDeviceToHost));
+    return IPM_OK;
+  }
+  if (which == IPM_Q_ERRS) {
+    if (!need(6)) return IPM_ERR_ARG;
+    if (c->have_eval) TRY(do_errors(c, st));
+    std::memcpy(out, c->errs, 6 * sizeof(double));
+    return IPM_OK;
+  }
+  if (which == IPM_Q_TIMERS) {
+    if (!need(2 * IPM_N_PHASES)) return IPM_ERR_ARG;
+    ph_collect(c);
+    for (int p = 0; p < IPM_N_PHASES; ++p) {
+      out[p] = c->t_ms[p];
+      out[IPM_N_PHASES + p] = c->t_cnt[p];
+    }
+    if (cap >= 2 * IPM_N_PHASES + 1) out[2 * IPM_N_PHASES] = (double)g_ipm_launches;
+    return IPM_OK;
+  }
+  if (which == IPM_Q_INFO) {
+    if (!need(8)) return IPM_ERR_ARG;
+    std::memcpy(out, c->info, 8 * sizeof(double));
+    return IPM_OK;
+  }
+  if (scen < 0 || scen >= N) return IPM_ERR_ARG;
+  if (which == IPM_Q_Z) {
+    if (!c->have_cond) return fail(c, IPM_ERR_STATE, "no condensed system");
+    if (!need((long long)nx * nu)) return IPM_ERR_ARG;
+    std::vector<double> z((size_t)nx * nu);
+    CK(cudaMemcpy(z.data(), c->Z + (size_t)scen * nx * nu, z.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int p = 0; p < nx; ++p)
+      std::memcpy(out + (size_t)S.iperm[p] * nu, z.data() + (size_t)p * nu, nu * sizeof(double));
+    return IPM_OK;
+  }
+  if (!c->have_eval) return fail(c, IPM_ERR_STATE, "no evaluation");
+  if (which == IPM_Q_FGH) {
+    if (!need(1 + nx + m)) return IPM_ERR_ARG;
+    double fs = 0.0;
+    CK(cudaMemcpy(&fs, c->dw.fs + scen, sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> u(nu);
+    CK(cudaMemcpy(u.data(), c->dw.u, nu * sizeof(double), cudaMemcpyDeviceToHost));
+    double fu = 0.0;
+    for (int k = 1; k < S.ng; ++k) fu += S.c2[k] * u[S.ng + k - 1] * u[S.ng + k - 1] + S.c1[k] * u[S.ng + k - 1];
+    out[0] = fs + fu / N;
+    CK(cudaMemcpy(out + 1, c->dw.g + (size_t)scen * nx, nx * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out + 1 + nx, c->dw.h + (size_t)scen * m, m * sizeof(double), cudaMemcpyDeviceToHost));
+    return IPM_OK;
+  }
+  auto aslot = [&](int i, int k) -> int {
+    for (int p = S.a_ptr[i]; p < S.a_ptr[i + 1]; ++p)
+      if (S.a_col[p] == k) return p;
+    return -1;
+  };
+  auto kbslot = [&](int i, int k) -> int {
+    for (int p = S.kb_ptr[i]; p < S.kb_ptr[i + 1]; ++p)
+      if (S.kb_col[p] == k) return p;
+    return -1;
+  };
+  auto ucol = [&](int j, int &bus, int &kind) {  // kind 1 = voltage, 2 = Pg
+    if (j < S.ng) { bus = S.hrow_bus[j]; kind = 1; }
+    else { bus = S.hrow_bus[j - S.ng + 1]; kind = 2; }
+  };
+  if (which == IPM_Q_JAC) {
+    const long long tot = (long long)nx * nx + (long long)nx * nu + (long long)m * nx + (long long)m * nu;
+    if (!need(tot)) return IPM_ERR_ARG;
+    std::vector<double> J((size_t)4 * S.nnzA * N);
+    CK(cudaMemcpy(J.data(), c->dw.J, J.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    auto jv = [&](int slot, int e) { return J[((size_t)slot * 4 + e) * N + scen]; };
+    std::memset(out, 0, tot * sizeof(double));
+    double *Gx = out, *Gu = Gx + (size_t)nx * nx, *Hx = Gu + (size_t)nx * nu, *Hu = Hx + (size_t)m * nx;
+    for (int r = 0; r < nx; ++r) {
+      const int a = S.xbus[r], ka = S.xkind[r];
+      for (int cidx = 0; cidx < nx; ++cidx) {
+        const int s = aslot(a, S.xbus[cidx]);
+        if (s >= 0) Gx[(size_t)r * nx + cidx] = jv(s, ka * 2 + S.xkind[cidx]);
+      }
+      for (int j = 0; j < nu; ++j) {
+        int b, kind;
+        ucol(j, b, kind);
+        if (kind == 1) {
+          const int s = aslot(a, b);
+          if (s >= 0) Gu[(size_t)r * nu + j] = jv(s, ka * 2 + 1);
+        } else if (ka == 0 && a == b) {
+          Gu[(size_t)r * nu + j] = -1.0;
+        }
+      }
+    }
+    for (int r = 0; r < m; ++r) {
+      const int g = S.hrow_bus[r], cp = S.hrow_comp[r];
+      for (int cidx = 0; cidx < nx; ++cidx) {
+        const int s = aslot(g, S.xbus[cidx]);
+        if (s >= 0) Hx[(size_t)r * nx + cidx] = jv(s, cp * 2 + S.xkind[cidx]);
+      }
+      for (int j = 0; j < nu; ++j) {
+        int b, kind;
+        ucol(j, b, kind);
+        if (kind == 1) {
+          const int s = aslot(g, b);
+          if (s >= 0) Hu[(size_t)r * nu + j] = jv(s, cp * 2 + 1);
+        }
+      }
+    }
+    return IPM_OK;
+  }
+  if (which == IPM_Q_HESS) {
+    if (!c->have_cond) return fail(c, IPM_ERR_STATE, "no condensed system");
+    const long long tot = (long long)nx * nx + (long long)nx * nu + (long long)nu * nu;
+    if (!need(tot)) return IPM_ERR_ARG;
+    std::vector<double> K((size_t)4 * S.nnzKB * N);
+    CK(cudaMemcpy(K.data(), c->dw.K, K.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    auto kv = [&](int slot, int e) { return K[((size_t)slot * 4 + e) * N + scen]; };
+    std::memset(out, 0, tot * sizeof(double));
+    double *Kxx = out, *Kxu = Kxx + (size_t)nx * nx, *Kuu = Kxu + (size_t)nx * nu;
+    for (int r = 0; r < nx; ++r) {
+      const int a = S.xbus[r], ka = S.xkind[r];
+      for (int cidx = 0; cidx < nx; ++cidx) {
+        const int s = kbslot(a, S.xbus[cidx]);
+        if (s >= 0) Kxx[(size_t)r * nx + cidx] = kv(s, ka * 2 + S.xkind[cidx]);
+      }
+      for (int j = 0; j < nu; ++j) {
+        int b, kind;
+        ucol(j, b, kind);
+        if (kind == 1) {
+          const int s = kbslot(a, b);
+          if (s >= 0) Kxu[(size_t)r * nu + j] = kv(s, ka * 2 + 1);
+        }
+      }
+    }
+    for (int i = 0; i < nu; ++i) {
+      int a, ka;
+      ucol(i, a, ka);
+      for (int j = 0; j < nu; ++j) {
+        int b, kb;
+        ucol(j, b, kb);
+        if (ka == 1 && kb == 1) {
+          const int s = kbslot(a, b);
+          if (s >= 0) Kuu[(size_t)i * nu + j] = kv(s, 3);
+        } else if (ka == 2 && kb == 2 && i == j) {
+          Kuu[(size_t)i * nu + j] = 2.0 * S.c2[j - S.ng + 1] / N;
+        }
+      }
+    }
+    return IPM_OK;
+  }
+  return IPM_ERR_ARG;
+}
+
+ipm_status ipm_set_profiling(ipm_ctx *c, int on) {
+  if (!c) return IPM_ERR_ARG;
+  if (on && !c->ev[0])
+    for (auto &e : c->ev) CK(cudaEventCreate(&e));
+  if (on == 2 || !on)
+    for (int p = 0; p < IPM_N_PHASES; ++p) {
+      c->t_ms[p] = 0;
+      c->t_cnt[p] = 0;
+      c->ev_pending[p] = false;
+    }
+  c->prof = on != 0;
+  return IPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Internal structures of the reduced-space IPM library (host side).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/ipm.h"
+
+struct HostNet {
+  int n = 0, L = 0, ng = 0;
+  std::vector<int> fr, to, gen;
+  std::vector<double> r, x, b, pmax, qmax, c2, c1, vmin, vmax;
+};
+
+// Symbolic structures built once per network (S1).  Index conventions:
+//  * bus variables: theta_i (kind 0) and v_i (kind 1);
+//  * x index: (theta_1..theta_{n-1}, v at non-generator buses); a g row has
+//    the same index as the x variable it pivots on (P_i <-> theta_i,
+//    Q_i <-> v_i);
+//  * u index: v at generator k (k = 0..ng-1), then Pg_k (k = 1..ng-1) at
+//    ng + k - 1;
+//  * position: place of an x variable in the static LU elimination order;
+//  * A: bus adjacency (with diagonal); a Jacobian value is stored per A slot
+//    as 4 entries e = comp*2 + kind (comp 0 = P, 1 = Q), scenario fastest;
+//  * KB: bus-level pattern of the condensed matrix K (A plus the couplings
+//    through every h row), 4 entries per block (row kind*2 + col kind).
+struct Sym {
+  int n = 0, L = 0, ng = 0, N = 0, nx = 0, nu = 0, m = 0;
+  std::vector<int> xth, xv, uv, gen_of_bus;  // per bus, -1 if none
+  std::vector<int> xbus, xkind;              // per x index
+  std::vector<int> lfr, lto;
+  std::vector<double> lg, lb, lbh;           // series g, series b, half charging
+  int nnzA = 0;
+  std::vector<int> a_ptr, a_col, a_diag;
+  std::vector<int> inc_ptr, inc_line, inc_other, inc_aslot;
+  int nnzKB = 0;
+  std::vector<int> kb_ptr, kb_col, kb_row, kb_aslot;
+  std::vector<int> kbi_ptr, kbi_r, kbi_ja, kbi_jb;
+  std::vector<int> hrow_bus, hrow_comp;      // per h row
+  std::vector<int> ht_ptr, ht_r, ht_aslot;   // per bus: h rows touching it
+  // static-pivot LU of G_x (positions)
+  std::vector<int> perm, iperm;
+  int nnzLU = 0;
+  std::vector<int> lu_colptr, lu_row, lu_diag, lu_init;
+  int nlev = 0, nlev_b = 0;
+  std::vector<int> f_lev_ptr, f_piv_ptr, f_piv, f_tgt, f_op_ptr, f_op_l, f_op_u, f_op_k;
+  std::vector<int> lsc_slot, lsc_k;
+  std::vector<int> fw_lev_ptr, fw_rows, fr_ptr, fr_col, fr_lslot, fr_uslot;
+  std::vector<int> bw_lev_ptr, bw_rows, br_ptr, br_col, br_uslot, br_lslot;
+  // sparse operators by position (x rows) or u rows
+  std::vector<int> gu_ptr, gu_col, gu_src;
+  std::vector<int> gut_ptr, gut_col, gut_src;
+  std::vector<int> kx_ptr, kx_col, kx_src;
+  std::vector<int> ku_ptr, ku_col, ku_src;
+  // bounds (+-inf allowed)
+  std::vector<double> xl, xu, ul, uu, sl, su;
+  std::vector<double> c2, c1, pmax, qmax;
+  long long n_ops = 0;
+};
+
+// Builds the symbolic structures.  Returns false with a message on invalid
+// networks (bad indices, duplicate or self lines, gen_bus[0] != 0, ...).
+bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err);

@@ -1,0 +1,67 @@
+// Host-side launch wrappers of the CUDA kernels (internal).
+#pragma once
+#include "dev.cuh"
+
+// kernels_eval.cu
+void launch_functions(const DevSym &S, const double *x, const double *u, double *P, double *Q, double *g,
+                      double *h, double *fs, cudaStream_t st);
+void launch_derivatives(const DevSym &S, DevWork &D, cudaStream_t st);
+void launch_sigmas(const DevSym &S, DevWork &D, cudaStream_t st);
+void launch_condense(const DevSym &S, DevWork &D, cudaStream_t st);
+void launch_rhs(const DevSym &S, DevWork &D, double mu, double *gLu, double *HTt_u, cudaStream_t st);
+void launch_ugrad(const DevSym &S, DevWork &D, double *gLu, cudaStream_t st);
+
+// kernels_lu.cu
+void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
+                      cudaStream_t st);
+void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
+                     double *Z, double *Y, double *Yu, cudaStream_t st);
+void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
+                   cudaStream_t st);
+
+// kernels_dense.cu
+void launch_gemm_tn64(int nx, int nu, int N, int spg, int ngroups, const double *A, const double *B,
+                      const int2 *tiles, int ntiles, double *partial, cudaStream_t st);
+void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const double *partial,
+                          const int *tile_of, const double *Yu, const double *diag, double *Khat,
+                          cudaStream_t st);
+void launch_shift(int nu, const double *Khat, const double *M, double delta, double *F, cudaStream_t st);
+void launch_cholesky(int n, double *A, int *flags, cudaStream_t st);
+void launch_chol_solve(int n, const double *L, double *b, cudaStream_t st);
+
+// kernels_step.cu
+void launch_errors(const DevSym &S, DevWork &D, const double *gLu, double *partial, double *out,
+                   cudaStream_t st);
+void launch_merit(const DevSym &S, const double *x, const double *u, const double *s, const double *g,
+                  const double *h, const double *fs, double *partial, double *out, cudaStream_t st);
+void launch_dir(const DevSym &S, DevWork &D, const double *px, const double *pu, const double *ps,
+                const double *kpx, const double *kpu, const double *Hp, double mu, double delta,
+                double *partial, double *out, cudaStream_t st);
+void launch_ftb(const DevSym &S, DevWork &D, const double *px, const double *pu, const double *ps,
+                const double *const *dz, double tau, double *partial, double *out, cudaStream_t st);
+void launch_gather_pos(int N, int nx, const int *iperm, const double *src, double *dst, double scale,
+                       cudaStream_t st);
+void launch_scatter_pos(int N, int nx, const int *iperm, const double *src, double *dst, double scale,
+                        cudaStream_t st);
+void launch_gu_apply(const DevSym &S, const double *J, const double *pu, double *v, cudaStream_t st);
+void launch_kapply(const DevSym &S, const double *K, const double *px_pos, const double *pu, double *kpx,
+                   double *kpu, cudaStream_t st);
+void launch_lincomb(long long n, double *out, double a, const double *x, double b, const double *y,
+                    double c, const double *z, cudaStream_t st);
+void launch_rhs_reduced(const DevSym &S, const double *J, const double *K, const double *rh2,
+                        const double *a, const double *b, double *rhs, cudaStream_t st);
+void launch_gut_sum(const DevSym &S, const double *J, const double *a, double scale, double *out,
+                    cudaStream_t st);
+void launch_pz_ps(const DevSym &S, DevWork &D, const double *px, const double *pu, double *Hp, double *pz,
+                  double *ps, cudaStream_t st);
+void launch_bound_steps(long long n, int period, const double *w, const double *dw, const double *l,
+                        const double *b, const double *zl, const double *zu, double mu, double *dzl,
+                        double *dzu, cudaStream_t st);
+void launch_dual_update(long long n, int period, const double *w, const double *l, const double *b,
+                        double *zl, double *zu, const double *dzl, const double *dzu, double az, double mu,
+                        double ks, cudaStream_t st);
+void launch_push(long long n, int period, double *w, const double *l, const double *b, double k1, double k2,
+                 cudaStream_t st);
+void launch_init_primal(const DevSym &S, double *x, double *u, const double *pmax, cudaStream_t st);
+void launch_fill_bound_duals(long long n, int period, const double *l, const double *b, double *zl,
+                             double *zu, cudaStream_t st);

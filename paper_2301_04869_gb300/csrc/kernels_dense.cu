@@ -1,0 +1,223 @@
+// K6 (FP64 path) and K7: the dense reduced Hessian
+//   K_hat = sum_i (Z_i^T Y_i + Y_u,i) + Sigma_u + (first-stage cost curvature)
+// (Prop. 2.3, K_hat = Z^T K Z, summed over scenarios as the global reduction of
+// §3.2 does with MPI_Allreduce), and its dense Cholesky factorization
+// (§4: the Schur complement is factorized with dense LAPACK on the GPU).
+//
+// The scenario sum is part of the contraction: K runs over (scenario, row)
+// pairs.  CTAs split that range into fixed groups of scenarios and write
+// partial tiles; one pass then adds the groups in index order (deterministic).
+// Only upper tiles (i <= j) are computed; the symmetric result is mirrored.
+#include "dev.cuh"
+#include "kernels.h"
+
+extern long long g_ipm_launches;
+
+namespace {
+
+constexpr int TB = 64;   // output tile
+constexpr int TK = 16;   // k chunk
+
+// partial[g][tile t][64*64]: sum over scenarios of group g of A_s^T B_s on tile t
+__global__ void __launch_bounds__(256) k_gemm_tn64(int nx, int nu, int N, int spg,
+                                                   const double *__restrict__ A,
+                                                   const double *__restrict__ B,
+                                                   const int2 *__restrict__ tiles, double *partial) {
+  __shared__ double As[TK][TB];
+  __shared__ double Bs[TK][TB];
+  const int t = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
+  const int i0 = tiles[t].x * TB, j0 = tiles[t].y * TB;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  const int s0 = g * spg, s1 = min(N, s0 + spg);
+  for (int s = s0; s < s1; ++s) {
+    const double *As_g = A + (size_t)s * nx * nu;
+    const double *Bs_g = B + (size_t)s * nx * nu;
+    for (int k0 = 0; k0 < nx; k0 += TK) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + q * 256, kk = e >> 6, cc = e & 63;
+        const int k = k0 + kk;
+        As[kk][cc] = (k < nx && i0 + cc < nu) ? As_g[(size_t)k * nu + i0 + cc] : 0.0;
+        Bs[kk][cc] = (k < nx && j0 + cc < nu) ? Bs_g[(size_t)k * nu + j0 + cc] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < TK; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+      __syncthreads();
+    }
+  }
+  double *P = partial + ((size_t)g * gridDim.x + t) * TB * TB;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) P[(ty * 4 + a) * TB + tx * 4 + b] = acc[a][b];
+}
+
+// K_hat[i][j] = K_hat[j][i] = sum_g partial + sum_s Yu[s][i][j] + diag  (i <= j)
+__global__ void k_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1,
+                                const double *__restrict__ partial, const int *__restrict__ tile_of,
+                                const double *__restrict__ Yu, const double *__restrict__ diag,
+                                double *Khat) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nu * nu) return;
+  const int i = (int)(t / nu), j = (int)(t % nu);
+  if (i > j) return;
+  const int ti = i / TB, tj = j / TB;
+  const int tt = tile_of[ti * nt1 + tj];
+  double v = 0.0;
+  for (int g = 0; g < ngroups; ++g)
+    v += partial[((size_t)g * ntiles + tt) * TB * TB + (i - ti * TB) * TB + (j - tj * TB)];
+  if (Yu)
+    for (int s = 0; s < N; ++s) v += Yu[(size_t)s * nu * nu + (size_t)i * nu + j];
+  if (diag && i == j) v += diag[i];
+  Khat[(size_t)i * nu + j] = v;
+  Khat[(size_t)j * nu + i] = v;
+}
+
+__global__ void k_shift(int nu, const double *Khat, const double *M, double delta, double *F) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nu * nu) return;
+  const int i = (int)(t / nu), j = (int)(t % nu);
+  double v = Khat[t];
+  if (delta != 0.0) v += delta * (M[t] + (i == j ? 1.0 : 0.0));
+  F[t] = v;
+}
+
+constexpr int CB = 32;  // Cholesky block
+
+// factor the CB x CB diagonal block at (k0, k0) in place (lower), unblocked
+__global__ void k_potrf_diag(int n, int k0, double *A, int *flags) {
+  __shared__ double a[CB][CB + 1];
+  const int nb = min(CB, n - k0), tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      const double d = a[k][k];
+      if (!(d > 0.0) || !isfinite(d)) { flags[FLAG_NOT_PD] = 1; a[k][k] = 1.0; }
+      else a[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) a[i][k] /= a[k][k];
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+      const int i = e / nb, j = e % nb;
+      if (i > k && j > k && j <= i) a[i][j] -= a[i][k] * a[j][k];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? a[i][j] : 0.0;
+  }
+}
+
+// rows below the diagonal block: L_ik = A_ik L_kk^{-T}
+__global__ void k_trsm_panel(int n, int k0, double *A) {
+  __shared__ double Lk[CB][CB + 1];
+  const int nb = min(CB, n - k0), tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += blockDim.x) Lk[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
+  __syncthreads();
+  const int i = k0 + nb + blockIdx.x * blockDim.x + tid;
+  if (i >= n) return;
+  double x[CB];
+  for (int j = 0; j < nb; ++j) {
+    double v = A[(size_t)i * n + k0 + j];
+    for (int t = 0; t < j; ++t) v -= x[t] * Lk[j][t];
+    x[j] = v / Lk[j][j];
+  }
+  for (int j = 0; j < nb; ++j) A[(size_t)i * n + k0 + j] = x[j];
+}
+
+// trailing update of the lower part: A_ij -= sum_t L_it L_jt (tiles CB x CB)
+__global__ void k_syrk_trail(int n, int k0, double *A) {
+  const int nb = min(CB, n - k0);
+  const int r0 = k0 + nb;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  __shared__ double Li[CB][CB + 1], Lj[CB][CB + 1];
+  const int tid = threadIdx.x;
+  const int i0 = r0 + bi * CB, j0 = r0 + bj * CB;
+  for (int e = tid; e < CB * nb; e += blockDim.x) {
+    const int rr = e / nb, t = e % nb;
+    Li[rr][t] = (i0 + rr < n) ? A[(size_t)(i0 + rr) * n + k0 + t] : 0.0;
+    Lj[rr][t] = (j0 + rr < n) ? A[(size_t)(j0 + rr) * n + k0 + t] : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < CB * CB; e += blockDim.x) {
+    const int ii = e / CB, jj = e % CB, i = i0 + ii, j = j0 + jj;
+    if (i >= n || j >= n || j > i) continue;
+    double v = 0.0;
+    for (int t = 0; t < nb; ++t) v += Li[ii][t] * Lj[jj][t];
+    A[(size_t)i * n + j] -= v;
+  }
+}
+
+// solve L L^T x = b in place (one CTA)
+__global__ void k_chol_solve(int n, const double *L, double *b) {
+  const int tid = threadIdx.x;
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    const double xk = b[k] / L[(size_t)k * n + k];
+    __syncthreads();
+    if (tid == 0) b[k] = xk;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) b[i] -= L[(size_t)i * n + k] * xk;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    __syncthreads();
+    const double xk = b[k] / L[(size_t)k * n + k];
+    __syncthreads();
+    if (tid == 0) b[k] = xk;
+    for (int i = tid; i < k; i += blockDim.x) b[i] -= L[(size_t)k * n + i] * xk;
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+void launch_gemm_tn64(int nx, int nu, int N, int spg, int ngroups, const double *A, const double *B,
+                      const int2 *tiles, int ntiles, double *partial, cudaStream_t st) {
+  dim3 grid(ntiles, ngroups);
+  k_gemm_tn64<<<grid, 256, 0, st>>>(nx, nu, N, spg, A, B, tiles, partial); ++g_ipm_launches;
+}
+void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const double *partial,
+                          const int *tile_of, const double *Yu, const double *diag, double *Khat,
+                          cudaStream_t st) {
+  long long tot = (long long)nu * nu;
+  k_khat_assemble<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, N, ngroups, ntiles, nt1, partial,
+                                                             tile_of, Yu, diag, Khat); ++g_ipm_launches;
+}
+void launch_shift(int nu, const double *Khat, const double *M, double delta, double *F, cudaStream_t st) {
+  long long tot = (long long)nu * nu;
+  k_shift<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, Khat, M, delta, F); ++g_ipm_launches;
+}
+void launch_cholesky(int n, double *A, int *flags, cudaStream_t st) {
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    k_potrf_diag<<<1, 256, 0, st>>>(n, k0, A, flags); ++g_ipm_launches;
+    const int nb = n - k0 < CB ? n - k0 : CB;
+    const int rest = n - k0 - nb;
+    if (rest > 0) {
+      k_trsm_panel<<<(rest + 127) / 128, 128, 0, st>>>(n, k0, A); ++g_ipm_launches;
+      const int nt = (rest + CB - 1) / CB;
+      k_syrk_trail<<<dim3(nt, nt), 256, 0, st>>>(n, k0, A); ++g_ipm_launches;
+    }
+  }
+}
+void launch_chol_solve(int n, const double *L, double *b, cudaStream_t st) {
+  k_chol_solve<<<1, 1024, 0, st>>>(n, L, b); ++g_ipm_launches;
+}

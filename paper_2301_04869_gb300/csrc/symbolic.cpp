@@ -1,0 +1,474 @@
+// Symbolic setup (S1): index maps, sparsity patterns, the fill-reducing
+// ordering and static-pivot LU schedule of G_x shared by all scenarios.
+//
+// The paper factorizes G_x^{1:M} with a sparse LU that can run in batch
+// because every scenario shares one sparsity pattern (§3.2, "Assembling the
+// sparse matrices": P G_x Q = L U, G_x^{-1} b = Q U^{-1} L^{-1} P b).  Here
+// P = Q^T is one symmetric permutation chosen once by minimum degree on the
+// bus graph, with pivots on the diagonal (dP_i/dtheta_i, dQ_i/dv_i); the
+// numeric factorization then replays a fixed, level-scheduled list of
+// operations for every scenario.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <limits>
+#include <map>
+#include <set>
+#include <unordered_map>
+
+#include "ipm_internal.h"
+
+namespace {
+
+inline int64_t key2(int a, int b) { return (int64_t)a * 2147483647LL + b; }
+
+// Minimum-degree elimination on an undirected graph (explicit elimination
+// graph; ties broken by the smaller vertex index).  Returns the order and,
+// for every vertex, its uneliminated neighbours at elimination (the
+// structure of its L column).  Once the remaining graph is complete, the
+// rest is appended in index order.
+void min_degree(int nv, std::vector<std::vector<int>> adj, std::vector<int> &order,
+                std::vector<std::vector<int>> &lpat) {
+  order.clear();
+  lpat.assign(nv, {});
+  std::vector<char> done(nv, 0);
+  std::set<std::pair<int, int>> pq;
+  for (int v = 0; v < nv; ++v) {
+    std::sort(adj[v].begin(), adj[v].end());
+    adj[v].erase(std::unique(adj[v].begin(), adj[v].end()), adj[v].end());
+    pq.insert({(int)adj[v].size(), v});
+  }
+  int remaining = nv;
+  std::vector<int> tmp;
+  while (remaining > 0) {
+    auto it = pq.begin();
+    int d = it->first, p = it->second;
+    if (d == remaining - 1) {
+      // remaining graph is a clique
+      std::vector<int> rest;
+      for (auto &e : pq) rest.push_back(e.second);
+      std::sort(rest.begin(), rest.end());
+      for (size_t i = 0; i < rest.size(); ++i) {
+        order.push_back(rest[i]);
+        lpat[rest[i]].assign(rest.begin() + i + 1, rest.end());
+        done[rest[i]] = 1;
+      }
+      break;
+    }
+    pq.erase(it);
+    done[p] = 1;
+    order.push_back(p);
+    const std::vector<int> nb = adj[p];
+    lpat[p] = nb;
+    for (int q : nb) {
+      pq.erase({(int)adj[q].size(), q});
+      tmp.clear();
+      std::set_union(adj[q].begin(), adj[q].end(), nb.begin(), nb.end(), std::back_inserter(tmp));
+      std::vector<int> nq;
+      nq.reserve(tmp.size());
+      for (int w : tmp)
+        if (w != q && w != p) nq.push_back(w);
+      adj[q].swap(nq);
+      pq.insert({(int)adj[q].size(), q});
+    }
+    adj[p].clear();
+    --remaining;
+  }
+}
+
+}  // namespace
+
+bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
+  const int n = net.n, L = net.L, ng = net.ng;
+  if (n < 2 || L < 1 || ng < 1 || N < 1) { err = "bad sizes"; return false; }
+  if ((int)net.fr.size() != L || (int)net.to.size() != L || (int)net.gen.size() != ng) {
+    err = "bad array sizes"; return false;
+  }
+  if (net.gen[0] != 0) { err = "gen_bus[0] must be 0 (slack)"; return false; }
+  S.n = n; S.L = L; S.ng = ng; S.N = N;
+  S.gen_of_bus.assign(n, -1);
+  for (int k = 0; k < ng; ++k) {
+    int g = net.gen[k];
+    if (g < 0 || g >= n) { err = "gen_bus out of range"; return false; }
+    if (S.gen_of_bus[g] >= 0) { err = "two generators on one bus"; return false; }
+    S.gen_of_bus[g] = k;
+  }
+  for (int l = 0; l < L; ++l) {
+    int a = net.fr[l], b = net.to[l];
+    if (a < 0 || a >= n || b < 0 || b >= n || a == b) { err = "bad line endpoints"; return false; }
+    double z2 = net.r[l] * net.r[l] + net.x[l] * net.x[l];
+    if (!(z2 > 0) || !std::isfinite(z2) || !std::isfinite(net.b[l])) { err = "bad line impedance"; return false; }
+  }
+  // ---- variable maps ----
+  S.xth.assign(n, -1); S.xv.assign(n, -1); S.uv.assign(n, -1);
+  int nx = 0;
+  for (int i = 1; i < n; ++i) S.xth[i] = nx++;
+  for (int i = 0; i < n; ++i)
+    if (S.gen_of_bus[i] < 0) S.xv[i] = nx++;
+  S.nx = nx;
+  S.nu = 2 * ng - 1;
+  S.m = ng + 1;
+  for (int k = 0; k < ng; ++k) S.uv[net.gen[k]] = k;
+  S.xbus.assign(nx, -1); S.xkind.assign(nx, -1);
+  for (int i = 0; i < n; ++i) {
+    if (S.xth[i] >= 0) { S.xbus[S.xth[i]] = i; S.xkind[S.xth[i]] = 0; }
+    if (S.xv[i] >= 0) { S.xbus[S.xv[i]] = i; S.xkind[S.xv[i]] = 1; }
+  }
+  // ---- line parameters (pi model) ----
+  S.lfr = net.fr; S.lto = net.to;
+  S.lg.resize(L); S.lb.resize(L); S.lbh.resize(L);
+  for (int l = 0; l < L; ++l) {
+    double z2 = net.r[l] * net.r[l] + net.x[l] * net.x[l];
+    S.lg[l] = net.r[l] / z2;
+    S.lb[l] = -net.x[l] / z2;
+    S.lbh[l] = 0.5 * net.b[l];
+  }
+  // ---- adjacency A (with diagonal) ----
+  std::vector<std::vector<int>> nbr(n);
+  {
+    std::set<int64_t> seen;
+    for (int l = 0; l < L; ++l) {
+      int a = std::min(net.fr[l], net.to[l]), b = std::max(net.fr[l], net.to[l]);
+      if (!seen.insert(key2(a, b)).second) { err = "duplicate (parallel) line"; return false; }
+      nbr[a].push_back(b);
+      nbr[b].push_back(a);
+    }
+  }
+  S.a_ptr.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    std::vector<int> row = nbr[i];
+    row.push_back(i);
+    std::sort(row.begin(), row.end());
+    S.a_ptr[i + 1] = S.a_ptr[i] + (int)row.size();
+    for (int c : row) S.a_col.push_back(c);
+  }
+  S.nnzA = S.a_ptr[n];
+  auto aslot = [&](int i, int k) -> int {
+    auto b = S.a_col.begin() + S.a_ptr[i], e = S.a_col.begin() + S.a_ptr[i + 1];
+    auto it = std::lower_bound(b, e, k);
+    if (it == e || *it != k) return -1;
+    return (int)(it - S.a_col.begin());
+  };
+  S.a_diag.resize(n);
+  for (int i = 0; i < n; ++i) S.a_diag[i] = aslot(i, i);
+  // incidence lists
+  S.inc_ptr.assign(n + 1, 0);
+  {
+    std::vector<std::vector<std::pair<int, int>>> inc(n);
+    for (int l = 0; l < L; ++l) {
+      inc[net.fr[l]].push_back({l, net.to[l]});
+      inc[net.to[l]].push_back({l, net.fr[l]});
+    }
+    for (int i = 0; i < n; ++i) {
+      S.inc_ptr[i + 1] = S.inc_ptr[i] + (int)inc[i].size();
+      for (auto &p : inc[i]) {
+        S.inc_line.push_back(p.first);
+        S.inc_other.push_back(p.second);
+        S.inc_aslot.push_back(aslot(i, p.second));
+      }
+    }
+  }
+  // ---- h rows: Qg of every generator, then Pg of the slack ----
+  S.hrow_bus.resize(S.m); S.hrow_comp.resize(S.m);
+  for (int k = 0; k < ng; ++k) { S.hrow_bus[k] = net.gen[k]; S.hrow_comp[k] = 1; }
+  S.hrow_bus[ng] = 0; S.hrow_comp[ng] = 0;
+  // nbhd(g) = {g} u nbr(g), i.e. A row g
+  // ---- KB pattern ----
+  std::vector<std::map<int, std::vector<int>>> kb(n);  // row bus -> col bus -> h rows
+  for (int i = 0; i < n; ++i)
+    for (int p = S.a_ptr[i]; p < S.a_ptr[i + 1]; ++p) kb[i][S.a_col[p]];
+  for (int r = 0; r < S.m; ++r) {
+    int g = S.hrow_bus[r];
+    for (int p = S.a_ptr[g]; p < S.a_ptr[g + 1]; ++p)
+      for (int q = S.a_ptr[g]; q < S.a_ptr[g + 1]; ++q) kb[S.a_col[p]][S.a_col[q]].push_back(r);
+  }
+  S.kb_ptr.assign(n + 1, 0);
+  S.kbi_ptr.push_back(0);
+  for (int i = 0; i < n; ++i) {
+    for (auto &kv : kb[i]) {
+      int j = kv.first;
+      S.kb_col.push_back(j);
+      S.kb_row.push_back(i);
+      S.kb_aslot.push_back(aslot(i, j));
+      for (int r : kv.second) {
+        int g = S.hrow_bus[r];
+        S.kbi_r.push_back(r);
+        S.kbi_ja.push_back(aslot(g, i));
+        S.kbi_jb.push_back(aslot(g, j));
+      }
+      S.kbi_ptr.push_back((int)S.kbi_r.size());
+    }
+    S.kb_ptr[i + 1] = (int)S.kb_col.size();
+  }
+  S.nnzKB = (int)S.kb_col.size();
+  auto kbslot = [&](int i, int k) -> int {
+    auto b = S.kb_col.begin() + S.kb_ptr[i], e = S.kb_col.begin() + S.kb_ptr[i + 1];
+    auto it = std::lower_bound(b, e, k);
+    if (it == e || *it != k) return -1;
+    return (int)(it - S.kb_col.begin());
+  };
+  // H^T lists per bus
+  {
+    std::vector<std::vector<std::pair<int, int>>> ht(n);
+    for (int r = 0; r < S.m; ++r) {
+      int g = S.hrow_bus[r];
+      for (int p = S.a_ptr[g]; p < S.a_ptr[g + 1]; ++p) ht[S.a_col[p]].push_back({r, p});
+    }
+    S.ht_ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      S.ht_ptr[i + 1] = S.ht_ptr[i] + (int)ht[i].size();
+      for (auto &p : ht[i]) { S.ht_r.push_back(p.first); S.ht_aslot.push_back(p.second); }
+    }
+  }
+  // ---- ordering: minimum degree on buses 1..n-1 ----
+  std::vector<std::vector<int>> badj(n - 1);
+  for (int i = 1; i < n; ++i)
+    for (int k : nbr[i])
+      if (k != 0) badj[i - 1].push_back(k - 1);
+  std::vector<int> border;
+  std::vector<std::vector<int>> blpat;
+  min_degree(n - 1, badj, border, blpat);
+  // x positions: theta then v of each bus, in elimination order
+  S.perm.assign(nx, -1);
+  S.iperm.assign(nx, -1);
+  std::vector<int> bus_pos0(n, -1);
+  {
+    int pos = 0;
+    for (int bb : border) {
+      int i = bb + 1;
+      bus_pos0[i] = pos;
+      if (S.xth[i] >= 0) { S.perm[S.xth[i]] = pos; S.iperm[pos] = S.xth[i]; ++pos; }
+      if (S.xv[i] >= 0) { S.perm[S.xv[i]] = pos; S.iperm[pos] = S.xv[i]; ++pos; }
+    }
+    if (pos != nx) { err = "internal: ordering size"; return false; }
+  }
+  // x-level pattern of L columns (rows below the pivot), sorted
+  std::vector<std::vector<int>> pat(nx);
+  for (int bb : border) {
+    int i = bb + 1;
+    std::vector<int> rows;
+    for (int q : blpat[bb]) {
+      int qb = q + 1;
+      if (S.xth[qb] >= 0) rows.push_back(S.perm[S.xth[qb]]);
+      if (S.xv[qb] >= 0) rows.push_back(S.perm[S.xv[qb]]);
+    }
+    std::sort(rows.begin(), rows.end());
+    int pth = S.perm[S.xth[i]];
+    if (S.xv[i] >= 0) {
+      int pv = S.perm[S.xv[i]];
+      pat[pth].push_back(pv);
+      for (int r : rows) pat[pth].push_back(r);
+      pat[pv] = rows;
+    } else {
+      pat[pth] = rows;
+    }
+  }
+  // ---- LU storage (CSC by position): U part, diagonal, L part ----
+  std::vector<std::vector<int>> ucols(nx);  // rows r < c with U(r,c) != 0
+  for (int r = 0; r < nx; ++r)
+    for (int c : pat[r]) ucols[c].push_back(r);
+  S.lu_colptr.assign(nx + 1, 0);
+  S.lu_diag.assign(nx, -1);
+  for (int c = 0; c < nx; ++c) {
+    for (int r : ucols[c]) S.lu_row.push_back(r);
+    S.lu_diag[c] = (int)S.lu_row.size();
+    S.lu_row.push_back(c);
+    for (int r : pat[c]) S.lu_row.push_back(r);
+    S.lu_colptr[c + 1] = (int)S.lu_row.size();
+  }
+  S.nnzLU = (int)S.lu_row.size();
+  auto luslot = [&](int r, int c) -> int {
+    auto b = S.lu_row.begin() + S.lu_colptr[c];
+    auto e = S.lu_row.begin() + S.lu_colptr[c + 1];
+    // U part sorted, then diag, then L part sorted; rows < c precede c
+    if (r < c) {
+      auto ee = S.lu_row.begin() + S.lu_diag[c];
+      auto it = std::lower_bound(b, ee, r);
+      if (it == ee || *it != r) return -1;
+      return (int)(it - S.lu_row.begin());
+    }
+    if (r == c) return S.lu_diag[c];
+    auto bb = S.lu_row.begin() + S.lu_diag[c] + 1;
+    auto it = std::lower_bound(bb, e, r);
+    if (it == e || *it != r) return -1;
+    return (int)(it - S.lu_row.begin());
+  };
+  // initial values: G_x entry = J[aslot(bus_r, bus_c)][kind_r*2 + kind_c]
+  S.lu_init.assign(S.nnzLU, -1);
+  for (int c = 0; c < nx; ++c) {
+    int xc = S.iperm[c];
+    int bc = S.xbus[xc], kc = S.xkind[xc];
+    for (int p = S.lu_colptr[c]; p < S.lu_colptr[c + 1]; ++p) {
+      int xr = S.iperm[S.lu_row[p]];
+      int br = S.xbus[xr], kr = S.xkind[xr];
+      int a = aslot(br, bc);
+      if (a >= 0) S.lu_init[p] = a * 4 + kr * 2 + kc;
+    }
+  }
+  // ---- levels: lev(p) = 1 + max over pivots k with p in pat(k) ----
+  std::vector<int> lev(nx, 0), blev(nx, 0);
+  for (int k = 0; k < nx; ++k)
+    for (int p : pat[k]) lev[p] = std::max(lev[p], lev[k] + 1);
+  for (int i = nx - 1; i >= 0; --i)
+    for (int k : pat[i]) blev[i] = std::max(blev[i], blev[k] + 1);
+  int nlev = 0, nlevb = 0;
+  for (int k = 0; k < nx; ++k) { nlev = std::max(nlev, lev[k] + 1); nlevb = std::max(nlevb, blev[k] + 1); }
+  S.nlev = nlev; S.nlev_b = nlevb;
+  // factorization targets per level (gather form, deterministic order)
+  std::vector<std::vector<int>> piv_of_lev(nlev);
+  for (int k = 0; k < nx; ++k) piv_of_lev[lev[k]].push_back(k);
+  S.f_lev_ptr.assign(nlev + 1, 0);
+  S.f_piv_ptr.assign(nlev + 1, 0);
+  for (int l = 0; l < nlev; ++l) {
+    for (int k : piv_of_lev[l]) S.f_piv.push_back(k);
+    S.f_piv_ptr[l + 1] = (int)S.f_piv.size();
+  }
+  S.f_op_ptr.push_back(0);
+  for (int l = 0; l < nlev; ++l) {
+    std::unordered_map<int, std::vector<int>> tg;  // target slot -> pivots
+    std::vector<int> tslots;
+    for (int k : piv_of_lev[l])
+      for (int i : pat[k])
+        for (int j : pat[k]) {
+          int t = luslot(i, j);
+          if (t < 0) { err = "internal: fill pattern not closed"; return false; }
+          auto &v = tg[t];
+          if (v.empty()) tslots.push_back(t);
+          v.push_back(k);
+        }
+    std::sort(tslots.begin(), tslots.end());
+    for (int t : tslots) {
+      int i = S.lu_row[t];
+      // column of slot t
+      int j = (int)(std::upper_bound(S.lu_colptr.begin(), S.lu_colptr.end(), t) - S.lu_colptr.begin()) - 1;
+      S.f_tgt.push_back(t);
+      for (int k : tg[t]) {
+        S.f_op_l.push_back(luslot(i, k));
+        S.f_op_u.push_back(luslot(k, j));
+        S.f_op_k.push_back(k);
+      }
+      S.f_op_ptr.push_back((int)S.f_op_l.size());
+    }
+    S.f_lev_ptr[l + 1] = (int)S.f_tgt.size();
+  }
+  S.n_ops = (long long)S.f_op_l.size();
+  for (int k = 0; k < nx; ++k)
+    for (int i : pat[k]) { S.lsc_slot.push_back(luslot(i, k)); S.lsc_k.push_back(k); }
+  // forward rows (L rows, k < i) with the matching U(k,i) slots
+  {
+    std::vector<std::vector<int>> frow(nx);
+    for (int k = 0; k < nx; ++k)
+      for (int i : pat[k]) frow[i].push_back(k);
+    S.fr_ptr.assign(nx + 1, 0);
+    for (int i = 0; i < nx; ++i) {
+      for (int k : frow[i]) {
+        S.fr_col.push_back(k);
+        S.fr_lslot.push_back(luslot(i, k));
+        S.fr_uslot.push_back(luslot(k, i));
+      }
+      S.fr_ptr[i + 1] = (int)S.fr_col.size();
+    }
+    S.br_ptr.assign(nx + 1, 0);
+    for (int i = 0; i < nx; ++i) {
+      for (int k : pat[i]) {
+        S.br_col.push_back(k);
+        S.br_uslot.push_back(luslot(i, k));
+        S.br_lslot.push_back(luslot(k, i));
+      }
+      S.br_ptr[i + 1] = (int)S.br_col.size();
+    }
+    std::vector<std::vector<int>> fl(nlev), bl(nlevb);
+    for (int i = 0; i < nx; ++i) { fl[lev[i]].push_back(i); bl[blev[i]].push_back(i); }
+    S.fw_lev_ptr.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+      for (int i : fl[l]) S.fw_rows.push_back(i);
+      S.fw_lev_ptr[l + 1] = (int)S.fw_rows.size();
+    }
+    S.bw_lev_ptr.assign(nlevb + 1, 0);
+    for (int l = 0; l < nlevb; ++l) {
+      for (int i : bl[l]) S.bw_rows.push_back(i);
+      S.bw_lev_ptr[l + 1] = (int)S.bw_rows.size();
+    }
+  }
+  // ---- G_u (rows: positions) and its transpose (rows: u) ----
+  const int nu = S.nu;
+  {
+    std::vector<std::vector<std::pair<int, int>>> gut(nu);
+    S.gu_ptr.assign(nx + 1, 0);
+    for (int p = 0; p < nx; ++p) {
+      int xi = S.iperm[p];
+      int a = S.xbus[xi], ka = S.xkind[xi];
+      std::vector<std::pair<int, int>> row;
+      for (int q = S.a_ptr[a]; q < S.a_ptr[a + 1]; ++q) {
+        int b = S.a_col[q];
+        if (S.uv[b] >= 0) row.push_back({S.uv[b], q * 4 + ka * 2 + 1});
+      }
+      if (ka == 0 && S.gen_of_bus[a] >= 1) row.push_back({ng + S.gen_of_bus[a] - 1, -1});
+      std::sort(row.begin(), row.end());
+      for (auto &e : row) {
+        S.gu_col.push_back(e.first);
+        S.gu_src.push_back(e.second);
+        gut[e.first].push_back({p, e.second});
+      }
+      S.gu_ptr[p + 1] = (int)S.gu_col.size();
+    }
+    S.gut_ptr.assign(nu + 1, 0);
+    for (int j = 0; j < nu; ++j) {
+      for (auto &e : gut[j]) { S.gut_col.push_back(e.first); S.gut_src.push_back(e.second); }
+      S.gut_ptr[j + 1] = (int)S.gut_col.size();
+    }
+  }
+  // ---- K_x (rows: positions) and K_u (rows: u) ----
+  auto var_col = [&](int b, int kind) -> int {  // column id: position or nx + u
+    if (kind == 0) return S.xth[b] >= 0 ? S.perm[S.xth[b]] : -1;
+    if (S.xv[b] >= 0) return S.perm[S.xv[b]];
+    return nx + S.uv[b];
+  };
+  S.kx_ptr.assign(nx + 1, 0);
+  for (int p = 0; p < nx; ++p) {
+    int xi = S.iperm[p];
+    int a = S.xbus[xi], ka = S.xkind[xi];
+    std::vector<std::pair<int, int>> row;
+    for (int q = S.kb_ptr[a]; q < S.kb_ptr[a + 1]; ++q) {
+      int b = S.kb_col[q];
+      for (int kb2 = 0; kb2 < 2; ++kb2) {
+        int c = var_col(b, kb2);
+        if (c >= 0) row.push_back({c, q * 4 + ka * 2 + kb2});
+      }
+    }
+    std::sort(row.begin(), row.end());
+    for (auto &e : row) { S.kx_col.push_back(e.first); S.kx_src.push_back(e.second); }
+    S.kx_ptr[p + 1] = (int)S.kx_col.size();
+  }
+  S.ku_ptr.assign(nu + 1, 0);
+  for (int j = 0; j < nu; ++j) {
+    std::vector<std::pair<int, int>> row;
+    if (j < ng) {
+      int a = net.gen[j];
+      for (int q = S.kb_ptr[a]; q < S.kb_ptr[a + 1]; ++q) {
+        int b = S.kb_col[q];
+        for (int kb2 = 0; kb2 < 2; ++kb2) {
+          int c = var_col(b, kb2);
+          if (c >= 0) row.push_back({c, q * 4 + 1 * 2 + kb2});
+        }
+      }
+    }
+    std::sort(row.begin(), row.end());
+    for (auto &e : row) { S.ku_col.push_back(e.first); S.ku_src.push_back(e.second); }
+    S.ku_ptr[j + 1] = (int)S.ku_col.size();
+  }
+  (void)kbslot;
+  // ---- bounds ----
+  const double inf = std::numeric_limits<double>::infinity();
+  S.xl.assign(nx, -inf); S.xu.assign(nx, inf);
+  for (int i = 0; i < n; ++i)
+    if (S.xv[i] >= 0) { S.xl[S.xv[i]] = net.vmin[i]; S.xu[S.xv[i]] = net.vmax[i]; }
+  S.ul.assign(nu, 0.0); S.uu.assign(nu, 0.0);
+  for (int k = 0; k < ng; ++k) { S.ul[k] = net.vmin[net.gen[k]]; S.uu[k] = net.vmax[net.gen[k]]; }
+  for (int k = 1; k < ng; ++k) { S.ul[ng + k - 1] = 0.0; S.uu[ng + k - 1] = net.pmax[k]; }
+  S.sl.assign(S.m, 0.0); S.su.assign(S.m, 0.0);
+  for (int k = 0; k < ng; ++k) { S.sl[k] = -net.qmax[k]; S.su[k] = net.qmax[k]; }
+  S.sl[ng] = -net.pmax[0]; S.su[ng] = -0.0;
+  S.c2 = net.c2; S.c1 = net.c1; S.pmax = net.pmax; S.qmax = net.qmax;
+  return true;
+}
