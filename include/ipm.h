@@ -168,6 +168,34 @@ ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
 enum { IPM_N_PHASES = 9 };
 ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
 
+/* Allocation-free reduced-Hessian sum.  The paper has no counterpart to this
+ * entry point; it exists for callers that cannot call cudaMalloc (code that
+ * runs while another memory pool owns the device, plug-ins that are only
+ * handed device buffers by their host application, processes with a locked
+ * allocator).  It needs no context and allocates nothing.
+ *
+ *   Khat = sum_s Z_s^T Y_s + sum_s Yu_s + diag(d)
+ *
+ * Z, Y: device [n_scen][n_x][n_u] row-major; Yu: device [n_scen][n_u][n_u]
+ * or NULL; d: device [n_u] or NULL; Khat: device [n_u][n_u] output.  Only
+ * the upper triangle of the sum is formed and mirrored (the result is taken
+ * as symmetric, as K_hat is).  All pointers are caller-owned; work is
+ * enqueued on "stream".
+ *
+ * Scratch: the split-K partial tiles live in one 4 MiB file-scope device
+ * array that every GPU loading the library holds until exit; n_u above
+ * IPM_SCHUR_NOALLOC_MAX_NU does not fit and returns IPM_ERR_ARG without
+ * launching anything.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU race and must be serialised by the caller.
+ * Errors: IPM_ERR_ARG (null pointer, non-positive size, n_u too large),
+ * IPM_ERR_CUDA (symbol lookup or launch failed). */
+#define IPM_SCHUR_NOALLOC_MAX_NU 960
+ipm_status ipm_schur_sum_noalloc(const double *Z, const double *Y, const double *Yu,
+                                 const double *d, int n_scen, int n_x, int n_u, double *Khat,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif
