@@ -37,7 +37,7 @@ METRIC = "scenario condensations/s & s per IPM iter (mixed vs FP64 path, 1e-8 KK
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per launch from one ncu capture of the kernel as it stands (profiles/); None once the
 # kernel changes until it is captured again.
-TRAFFIC = {"k_gemm_tn64": 6.14e8}
+TRAFFIC = {"k_gemm_tn64": None}
 UNIT = "scenario condensations/s"
 
 

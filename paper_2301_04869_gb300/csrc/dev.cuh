@@ -5,7 +5,7 @@
 #include <stdint.h>
 
 struct DevSym {
-  int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b;
+  int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b, nlev_f, t0, nd;
   const int *xth, *xv, *uv, *gen_of_bus, *xbus, *xkind;
   const int *lfr, *lto;
   const double *lg, *lb, *lbh;
@@ -13,7 +13,7 @@ struct DevSym {
   const int *kb_ptr, *kb_col, *kb_row, *kb_aslot, *kbi_ptr, *kbi_r, *kbi_ja, *kbi_jb;
   const int *hrow_bus, *hrow_comp, *ht_ptr, *ht_r, *ht_aslot;
   const int *perm, *iperm;
-  const int *lu_diag, *lu_init;
+  const int *lu_diag, *lu_init, *tail_slot;
   const int *f_lev_ptr, *f_piv_ptr, *f_piv, *f_tgt, *f_op_ptr, *f_op_l, *f_op_u, *f_op_k;
   const int *lsc_slot, *lsc_k;
   const int *fw_lev_ptr, *fw_rows, *fr_ptr, *fr_col, *fr_lslot, *fr_uslot;

@@ -42,9 +42,10 @@ struct ipm_ctx {
   double *Z = nullptr, *Y = nullptr, *Yu = nullptr, *partial = nullptr;
   int2 *tiles = nullptr;
   int *tile_of = nullptr;
-  int ntiles = 0, nt1 = 0, ngroups = 0, spg = 0;
+  int ntiles = 0, nt1 = 0, ngroups = 0;
+  long long kchunk = 0;
   double *Khat = nullptr, *M = nullptr, *F = nullptr, *diag1 = nullptr, *rhs_u = nullptr;
-  double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta) and its scratch
+  double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta); scratch [N][max(nx,nu)]
   double *gLu = nullptr, *HTt_u = nullptr;
   double *pg_curv = nullptr, *pmax_d = nullptr;
   double *step = nullptr, *px = nullptr, *pu = nullptr, *ps = nullptr, *py = nullptr, *pz = nullptr;
@@ -131,6 +132,7 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   DevSym &d = c->ds;
   d.n = S.n; d.L = S.L; d.ng = S.ng; d.N = S.N; d.nx = S.nx; d.nu = S.nu; d.m = S.m;
   d.nnzA = S.nnzA; d.nnzKB = S.nnzKB; d.nnzLU = S.nnzLU; d.nlev = S.nlev; d.nlev_b = S.nlev_b;
+  d.nlev_f = S.nlev_f; d.t0 = S.t0; d.nd = S.nd;
   TRY(upload(c, &d.xth, S.xth)); TRY(upload(c, &d.xv, S.xv)); TRY(upload(c, &d.uv, S.uv));
   TRY(upload(c, &d.gen_of_bus, S.gen_of_bus)); TRY(upload(c, &d.xbus, S.xbus)); TRY(upload(c, &d.xkind, S.xkind));
   TRY(upload(c, &d.lfr, S.lfr)); TRY(upload(c, &d.lto, S.lto));
@@ -145,6 +147,7 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   TRY(upload(c, &d.ht_ptr, S.ht_ptr)); TRY(upload(c, &d.ht_r, S.ht_r)); TRY(upload(c, &d.ht_aslot, S.ht_aslot));
   TRY(upload(c, &d.perm, S.perm)); TRY(upload(c, &d.iperm, S.iperm));
   TRY(upload(c, &d.lu_diag, S.lu_diag)); TRY(upload(c, &d.lu_init, S.lu_init));
+  TRY(upload(c, &d.tail_slot, S.tail_slot));
   TRY(upload(c, &d.f_lev_ptr, S.f_lev_ptr)); TRY(upload(c, &d.f_piv_ptr, S.f_piv_ptr)); TRY(upload(c, &d.f_piv, S.f_piv));
   TRY(upload(c, &d.f_tgt, S.f_tgt)); TRY(upload(c, &d.f_op_ptr, S.f_op_ptr)); TRY(upload(c, &d.f_op_l, S.f_op_l));
   TRY(upload(c, &d.f_op_u, S.f_op_u)); TRY(upload(c, &d.f_op_k, S.f_op_k));
@@ -209,9 +212,17 @@ ipm_status alloc_work(ipm_ctx *c) {
       tl.push_back(make_int2(i, j));
     }
   c->ntiles = (int)tl.size();
-  int G = (int)std::min<long long>(N, std::max(1, (3 * 152 + c->ntiles - 1) / c->ntiles));
-  c->spg = (int)((N + G - 1) / G);
-  c->ngroups = (int)((N + c->spg - 1) / c->spg);
+  // split the N*nx contraction rows into equal chunks so that tiles x chunks
+  // fills one wave (3 CTAs of 256 threads per SM, 152 SMs)
+  {
+    const long long krows = N * nx;
+    long long G = std::max(1, (3 * 152) / c->ntiles);
+    G = std::min(G, (krows + 15) / 16);
+    long long kc = (krows + G - 1) / G;
+    kc = (kc + 15) / 16 * 16;
+    c->kchunk = kc;
+    c->ngroups = (int)((krows + kc - 1) / kc);
+  }
   TRY(dalloc(c, &c->tiles, tl.size()));
   CK(cudaMemcpy(c->tiles, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice));
   TRY(dalloc(c, &c->tile_of, tof.size()));
@@ -219,7 +230,7 @@ ipm_status alloc_work(ipm_ctx *c) {
   TRY(dalloc(c, &c->partial, (long long)c->ngroups * c->ntiles * 4096));
   TRY(dalloc(c, &c->Khat, nu * nu)); TRY(dalloc(c, &c->M, nu * nu)); TRY(dalloc(c, &c->F, nu * nu));
   TRY(dalloc(c, &c->diag1, nu)); TRY(dalloc(c, &c->rhs_u, nu));
-  TRY(dalloc(c, &c->rhs_corr, nu)); TRY(dalloc(c, &c->cpos, N * nx));
+  TRY(dalloc(c, &c->rhs_corr, nu)); TRY(dalloc(c, &c->cpos, N * std::max(nx, nu)));
   TRY(dalloc(c, &c->gLu, nu)); TRY(dalloc(c, &c->HTt_u, nu));
   {
     std::vector<double> pgc(nu, 0.0);
@@ -366,21 +377,22 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st);
   ph_end(c, PH_ZSOLVE, st);
   ph_begin(c, PH_GEMM, st);
-  launch_gemm_tn64(S.nx, S.nu, S.N, c->spg, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles, c->partial, st);
+  launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles, c->partial, st);
   // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
   launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
   launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
                        c->Khat, st);
   ph_end(c, PH_GEMM, st);
   ph_begin(c, PH_RRHS, st);
-  // reduced RHS, eq. (11): b = G_x^{-1} r3, a = G_x^{-T}(rhat1 - K_xx b)
+  // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
+  //   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
   launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
   launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
   launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
   launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
   launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
-  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
-  launch_rhs_reduced(S, D.J, D.K, D.rh2, c->apos, c->bpos, c->rhs_u, st);
+  launch_lincomb(S.nu, c->rhs_u, -1.0, D.rh2, 0.0, nullptr, 0.0, nullptr, st);
+  launch_zt_apply(S, c->Z, c->apos, D.K, c->bpos, -1.0, 1.0, c->rhs_u, c->cpos, st);
   ph_end(c, PH_RRHS, st);
   CK(cudaGetLastError());
   TRY(read_flags(c, st));
@@ -397,14 +409,12 @@ ipm_status do_factor(ipm_ctx *c, double delta, int *is_pd, cudaStream_t st) {
   const DevSym &S = c->ds;
   if (delta != 0.0 && !c->M_valid) {
     // M = sum_i Z_i^T Z_i, so that K_hat(K + delta I) = K_hat(K) + delta (M + I)
-    launch_gemm_tn64(S.nx, S.nu, S.N, c->spg, c->ngroups, c->Z, c->Z, c->tiles, c->ntiles, c->partial, st);
+    launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Z, c->tiles, c->ntiles, c->partial, st);
     launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, nullptr, nullptr,
                          c->M, st);
     // eq. (11) contains K_xx: with K_xx + delta I the reduced right-hand side
-    // gains -delta sum_i G_u^T G_x^{-T} b_i (b_i = G_x^{-1} r3_i)
-    CK(cudaMemcpyAsync(c->cpos, c->bpos, (size_t)S.N * S.nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    launch_solve1(S, c->dw.LU, c->dw.rd, c->cpos, 1, st);
-    launch_gut_sum(S, c->dw.J, c->cpos, -1.0, c->rhs_corr, st);
+    // gains -delta sum_i G_u^T G_x^{-T} b_i = delta sum_i Z_i^T b_i
+    launch_zt_apply(S, c->Z, c->bpos, nullptr, nullptr, 1.0, 0.0, c->rhs_corr, c->cpos, st);
     c->M_valid = true;
   }
   ph_begin(c, PH_CHOL, st);
@@ -432,11 +442,9 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st) {
   ph_begin(c, PH_RECOVER, st);
   launch_lincomb(S.nu, c->pu, 1.0, c->rhs_u, delta, delta != 0.0 ? c->rhs_corr : nullptr, 0.0, nullptr, st);
   launch_chol_solve(S.nu, c->F, c->pu, st);
-  // p_x = -G_x^{-1} (r3 + G_u p_u)
-  launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->vpos, 1.0, st);
-  launch_gu_apply(S, D.J, c->pu, c->vpos, st);
-  launch_solve1(S, D.LU, D.rd, c->vpos, 0, st);
-  launch_lincomb(NX, c->vpos, -1.0, c->vpos, 0.0, nullptr, 0.0, nullptr, st);
+  // p_x = -G_x^{-1} (r3 + G_u p_u) = Z p_u - b
+  CK(cudaMemcpyAsync(c->vpos, c->bpos, NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_z_apply(S, c->Z, c->pu, -1.0, c->vpos, st);
   launch_scatter_pos(S.N, S.nx, S.iperm, c->vpos, c->px, 1.0, st);
   // p_y = -G_x^{-T} (rhat1 + (K_xx + delta I) p_x + K_xu p_u)
   launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);

@@ -20,7 +20,7 @@ void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *
                    cudaStream_t st);
 
 // kernels_dense.cu
-void launch_gemm_tn64(int nx, int nu, int N, int spg, int ngroups, const double *A, const double *B,
+void launch_gemm_tn64(long long krows, long long kc, int nu, int ngroups, const double *A, const double *B,
                       const int2 *tiles, int ntiles, double *partial, cudaStream_t st);
 void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const double *partial,
                           const int *tile_of, const double *Yu, const double *diag, double *Khat,
@@ -50,6 +50,9 @@ void launch_lincomb(long long n, double *out, double a, const double *x, double 
                     double c, const double *z, cudaStream_t st);
 void launch_rhs_reduced(const DevSym &S, const double *J, const double *K, const double *rh2,
                         const double *a, const double *b, double *rhs, cudaStream_t st);
+void launch_zt_apply(const DevSym &S, const double *Z, const double *w, const double *K, const double *b,
+                     double alpha, double beta, double *out, double *part, cudaStream_t st);
+void launch_z_apply(const DevSym &S, const double *Z, const double *pu, double a, double *v, cudaStream_t st);
 void launch_gut_sum(const DevSym &S, const double *J, const double *a, double scale, double *out,
                     cudaStream_t st);
 void launch_pz_ps(const DevSym &S, DevWork &D, const double *px, const double *pu, double *Hp, double *pz,

@@ -18,8 +18,10 @@ namespace {
 constexpr int TB = 64;   // output tile
 constexpr int TK = 16;   // k chunk
 
-// partial[g][tile t][64*64]: sum over scenarios of group g of A_s^T B_s on tile t
-__global__ void __launch_bounds__(256) k_gemm_tn64(int nx, int nu, int N, int spg,
+// partial[g][tile t][64*64] = A^T B on tile t over the rows [g*kc, (g+1)*kc) of
+// the (N*nx) x nu matrices A, B (scenario-major storage makes the scenario
+// sum one contraction over the concatenated rows)
+__global__ void __launch_bounds__(256) k_gemm_tn64(long long krows, long long kc, int nu,
                                                    const double *__restrict__ A,
                                                    const double *__restrict__ B,
                                                    const int2 *__restrict__ tiles, double *partial) {
@@ -33,17 +35,15 @@ __global__ void __launch_bounds__(256) k_gemm_tn64(int nx, int nu, int N, int sp
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  const int s0 = g * spg, s1 = min(N, s0 + spg);
-  for (int s = s0; s < s1; ++s) {
-    const double *As_g = A + (size_t)s * nx * nu;
-    const double *Bs_g = B + (size_t)s * nx * nu;
-    for (int k0 = 0; k0 < nx; k0 += TK) {
+  const long long r0 = (long long)g * kc, r1 = min(krows, r0 + kc);
+  {
+    for (long long k0 = r0; k0 < r1; k0 += TK) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int e = tid + q * 256, kk = e >> 6, cc = e & 63;
-        const int k = k0 + kk;
-        As[kk][cc] = (k < nx && i0 + cc < nu) ? As_g[(size_t)k * nu + i0 + cc] : 0.0;
-        Bs[kk][cc] = (k < nx && j0 + cc < nu) ? Bs_g[(size_t)k * nu + j0 + cc] : 0.0;
+        const long long k = k0 + kk;
+        As[kk][cc] = (k < r1 && i0 + cc < nu) ? A[k * nu + i0 + cc] : 0.0;
+        Bs[kk][cc] = (k < r1 && j0 + cc < nu) ? B[k * nu + j0 + cc] : 0.0;
       }
       __syncthreads();
 #pragma unroll
@@ -190,10 +190,10 @@ __global__ void k_chol_solve(int n, const double *L, double *b) {
 
 }  // namespace
 
-void launch_gemm_tn64(int nx, int nu, int N, int spg, int ngroups, const double *A, const double *B,
+void launch_gemm_tn64(long long krows, long long kc, int nu, int ngroups, const double *A, const double *B,
                       const int2 *tiles, int ntiles, double *partial, cudaStream_t st) {
   dim3 grid(ntiles, ngroups);
-  k_gemm_tn64<<<grid, 256, 0, st>>>(nx, nu, N, spg, A, B, tiles, partial); ++g_ipm_launches;
+  k_gemm_tn64<<<grid, 256, 0, st>>>(krows, kc, nu, A, B, tiles, partial); ++g_ipm_launches;
 }
 void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const double *partial,
                           const int *tile_of, const double *Yu, const double *diag, double *Khat,

@@ -34,9 +34,14 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
   return r;
 }
 
+// Batched LU: the sparse pivots follow the level schedule (gather-form
+// updates), then the dense trailing block [t0, nx) is factorized right-looking
+// in shared memory when it fits (dynamic shared memory of nd*nd doubles),
+// else in place through the slot map.
 __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, double *LU, double *rd,
-                            int *flags, double piv_tol) {
+                            int *flags, double piv_tol, int ns) {
   __shared__ double sh[32];
+  extern __shared__ double T[];
   const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
   double *A = LU + (size_t)sc * S.nnzLU;
   double *r = rd + (size_t)sc * S.nx;
@@ -48,7 +53,7 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
     amax = fmax(amax, fabs(v));
   }
   amax = block_max(amax, sh);
-  for (int l = 0; l < S.nlev; ++l) {
+  for (int l = 0; l < S.nlev_f; ++l) {
     for (int e = S.f_piv_ptr[l] + tid; e < S.f_piv_ptr[l + 1]; e += bd) {
       const int k = S.f_piv[e];
       const double d = A[S.lu_diag[k]];
@@ -66,6 +71,49 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
     __syncthreads();
   }
   for (int e = tid; e < nL; e += bd) A[S.lsc_slot[e]] *= r[S.lsc_k[e]];
+  // dense trailing block: columns [0, k0) in place through the slot map,
+  // then the remaining (nd-k0)^2 block in shared memory (k0 = nd - ns)
+  const int nd = S.nd, t0 = S.t0;
+  if (nd == 0) return;
+  const int *ts = S.tail_slot;
+  const int k0 = nd - ns;
+  __syncthreads();
+  for (int k = 0; k < k0; ++k) {
+    const double d = A[ts[k * nd + k]];
+    if (tid == 0) {
+      if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
+      r[t0 + k] = 1.0 / d;
+    }
+    const double rk = 1.0 / d;
+    const int m = nd - k - 1;
+    for (int e = tid; e < m; e += bd) A[ts[(k + 1 + e) * nd + k]] *= rk;
+    __syncthreads();
+    for (int e = tid; e < m * m; e += bd) {
+      const int a = k + 1 + e / m, b = k + 1 + e % m;
+      A[ts[a * nd + b]] -= A[ts[a * nd + k]] * A[ts[k * nd + b]];
+    }
+    __syncthreads();
+  }
+  if (ns == 0) return;
+  for (int e = tid; e < ns * ns; e += bd) T[e] = A[ts[(k0 + e / ns) * nd + k0 + e % ns]];
+  __syncthreads();
+  for (int k = 0; k < ns; ++k) {
+    const double d = T[k * ns + k];
+    if (tid == 0) {
+      if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
+      r[t0 + k0 + k] = 1.0 / d;
+    }
+    const double rk = 1.0 / d;
+    const int m = ns - k - 1;
+    for (int e = tid; e < m; e += bd) T[(k + 1 + e) * ns + k] *= rk;
+    __syncthreads();
+    for (int e = tid; e < m * m; e += bd) {
+      const int a = k + 1 + e / m, b = k + 1 + e % m;
+      T[a * ns + b] -= T[a * ns + k] * T[k * ns + b];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < ns * ns; e += bd) A[ts[(k0 + e / ns) * nd + k0 + e % ns]] = T[e];
 }
 
 // Z = -U^{-1} L^{-1} (P G_u) for one scenario and one panel of 32 RHS
@@ -133,38 +181,34 @@ __global__ void __launch_bounds__(256) k_zsolve64(DevSym S, const double *__rest
 }
 
 // In-place solve of G_x v = b (trans = 0) or G_x^T v = b (trans = 1) for every
-// scenario; v is [N][nx] in LU position order.
+// scenario; v is [N][nx] in LU position order.  One CTA per scenario walks
+// the level schedule; within a level each warp takes one row and its lanes
+// split the row's entries (the trailing rows of the factor are dense).
 __global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
                          double *v, int trans) {
-  const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const int sc = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double *A = LU + (size_t)sc * S.nnzLU;
   const double *r = rd + (size_t)sc * S.nx;
   double *vs = v + (size_t)sc * S.nx;
+  const int *fsl = trans ? S.fr_uslot : S.fr_lslot;
+  const int *bsl = trans ? S.br_lslot : S.br_uslot;
   for (int l = 0; l < S.nlev; ++l) {
-    for (int e = S.fw_lev_ptr[l] + tid; e < S.fw_lev_ptr[l + 1]; e += bd) {
+    for (int e = S.fw_lev_ptr[l] + warp; e < S.fw_lev_ptr[l + 1]; e += nw) {
       const int row = S.fw_rows[e];
-      double acc = vs[row];
-      if (trans) {
-        for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1]; ++f) acc -= A[S.fr_uslot[f]] * vs[S.fr_col[f]];
-        vs[row] = acc * r[row];
-      } else {
-        for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1]; ++f) acc -= A[S.fr_lslot[f]] * vs[S.fr_col[f]];
-        vs[row] = acc;
-      }
+      double part = 0.0;
+      for (int f = S.fr_ptr[row] + lane; f < S.fr_ptr[row + 1]; f += 32) part += A[fsl[f]] * vs[S.fr_col[f]];
+      part = warp_sum(part);
+      if (lane == 0) vs[row] = trans ? (vs[row] - part) * r[row] : vs[row] - part;
     }
     __syncthreads();
   }
   for (int l = 0; l < S.nlev_b; ++l) {
-    for (int e = S.bw_lev_ptr[l] + tid; e < S.bw_lev_ptr[l + 1]; e += bd) {
+    for (int e = S.bw_lev_ptr[l] + warp; e < S.bw_lev_ptr[l + 1]; e += nw) {
       const int row = S.bw_rows[e];
-      double acc = vs[row];
-      if (trans) {
-        for (int f = S.br_ptr[row]; f < S.br_ptr[row + 1]; ++f) acc -= A[S.br_lslot[f]] * vs[S.br_col[f]];
-        vs[row] = acc;
-      } else {
-        for (int f = S.br_ptr[row]; f < S.br_ptr[row + 1]; ++f) acc -= A[S.br_uslot[f]] * vs[S.br_col[f]];
-        vs[row] = acc * r[row];
-      }
+      double part = 0.0;
+      for (int f = S.br_ptr[row] + lane; f < S.br_ptr[row + 1]; f += 32) part += A[bsl[f]] * vs[S.br_col[f]];
+      part = warp_sum(part);
+      if (lane == 0) vs[row] = trans ? vs[row] - part : (vs[row] - part) * r[row];
     }
     __syncthreads();
   }
@@ -174,7 +218,11 @@ __global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *
 
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
                       cudaStream_t st) {
-  k_lu_factor<<<S.N, 256, 0, st>>>(S, nL, J, LU, rd, flags, 1e-14); ++g_ipm_launches;
+  // trailing sub-block held in shared memory: up to 160 x 160 doubles (200 KB)
+  const int ns = S.nd < 160 ? S.nd : 160;
+  const size_t smem = (size_t)ns * ns * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_lu_factor<<<S.N, 512, smem, st>>>(S, nL, J, LU, rd, flags, 1e-14, ns); ++g_ipm_launches;
 }
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J,
                      const double *K, double *Z, double *Y, double *Yu, cudaStream_t st) {
@@ -183,5 +231,5 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
 }
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st) {
-  k_solve1<<<S.N, 256, 0, st>>>(S, LU, rd, v, trans); ++g_ipm_launches;
+  k_solve1<<<S.N, 512, 0, st>>>(S, LU, rd, v, trans); ++g_ipm_launches;
 }

@@ -314,6 +314,50 @@ __global__ void k_rhs_reduced(DevSym S, const double *J, const double *K, const 
   rhs[j] = acc;
 }
 
+// part[s][j] = (Z_s^T w_s)[j]: thread per (scenario, column), rows swept in
+// order, consecutive threads read consecutive columns (coalesced).
+__global__ void k_zt_part(DevSym S, const double *__restrict__ Z, const double *__restrict__ w,
+                          double *part) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)S.N * S.nu) return;
+  const int sc = (int)(t / S.nu), j = (int)(t - (long long)sc * S.nu);
+  const double *Zs = Z + (size_t)sc * S.nx * S.nu;
+  const double *ws = w + (size_t)sc * S.nx;
+  double acc = 0.0;
+  for (int p = 0; p < S.nx; ++p) acc += Zs[(size_t)p * S.nu + j] * ws[p];
+  part[t] = acc;
+}
+
+// out[j] = beta*out[j] + sum_s (alpha part[s][j] (+ (K_ux b_s)[j] when b != null))
+__global__ void k_zt_sum(DevSym S, const double *part, const double *K, const double *b, double alpha,
+                         double beta, double *out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= S.nu) return;
+  double acc = 0.0;
+  for (int sc = 0; sc < S.N; ++sc) {
+    acc += alpha * part[(size_t)sc * S.nu + j];
+    if (b)
+      for (int e = S.ku_ptr[j]; e < S.ku_ptr[j + 1]; ++e) {
+        const int col = S.ku_col[e];
+        if (col < S.nx) acc += K[(size_t)S.ku_src[e] * S.N + sc] * b[(size_t)sc * S.nx + col];
+      }
+  }
+  out[j] = beta * out[j] + acc;
+}
+
+// v[s][p] = a * v[s][p] + (Z_s pu)[p]   (position rows)
+__global__ void k_z_apply(DevSym S, const double *__restrict__ Z, const double *__restrict__ pu, double a,
+                          double *v) {
+  const int lane = threadIdx.x & 31;
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= (long long)S.N * S.nx) return;
+  const double *Zr = Z + (size_t)row * S.nu;
+  double part = 0.0;
+  for (int j = lane; j < S.nu; j += 32) part += Zr[j] * pu[j];
+  part = warp_sum(part);
+  if (lane == 0) v[row] = a * v[row] + part;
+}
+
 // out[j] = scale * sum_s (G_u^T a_s)[j]   (a in position order)
 __global__ void k_gut_sum(DevSym S, const double *J, const double *a, double scale, double *out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -480,6 +524,14 @@ void launch_lincomb(long long n, double *out, double a, const double *x, double 
 void launch_rhs_reduced(const DevSym &S, const double *J, const double *K, const double *rh2,
                         const double *a, const double *b, double *rhs, cudaStream_t st) {
   k_rhs_reduced<<<nblk(S.nu, 64), 64, 0, st>>>(S, J, K, rh2, a, b, rhs); ++g_ipm_launches;
+}
+void launch_zt_apply(const DevSym &S, const double *Z, const double *w, const double *K, const double *b,
+                     double alpha, double beta, double *out, double *part, cudaStream_t st) {
+  k_zt_part<<<nblk((long long)S.N * S.nu, 128), 128, 0, st>>>(S, Z, w, part); ++g_ipm_launches;
+  k_zt_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, part, K, b, alpha, beta, out); ++g_ipm_launches;
+}
+void launch_z_apply(const DevSym &S, const double *Z, const double *pu, double a, double *v, cudaStream_t st) {
+  k_z_apply<<<nblk((long long)S.N * S.nx * 32, 256), 256, 0, st>>>(S, Z, pu, a, v); ++g_ipm_launches;
 }
 void launch_gut_sum(const DevSym &S, const double *J, const double *a, double scale, double *out,
                     cudaStream_t st) {

@@ -314,17 +314,30 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   int nlev = 0, nlevb = 0;
   for (int k = 0; k < nx; ++k) { nlev = std::max(nlev, lev[k] + 1); nlevb = std::max(nlevb, blev[k] + 1); }
   S.nlev = nlev; S.nlev_b = nlevb;
-  // factorization targets per level (gather form, deterministic order)
-  std::vector<std::vector<int>> piv_of_lev(nlev);
-  for (int k = 0; k < nx; ++k) piv_of_lev[lev[k]].push_back(k);
-  S.f_lev_ptr.assign(nlev + 1, 0);
-  S.f_piv_ptr.assign(nlev + 1, 0);
-  for (int l = 0; l < nlev; ++l) {
+  // dense trailing block: the largest suffix [t0, nx) whose L columns are full
+  int t0 = nx;
+  while (t0 > 0 && (int)pat[t0 - 1].size() == nx - t0) --t0;
+  if (nx - t0 < 2) t0 = nx;  // nothing worth a dense phase
+  S.t0 = t0;
+  S.nd = nx - t0;
+  S.tail_slot.assign((size_t)S.nd * S.nd, -1);
+  for (int a = 0; a < S.nd; ++a)
+    for (int b = 0; b < S.nd; ++b) S.tail_slot[(size_t)a * S.nd + b] = luslot(t0 + a, t0 + b);
+  // factorization levels of the sparse pivots only (the trailing block is
+  // factorized densely afterwards; sparse pivots never depend on it)
+  int nlevf = 0;
+  for (int k = 0; k < t0; ++k) nlevf = std::max(nlevf, lev[k] + 1);
+  S.nlev_f = nlevf;
+  std::vector<std::vector<int>> piv_of_lev(nlevf);
+  for (int k = 0; k < t0; ++k) piv_of_lev[lev[k]].push_back(k);
+  S.f_lev_ptr.assign(nlevf + 1, 0);
+  S.f_piv_ptr.assign(nlevf + 1, 0);
+  for (int l = 0; l < nlevf; ++l) {
     for (int k : piv_of_lev[l]) S.f_piv.push_back(k);
     S.f_piv_ptr[l + 1] = (int)S.f_piv.size();
   }
   S.f_op_ptr.push_back(0);
-  for (int l = 0; l < nlev; ++l) {
+  for (int l = 0; l < nlevf; ++l) {
     std::unordered_map<int, std::vector<int>> tg;  // target slot -> pivots
     std::vector<int> tslots;
     for (int k : piv_of_lev[l])
@@ -352,7 +365,7 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
     S.f_lev_ptr[l + 1] = (int)S.f_tgt.size();
   }
   S.n_ops = (long long)S.f_op_l.size();
-  for (int k = 0; k < nx; ++k)
+  for (int k = 0; k < t0; ++k)
     for (int i : pat[k]) { S.lsc_slot.push_back(luslot(i, k)); S.lsc_k.push_back(k); }
   // forward rows (L rows, k < i) with the matching U(k,i) slots
   {
