@@ -63,4 +63,4 @@ __device__ __forceinline__ double bus_v(const DevSym &S, const double *x, const 
 }
 
 // flags
-enum { FLAG_SINGULAR = 0, FLAG_NOT_PD = 1, FLAG_NONFINITE = 2, FLAG_COUNT = 8 };
+enum { FLAG_SINGULAR = 0, FLAG_NOT_PD = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 3, FLAG_COUNT = 8 };

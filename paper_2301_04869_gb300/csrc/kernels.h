@@ -68,3 +68,16 @@ void launch_push(long long n, int period, double *w, const double *l, const doub
 void launch_init_primal(const DevSym &S, double *x, double *u, const double *pmax, cudaStream_t st);
 void launch_fill_bound_duals(long long n, int period, const double *l, const double *b, double *zl,
                              double *zu, cudaStream_t st);
+
+// kernels_tc.cu (tcgen05 BF16x3 reduced-Hessian product)
+struct TcPlan {
+  int nu = 0, nt1 = 0, ntiles = 0, kb_total = 0, kb_per_group = 0, ngroups = 0;
+  long long kpad = 0;
+  alignas(64) unsigned char maps[6 * 128];  // six CUtensorMap (A planes, B planes)
+};
+void tc_plan(int nu, long long krows, TcPlan &P);
+bool tc_set_operands(TcPlan &P, const void *a_planes, const void *b_planes);
+void launch_split_t(long long krows, int nu, long long kpad, const float *src, void *planes, cudaStream_t st);
+void launch_tc_schur(const TcPlan &P, double *partial, int *flags, cudaStream_t st);
+void launch_tc_assemble(const TcPlan &P, int N, const double *partial, const double *Yu, const double *diag,
+                        double *Khat, cudaStream_t st);
