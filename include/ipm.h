@@ -65,13 +65,19 @@ typedef struct {
 
 enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1 };
 
+enum { IPM_BARRIER_MONOTONE = 0, IPM_BARRIER_ADAPTIVE = 1 };
+
 typedef struct {
   double tol;            /* KKT residual E_0 target (1e-8) */
   int max_iter;          /* 200 */
   int precision;         /* IPM_PREC_FP64 or IPM_PREC_MIXED */
   int max_refine;        /* iterative-refinement sweeps of the KKT solve (mixed) */
   int panel;             /* RHS columns per CTA in the multi-RHS solves (0 = auto) */
-  int reserved[7];
+  int barrier_rule;      /* IPM_BARRIER_ADAPTIVE (default): mu = max(tol/10, sigma * mean
+                            complementarity) at every iteration; IPM_BARRIER_MONOTONE:
+                            mu <- max(tol/10, min(0.2 mu, mu^1.5)) when E_mu <= 10 mu */
+  int reserved[6];
+  double sigma;          /* centring factor of the adaptive rule (0.1) */
 } ipm_options;
 
 /* Sizes of a context.  state_len = 4 N n_x + 4 N m + 3 n_u + 3; the state

@@ -11,7 +11,9 @@ path implements the same rules so that both take the same iterates:
     (push = min(k1 max(1,|l|), k2 (b-l)), k1 = k2 = 1e-2); s = -h pushed the
     same way; y = z = 0; bound duals 1; mu = 0.1; rho = 1.
  1. evaluate f, g, h and first/second derivatives (opf.Model);
- 2. stop if E_0 <= tol; if E_mu <= 10 mu: mu <- max(tol/10, min(0.2 mu, mu^1.5));
+ 2. stop if E_0 <= tol; barrier update, adaptive (default): mu = max(tol/10,
+    sigma * mean complementarity), sigma = 0.1, at every iteration; or
+    monotone: if E_mu <= 10 mu, mu <- max(tol/10, min(0.2 mu, mu^1.5));
  3. condense (Prop. 2.1/2.2), reduce (Prop. 2.3), Cholesky of K_hat; if it
     is not positive definite add delta*I to the (x,u) diagonal of K and retry
     (first delta 1e-4, else max(1e-20, delta_last/3); x100 on the first
@@ -44,7 +46,8 @@ OPTS = dict(tol=1e-8, max_iter=200, mu0=0.1, k1=1e-2, k2=1e-2, tau_min=0.99,
             kappa_eps=10.0, kappa_mu=0.2, theta_mu=1.5, eta=1e-4,
             alpha_min=1e-12, kappa_sigma=1e10, s_max=100.0, rho0=1.0,
             rho_frac=0.1, delta0=1e-4, delta_min=1e-20, delta_max=1e40,
-            kw_minus=1.0 / 3.0, kw_plus=8.0, kw_plus_bar=100.0)
+            kw_minus=1.0 / 3.0, kw_plus=8.0, kw_plus_bar=100.0,
+            barrier_rule="adaptive", sigma=0.1)
 
 
 EPS = float(np.finfo(np.float64).eps)
@@ -230,7 +233,14 @@ def iterate(model, st, D=None, opts=OPTS, log=None):
         return True, info
     mu = st["mu"]
     mu_min = opts["tol"] / 10.0
-    if e_mu(errs, mu) <= opts["kappa_eps"] * mu and mu > mu_min:
+    if opts.get("barrier_rule", "adaptive") == "adaptive":
+        comp = np.concatenate([
+            _compl(st["x"], model.xl, model.xu, st["zl_x"], st["zu_x"]),
+            _compl(st["u"], model.ul, model.uu, st["zl_u"], st["zu_u"]),
+            _compl(st["s"], model.sl, model.su, st["zl_s"], st["zu_s"])])
+        mu = max(mu_min, opts["sigma"] * comp.sum() / comp.size)
+        st["mu"] = mu
+    elif e_mu(errs, mu) <= opts["kappa_eps"] * mu and mu > mu_min:
         mu = max(mu_min, min(opts["kappa_mu"] * mu, mu ** opts["theta_mu"]))
         st["mu"] = mu
     C, Lc, delta = factor_with_inertia_correction(model, st, D, mu, opts)

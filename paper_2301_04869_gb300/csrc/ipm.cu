@@ -64,6 +64,7 @@ struct ipm_ctx {
   bool have_eval = false, have_cond = false, have_fact = false, M_valid = false;
   double info[8] = {0};
   double errs[6] = {0};
+  double mean_compl = 0.0;
   // phase timers
   bool prof = false;
   cudaEvent_t ev[2 * IPM_N_PHASES] = {};
@@ -345,7 +346,8 @@ ipm_status do_eval(ipm_ctx *c, cudaStream_t st) {
 // optimality error pieces -> c->errs (dual, primal, compl max, compl min, s_d, s_c)
 ipm_status do_errors(ipm_ctx *c, cudaStream_t st) {
   launch_errors(c->ds, c->dw, c->gLu, c->red_partial, c->red_out, st);
-  TRY(read_red(c, 6, st));
+  TRY(read_red(c, 7, st));
+  c->mean_compl = c->h_red[6] / std::max(1.0, (double)c->n_bounds);
   const Sym &S = c->S;
   const double nlam = (double)S.N * (S.nx + S.m);
   const double nb = (double)c->n_bounds;
@@ -499,7 +501,10 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
   *converged = 0;
   double mu = c->mu;
   const double mu_min = c->opt.tol / 10.0;
-  if (emu(c->errs, mu) <= KAPPA_EPS * mu && mu > mu_min) {
+  if (c->opt.barrier_rule == IPM_BARRIER_ADAPTIVE) {
+    mu = std::max(mu_min, c->opt.sigma * c->mean_compl);
+    c->mu = mu;
+  } else if (emu(c->errs, mu) <= KAPPA_EPS * mu && mu > mu_min) {
     mu = std::max(mu_min, std::min(KAPPA_MU * mu, std::pow(mu, THETA_MU)));
     c->mu = mu;
   }
@@ -591,6 +596,8 @@ ipm_status ipm_default_options(ipm_options *opt) {
   opt->precision = IPM_PREC_FP64;
   opt->max_refine = 10;
   opt->panel = 0;
+  opt->barrier_rule = IPM_BARRIER_ADAPTIVE;
+  opt->sigma = 0.1;
   return IPM_OK;
 }
 
@@ -610,7 +617,8 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
   ipm_ctx *c = new ipm_ctx();
   if (opt) c->opt = *opt;
   else ipm_default_options(&c->opt);
-  if (c->opt.precision != IPM_PREC_FP64 || !(c->opt.tol > 0) || c->opt.max_iter < 0) {
+  if (c->opt.precision != IPM_PREC_FP64 || !(c->opt.tol > 0) || c->opt.max_iter < 0 ||
+      (c->opt.barrier_rule == IPM_BARRIER_ADAPTIVE && !(c->opt.sigma > 0 && c->opt.sigma < 1))) {
     delete c;
     return IPM_ERR_ARG;
   }

@@ -77,16 +77,16 @@ __device__ __forceinline__ double blog(double w, double l, double b) {
 }
 
 // optimality error pieces: dual max, primal max, compl max, compl min,
-// sum |y|+|z|, sum |bound duals|
+// sum |y|+|z|, sum |bound duals|, sum of complementarity products
 struct ErrF {
-  static constexpr int NV = 6;
+  static constexpr int NV = 7;
   __device__ static int op(int i) { return i == 3 ? OP_MIN : (i >= 4 ? OP_SUM : OP_MAX); }
   DevSym S;
   DevWork D;
   const double *gLu;
   __device__ void compl_of(double w, double l, double b, double zl, double zu, double *acc) const {
-    if (isfinite(l)) { const double c = zl * (w - l); acc[2] = fmax(acc[2], c); acc[3] = fmin(acc[3], c); acc[5] += fabs(zl); }
-    if (isfinite(b)) { const double c = zu * (b - w); acc[2] = fmax(acc[2], c); acc[3] = fmin(acc[3], c); acc[5] += fabs(zu); }
+    if (isfinite(l)) { const double c = zl * (w - l); acc[2] = fmax(acc[2], c); acc[3] = fmin(acc[3], c); acc[5] += fabs(zl); acc[6] += c; }
+    if (isfinite(b)) { const double c = zu * (b - w); acc[2] = fmax(acc[2], c); acc[3] = fmin(acc[3], c); acc[5] += fabs(zu); acc[6] += c; }
   }
   __device__ void operator()(long long t, double *acc) const {
     const long long nX = (long long)S.N * S.nx, nS = (long long)S.N * S.m;

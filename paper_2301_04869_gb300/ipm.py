@@ -43,9 +43,13 @@ class Network(ctypes.Structure):
                 ("c2", _D), ("c1", _D), ("vmin", _D), ("vmax", _D)]
 
 
+BARRIER_MONOTONE, BARRIER_ADAPTIVE = 0, 1
+
+
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("panel", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("max_refine", ctypes.c_int), ("panel", ctypes.c_int), ("barrier_rule", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6), ("sigma", ctypes.c_double)]
 
 
 class Dims(ctypes.Structure):
@@ -109,7 +113,8 @@ def _stream(stream):
 class Solver:
     """One context: a network with N load scenarios on the current GPU."""
 
-    def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=10):
+    def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=10,
+                 barrier_rule=None, sigma=None):
         lib = load()
         self._lib = lib
         self._keep = dict(
@@ -133,6 +138,10 @@ class Solver:
         opt.max_iter = max_iter
         opt.precision = precision
         opt.max_refine = max_refine
+        if barrier_rule is not None:
+            opt.barrier_rule = barrier_rule
+        if sigma is not None:
+            opt.sigma = sigma
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]
