@@ -12,6 +12,17 @@
  * Z^T K Z over scenarios (the Schur complement of Prop. 2.4) and factors it
  * by dense Cholesky.
  *
+ * Precision (ipm_options.precision): IPM_PREC_FP64 runs every step in FP64.
+ * IPM_PREC_MIXED runs the multi-RHS solves in FP32 and the Z^T Y products as
+ * three-term BF16 split products on the tensor cores (FP32 accumulation per
+ * 64-wide block, FP64 across blocks); the LU of G_x, the Cholesky and the
+ * recovery stay FP64, and the reduced step is refined to FP64 accuracy by
+ * conjugate gradients on the exact FP64 reduced operator, preconditioned by
+ * the mixed-precision factor.  When that factor is not positive definite or
+ * the refinement meets non-positive curvature (K_hat ill-conditioned near
+ * the solution), the iteration is condensed again in FP64 and the inertia
+ * decision is taken on the exact K_hat.
+ *
  * Conventions (all entry points):
  *  - Every call returns an ipm_status; nothing aborts or traps.  On error,
  *    ipm_last_error() describes the failure.
@@ -155,8 +166,10 @@ ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
  *        the x order of the state vector), IPM_Q_FGH (scen: f, g[n_x], h[m]),
  *        IPM_Q_JAC (scen: dense G_x, G_u, H_x, H_u row-major, concatenated),
  *        IPM_Q_HESS (scen: dense W_xx, W_xu, W_uu^i), IPM_Q_ERRS (6 doubles:
- *        dual, primal, compl max, compl min, s_d, s_c), IPM_Q_INFO (8 doubles:
- *        alpha, alpha_max, alpha_z, delta, trials, rho, mu_used, refine),
+ *        dual, primal, compl max, compl min, s_d, s_c), IPM_Q_INFO (10 doubles:
+ *        alpha, alpha_max, alpha_z, delta, trials, rho, mu_used, refinement
+ *        iterations, refinement relative residual, 1 if the iteration fell back
+ *        to the FP64 condensation),
  *        IPM_Q_TIMERS (2*IPM_N_PHASES doubles: accumulated device milliseconds
  *        and call counts per phase, see ipm_set_profiling; a further double,
  *        if cap allows, is the total number of kernels the library launched).

@@ -5,7 +5,7 @@
 #include <stdint.h>
 
 struct DevSym {
-  int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b, nlev_f, t0, nd;
+  int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b, nlev_f, t0, nd, nlev_fs, nlev_bs;
   const int *xth, *xv, *uv, *gen_of_bus, *xbus, *xkind;
   const int *lfr, *lto;
   const double *lg, *lb, *lbh;
@@ -18,6 +18,7 @@ struct DevSym {
   const int *lsc_slot, *lsc_k;
   const int *fw_lev_ptr, *fw_rows, *fr_ptr, *fr_col, *fr_lslot, *fr_uslot;
   const int *bw_lev_ptr, *bw_rows, *br_ptr, *br_col, *br_uslot, *br_lslot;
+  const int *fs_lev_ptr, *fs_rows, *bs_lev_ptr, *bs_rows;
   const int *gu_ptr, *gu_col, *gu_src, *gut_ptr, *gut_col, *gut_src;
   const int *kx_ptr, *kx_col, *kx_src, *ku_ptr, *ku_col, *ku_src;
   const double *xl, *xu, *ul, *uu, *sl, *su, *c2, *c1;

@@ -48,6 +48,18 @@ struct ipm_ctx {
   double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta); scratch [N][max(nx,nu)]
   double *gLu = nullptr, *HTt_u = nullptr;
   double *pg_curv = nullptr, *pmax_d = nullptr;
+  // mixed path
+  bool mixed = false;
+  float *Z32 = nullptr, *Y32 = nullptr;
+  void *zpl = nullptr, *ypl = nullptr;  // BF16x3 planes, K-major [3][nu][kpad]
+  double *tcpart = nullptr;
+  TcPlan planZY, planZZ;
+  double *pcg_b = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_Ap = nullptr;
+  int refine_iters = 0;
+  double refine_res = 0.0;
+  bool neg_curv = false;     // CG met p^T A p <= 0
+  bool exact_iter = false;   // this iteration runs the FP64 condensation (mixed fallback)
+  long long n_fallback = 0;  // mixed-path iterations that needed the FP64 condensation
   double *step = nullptr, *px = nullptr, *pu = nullptr, *ps = nullptr, *py = nullptr, *pz = nullptr;
   double *dz[6] = {};
   double *Hp = nullptr, *kpx = nullptr, *kpu = nullptr, *vpos = nullptr, *bpos = nullptr, *apos = nullptr;
@@ -62,7 +74,7 @@ struct ipm_ctx {
   double mu = MU0, rho = RHO0, delta_last = 0.0;
   double delta_fact = 0.0;
   bool have_eval = false, have_cond = false, have_fact = false, M_valid = false;
-  double info[8] = {0};
+  double info[10] = {0};
   double errs[6] = {0};
   double mean_compl = 0.0;
   // phase timers
@@ -133,7 +145,7 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   DevSym &d = c->ds;
   d.n = S.n; d.L = S.L; d.ng = S.ng; d.N = S.N; d.nx = S.nx; d.nu = S.nu; d.m = S.m;
   d.nnzA = S.nnzA; d.nnzKB = S.nnzKB; d.nnzLU = S.nnzLU; d.nlev = S.nlev; d.nlev_b = S.nlev_b;
-  d.nlev_f = S.nlev_f; d.t0 = S.t0; d.nd = S.nd;
+  d.nlev_f = S.nlev_f; d.t0 = S.t0; d.nd = S.nd; d.nlev_fs = S.nlev_fs; d.nlev_bs = S.nlev_bs;
   TRY(upload(c, &d.xth, S.xth)); TRY(upload(c, &d.xv, S.xv)); TRY(upload(c, &d.uv, S.uv));
   TRY(upload(c, &d.gen_of_bus, S.gen_of_bus)); TRY(upload(c, &d.xbus, S.xbus)); TRY(upload(c, &d.xkind, S.xkind));
   TRY(upload(c, &d.lfr, S.lfr)); TRY(upload(c, &d.lto, S.lto));
@@ -149,6 +161,8 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   TRY(upload(c, &d.perm, S.perm)); TRY(upload(c, &d.iperm, S.iperm));
   TRY(upload(c, &d.lu_diag, S.lu_diag)); TRY(upload(c, &d.lu_init, S.lu_init));
   TRY(upload(c, &d.tail_slot, S.tail_slot));
+  TRY(upload(c, &d.fs_lev_ptr, S.fs_lev_ptr)); TRY(upload(c, &d.fs_rows, S.fs_rows));
+  TRY(upload(c, &d.bs_lev_ptr, S.bs_lev_ptr)); TRY(upload(c, &d.bs_rows, S.bs_rows));
   TRY(upload(c, &d.f_lev_ptr, S.f_lev_ptr)); TRY(upload(c, &d.f_piv_ptr, S.f_piv_ptr)); TRY(upload(c, &d.f_piv, S.f_piv));
   TRY(upload(c, &d.f_tgt, S.f_tgt)); TRY(upload(c, &d.f_op_ptr, S.f_op_ptr)); TRY(upload(c, &d.f_op_l, S.f_op_l));
   TRY(upload(c, &d.f_op_u, S.f_op_u)); TRY(upload(c, &d.f_op_k, S.f_op_k));
@@ -202,7 +216,36 @@ ipm_status alloc_work(ipm_ctx *c) {
   TRY(dalloc(c, &D.LU, (long long)S.nnzLU * N)); TRY(dalloc(c, &D.rd, N * nx));
   TRY(dalloc(c, &D.flags, FLAG_COUNT));
   CK(cudaMemset(D.flags, 0, FLAG_COUNT * sizeof(int)));
-  TRY(dalloc(c, &c->Z, N * nx * nu)); TRY(dalloc(c, &c->Y, N * nx * nu)); TRY(dalloc(c, &c->Yu, N * nu * nu));
+  c->mixed = c->opt.precision == IPM_PREC_MIXED;
+  TRY(dalloc(c, &c->Yu, N * nu * nu));
+  if (!c->mixed) {
+    TRY(dalloc(c, &c->Z, N * nx * nu));
+    TRY(dalloc(c, &c->Y, N * nx * nu));
+  } else {
+    // one region holds either the mixed operands (FP32 Z, Y and the BF16x3
+    // planes) or, in an iteration that falls back, the FP64 Z and Y
+    tc_plan((int)nu, N * nx, c->planZY);
+    c->planZZ = c->planZY;
+    const size_t E = (size_t)N * nx * nu;
+    const size_t pl = (size_t)3 * nu * c->planZY.kpad;  // bf16 elements per operand
+    const size_t mixed_bytes = E * 4 * 2 + pl * 2 * 2;
+    const size_t bytes = std::max(mixed_bytes, E * 8 * 2);
+    unsigned char *region = nullptr;
+    TRY(dalloc(c, &region, (bytes + 255) / 256 * 256));
+    c->Z32 = (float *)region;
+    c->Y32 = (float *)(region + E * 4);
+    c->zpl = region + ((E * 8 + 255) / 256) * 256;
+    c->ypl = (unsigned char *)c->zpl + pl * 2;
+    c->Z = (double *)region;
+    c->Y = (double *)(region + E * 8);
+    if ((size_t)((unsigned char *)c->ypl - region) + pl * 2 > (bytes + 255) / 256 * 256)
+      return fail(c, IPM_ERR_ARG, "internal: mixed region layout");
+    if (!tc_set_operands(c->planZY, c->zpl, c->ypl) || !tc_set_operands(c->planZZ, c->zpl, c->zpl))
+      return fail(c, IPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    TRY(dalloc(c, &c->tcpart, (long long)c->planZY.ngroups * c->planZY.ntiles * 128 * 128));
+    TRY(dalloc(c, &c->pcg_b, nu)); TRY(dalloc(c, &c->pcg_r, nu)); TRY(dalloc(c, &c->pcg_z, nu));
+    TRY(dalloc(c, &c->pcg_p, nu)); TRY(dalloc(c, &c->pcg_Ap, nu));
+  }
   // GEMM tiling: upper tiles, scenario groups
   c->nt1 = (int)((nu + 63) / 64);
   std::vector<int2> tl;
@@ -375,52 +418,85 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   ph_begin(c, PH_LU, st);
   launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st);
   ph_end(c, PH_LU, st);
-  ph_begin(c, PH_ZSOLVE, st);
-  launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st);
-  ph_end(c, PH_ZSOLVE, st);
-  ph_begin(c, PH_GEMM, st);
-  launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles, c->partial, st);
   // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
   launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
-  launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
-                       c->Khat, st);
-  ph_end(c, PH_GEMM, st);
-  ph_begin(c, PH_RRHS, st);
-  // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
-  //   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
-  launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
-  launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
-  launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
-  launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
-  launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
-  launch_lincomb(S.nu, c->rhs_u, -1.0, D.rh2, 0.0, nullptr, 0.0, nullptr, st);
-  launch_zt_apply(S, c->Z, c->apos, D.K, c->bpos, -1.0, 1.0, c->rhs_u, c->cpos, st);
+  if (!c->mixed || c->exact_iter) {
+    ph_begin(c, PH_ZSOLVE, st);
+    launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st);
+    ph_end(c, PH_ZSOLVE, st);
+    ph_begin(c, PH_GEMM, st);
+    launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
+                     c->partial, st);
+    launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
+                         c->Khat, st);
+    ph_end(c, PH_GEMM, st);
+    ph_begin(c, PH_RRHS, st);
+    // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
+    //   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
+    launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
+    launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+    launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
+    launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
+    launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
+    launch_lincomb(S.nu, c->rhs_u, -1.0, D.rh2, 0.0, nullptr, 0.0, nullptr, st);
+    launch_zt_apply(S, c->Z, c->apos, D.K, c->bpos, -1.0, 1.0, c->rhs_u, c->cpos, st);
+  } else {
+    // mixed: FP32 solves, BF16x3 planes, tcgen05 product; exact FP64 right-hand side
+    ph_begin(c, PH_ZSOLVE, st);
+    launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st);
+    launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);
+    launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
+    ph_end(c, PH_ZSOLVE, st);
+    ph_begin(c, PH_GEMM, st);
+    launch_tc_schur(c->planZY, c->tcpart, D.flags, st);
+    launch_tc_assemble(c->planZY, S.N, c->tcpart, c->Yu, c->diag1, c->Khat, st);
+    ph_end(c, PH_GEMM, st);
+    ph_begin(c, PH_RRHS, st);
+    // eq. (11) with FP64 solves: b = G_x^{-1} r3, a = G_x^{-T}(rhat1 - K_xx b)
+    launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
+    launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+    launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
+    launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
+    launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
+    launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+    launch_rhs_reduced(S, D.J, D.K, D.rh2, c->apos, c->bpos, c->rhs_u, st);
+  }
   ph_end(c, PH_RRHS, st);
   CK(cudaGetLastError());
   TRY(read_flags(c, st));
   ph_collect(c);
   if (c->h_flags[FLAG_SINGULAR]) return fail(c, IPM_ERR_SINGULAR_GX, "singular pivot in the LU of G_x");
+  if (c->h_flags[FLAG_TIMEOUT]) return fail(c, IPM_ERR_TIMEOUT, "a bounded device wait gave up");
   c->have_cond = true;
   c->have_fact = false;
   c->M_valid = false;
   return IPM_OK;
 }
 
-ipm_status do_factor(ipm_ctx *c, double delta, int *is_pd, cudaStream_t st) {
+ipm_status do_factor(ipm_ctx *c, double delta, int *is_pd, cudaStream_t st, double tau = 0.0) {
   if (!c->have_cond) return fail(c, IPM_ERR_STATE, "factor before condense");
   const DevSym &S = c->ds;
   if (delta != 0.0 && !c->M_valid) {
-    // M = sum_i Z_i^T Z_i, so that K_hat(K + delta I) = K_hat(K) + delta (M + I)
-    launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Z, c->tiles, c->ntiles, c->partial, st);
-    launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, nullptr, nullptr,
-                         c->M, st);
+    // M = sum_i Z_i^T Z_i, so that K_hat(K + delta I) = K_hat(K) + delta (M + I);
     // eq. (11) contains K_xx: with K_xx + delta I the reduced right-hand side
     // gains -delta sum_i G_u^T G_x^{-T} b_i = delta sum_i Z_i^T b_i
-    launch_zt_apply(S, c->Z, c->bpos, nullptr, nullptr, 1.0, 0.0, c->rhs_corr, c->cpos, st);
+    if (!c->mixed || c->exact_iter) {
+      launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Z, c->tiles, c->ntiles,
+                       c->partial, st);
+      launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, nullptr, nullptr,
+                           c->M, st);
+      launch_zt_apply(S, c->Z, c->bpos, nullptr, nullptr, 1.0, 0.0, c->rhs_corr, c->cpos, st);
+    } else {
+      launch_tc_schur(c->planZZ, c->tcpart, c->dw.flags, st);
+      launch_tc_assemble(c->planZZ, S.N, c->tcpart, nullptr, nullptr, c->M, st);
+      CK(cudaMemcpyAsync(c->cpos, c->bpos, (size_t)S.N * S.nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      launch_solve1(S, c->dw.LU, c->dw.rd, c->cpos, 1, st);
+      launch_gut_sum(S, c->dw.J, c->cpos, -1.0, c->rhs_corr, st);
+    }
     c->M_valid = true;
   }
   ph_begin(c, PH_CHOL, st);
-  launch_shift(S.nu, c->Khat, c->M, delta, c->F, st);
+  launch_shift(S.nu, c->Khat, c->M, delta, tau, c->F, st);
   CK(cudaMemsetAsync(c->dw.flags + FLAG_NOT_PD, 0, sizeof(int), st));
   launch_cholesky(S.nu, c->F, c->dw.flags, st);
   ph_end(c, PH_CHOL, st);
@@ -430,6 +506,73 @@ ipm_status do_factor(ipm_ctx *c, double delta, int *is_pd, cudaStream_t st) {
   *is_pd = c->h_flags[FLAG_NOT_PD] ? 0 : 1;
   c->have_fact = *is_pd != 0;
   c->delta_fact = delta;
+  return IPM_OK;
+}
+
+// Exact FP64 product of the reduced matrix of K + delta I with v (matrix-free,
+// Prop. 2.3): w_i = -G_x^{-1} G_u v, then
+// out = sum_i [ -G_u^T G_x^{-T}((K_xx + delta) w_i + K_xu v) + K_ux w_i + K_uu^i v ] + (diag1 + delta) v
+ipm_status reduced_apply(ipm_ctx *c, const double *v, double *out, double delta, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const long long NX = (long long)S.N * S.nx;
+  CK(cudaMemsetAsync(c->vpos, 0, NX * sizeof(double), st));
+  launch_gu_apply(S, D.J, v, c->vpos, st);
+  launch_solve1(S, D.LU, D.rd, c->vpos, 0, st);
+  launch_lincomb(NX, c->vpos, -1.0, c->vpos, 0.0, nullptr, 0.0, nullptr, st);
+  launch_kapply(S, D.K, c->vpos, v, c->kpx, c->kpu, st);
+  launch_lincomb(NX, c->apos, 1.0, c->kpx, delta, c->vpos, 0.0, nullptr, st);
+  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+  launch_gut_sum(S, D.J, c->apos, -1.0, out, st);
+  launch_apply_finish(S, c->kpu, c->diag1, delta, v, out, st);
+  return IPM_OK;
+}
+
+// p_u of the reduced system eq. (11) to FP64 accuracy: conjugate gradients on
+// the exact operator, preconditioned by the Cholesky factor of the BF16x3
+// K_hat; c->pu holds the right-hand side on entry and the solution on exit.
+ipm_status pcg_reduced(ipm_ctx *c, double delta, cudaStream_t st) {
+  const int nu = c->ds.nu;
+  double *x = c->pu, *b = c->pcg_b, *r = c->pcg_r, *z = c->pcg_z, *p = c->pcg_p, *Ap = c->pcg_Ap;
+  c->neg_curv = false;
+  CK(cudaMemcpyAsync(b, x, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_chol_solve(nu, c->F, x, st);
+  TRY(reduced_apply(c, x, Ap, delta, st));
+  launch_lincomb(nu, r, 1.0, b, -1.0, Ap, 0.0, nullptr, st);
+  CK(cudaMemcpyAsync(z, r, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_chol_solve(nu, c->F, z, st);
+  CK(cudaMemcpyAsync(p, z, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_dot2(nu, r, z, b, b, c->red_out, st);
+  TRY(read_red(c, 2, st));
+  double rz = c->h_red[0];
+  const double bnorm = std::sqrt(std::max(c->h_red[1], 1e-300));
+  launch_dot2(nu, r, r, nullptr, nullptr, c->red_out, st);
+  TRY(read_red(c, 1, st));
+  double res = std::sqrt(c->h_red[0]) / bnorm;
+  int it = 0;
+  for (; it < c->opt.max_refine && res > 1e-13 && rz > 0.0; ++it) {
+    TRY(reduced_apply(c, p, Ap, delta, st));
+    launch_dot2(nu, p, Ap, nullptr, nullptr, c->red_out, st);
+    TRY(read_red(c, 1, st));
+    const double pAp = c->h_red[0];
+    if (!(pAp > 0.0)) {
+      c->neg_curv = true;
+      break;
+    }
+    const double alpha = rz / pAp;
+    launch_lincomb(nu, x, 1.0, x, alpha, p, 0.0, nullptr, st);
+    launch_lincomb(nu, r, 1.0, r, -alpha, Ap, 0.0, nullptr, st);
+    CK(cudaMemcpyAsync(z, r, nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_chol_solve(nu, c->F, z, st);
+    launch_dot2(nu, r, z, r, r, c->red_out, st);
+    TRY(read_red(c, 2, st));
+    const double rz_new = c->h_red[0];
+    res = std::sqrt(c->h_red[1]) / bnorm;
+    launch_lincomb(nu, p, 1.0, z, rz_new / rz, p, 0.0, nullptr, st);
+    rz = rz_new;
+  }
+  c->refine_iters = it;
+  c->refine_res = res;
   return IPM_OK;
 }
 
@@ -443,10 +586,19 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st) {
   const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
   ph_begin(c, PH_RECOVER, st);
   launch_lincomb(S.nu, c->pu, 1.0, c->rhs_u, delta, delta != 0.0 ? c->rhs_corr : nullptr, 0.0, nullptr, st);
-  launch_chol_solve(S.nu, c->F, c->pu, st);
-  // p_x = -G_x^{-1} (r3 + G_u p_u) = Z p_u - b
-  CK(cudaMemcpyAsync(c->vpos, c->bpos, NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  launch_z_apply(S, c->Z, c->pu, -1.0, c->vpos, st);
+  if (!c->mixed || c->exact_iter) {
+    launch_chol_solve(S.nu, c->F, c->pu, st);
+    // p_x = -G_x^{-1} (r3 + G_u p_u) = Z p_u - b
+    CK(cudaMemcpyAsync(c->vpos, c->bpos, NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_z_apply(S, c->Z, c->pu, -1.0, c->vpos, st);
+  } else {
+    TRY(pcg_reduced(c, delta, st));
+    // p_x = -G_x^{-1} (r3 + G_u p_u) with FP64 solves
+    launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->vpos, 1.0, st);
+    launch_gu_apply(S, D.J, c->pu, c->vpos, st);
+    launch_solve1(S, D.LU, D.rd, c->vpos, 0, st);
+    launch_lincomb(NX, c->vpos, -1.0, c->vpos, 0.0, nullptr, 0.0, nullptr, st);
+  }
   launch_scatter_pos(S.N, S.nx, S.iperm, c->vpos, c->px, 1.0, st);
   // p_y = -G_x^{-T} (rhat1 + (K_xx + delta I) p_x + K_xu p_u)
   launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);
@@ -508,9 +660,28 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
     mu = std::max(mu_min, std::min(KAPPA_MU * mu, std::pow(mu, THETA_MU)));
     c->mu = mu;
   }
+  c->exact_iter = false;
   TRY(do_condense(c, st));
   int pd = 0;
   TRY(do_factor(c, 0.0, &pd, st));
+  if (c->mixed && !pd) {
+    // The BF16x3 K_hat carries errors ~5e-7 of its largest entries; near the
+    // solution (Sigma ~ 1/mu) that can make it indefinite although the exact
+    // K_hat is positive definite.  Shift only the preconditioner (tau I,
+    // tau = 1e-8 .. 1e-5 of its largest diagonal entry); the system keeps
+    // delta = 0 and conjugate gradients on the exact operator decide: non-
+    // positive curvature sends the iteration to the FP64 condensation.
+    launch_maxdiag(S.nu, c->Khat, c->red_out, st);
+    TRY(read_red(c, 1, st));
+    const double dmax = c->h_red[0];
+    for (double f = 1e-8; f <= 1e-5 * 1.0001 && !pd; f *= 10.0) TRY(do_factor(c, 0.0, &pd, st, f * dmax));
+    if (!pd) {
+      c->exact_iter = true;
+      ++c->n_fallback;
+      TRY(do_condense(c, st));
+      TRY(do_factor(c, 0.0, &pd, st));
+    }
+  }
   double delta = 0.0;
   if (!pd) {
     const double dl = c->delta_last;
@@ -526,6 +697,29 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
     }
   }
   TRY(do_solve(c, st));
+  if (c->mixed && !c->exact_iter && (c->neg_curv || !(c->refine_res <= 1e-10))) {
+    // CG met non-positive curvature or did not converge: redo in FP64
+    c->exact_iter = true;
+    ++c->n_fallback;
+    TRY(do_condense(c, st));
+    pd = 0;
+    TRY(do_factor(c, 0.0, &pd, st));
+    delta = 0.0;
+    if (!pd) {
+      const double dl = c->delta_last;
+      delta = dl == 0.0 ? DELTA0 : std::max(DELTA_MIN, KW_MINUS * dl);
+      while (true) {
+        TRY(do_factor(c, delta, &pd, st));
+        if (pd) {
+          c->delta_last = delta;
+          break;
+        }
+        delta *= (dl == 0.0) ? KW_PLUS_BAR : KW_PLUS;
+        if (delta > DELTA_MAX) return fail(c, IPM_ERR_NOT_PD, "inertia correction exceeded delta_max");
+      }
+    }
+    TRY(do_solve(c, st));
+  }
   ph_begin(c, PH_LS, st);
   const double tau = std::max(TAU_MIN, 1.0 - mu);
   launch_ftb(S, D, c->px, c->pu, c->ps, c->dz, tau, c->red_partial, c->red_out, st);
@@ -570,7 +764,9 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
   ph_end(c, PH_LS, st);
   CK(cudaGetLastError());
   c->info[0] = alpha; c->info[1] = amax; c->info[2] = az; c->info[3] = delta;
-  c->info[4] = trials; c->info[5] = rho; c->info[6] = mu; c->info[7] = 0;
+  c->info[4] = trials; c->info[5] = rho; c->info[6] = mu; c->info[7] = c->mixed ? c->refine_iters : 0;
+  c->info[8] = c->mixed ? c->refine_res : 0.0; c->info[9] = c->exact_iter ? 1.0 : 0.0;
+  c->exact_iter = false;
   c->have_eval = c->have_cond = c->have_fact = false;
   ipm_status ws = write_scalars(c, st);
   ph_collect(c);
@@ -594,7 +790,7 @@ ipm_status ipm_default_options(ipm_options *opt) {
   opt->tol = 1e-8;
   opt->max_iter = 200;
   opt->precision = IPM_PREC_FP64;
-  opt->max_refine = 10;
+  opt->max_refine = 25;
   opt->panel = 0;
   opt->barrier_rule = IPM_BARRIER_ADAPTIVE;
   opt->sigma = 0.1;
@@ -617,7 +813,8 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
   ipm_ctx *c = new ipm_ctx();
   if (opt) c->opt = *opt;
   else ipm_default_options(&c->opt);
-  if (c->opt.precision != IPM_PREC_FP64 || !(c->opt.tol > 0) || c->opt.max_iter < 0 ||
+  if ((c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || !(c->opt.tol > 0) ||
+      c->opt.max_iter < 0 || c->opt.max_refine < 0 ||
       (c->opt.barrier_rule == IPM_BARRIER_ADAPTIVE && !(c->opt.sigma > 0 && c->opt.sigma < 1))) {
     delete c;
     return IPM_ERR_ARG;
@@ -717,7 +914,7 @@ ipm_status ipm_solve_kkt(ipm_ctx *c, double *step, double *refine_resid, void *s
   cudaStream_t st = STR(stream);
   TRY(do_solve(c, st));
   if (step) CK(cudaMemcpyAsync(step, c->step, c->step_len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if (refine_resid) *refine_resid = 0.0;
+  if (refine_resid) *refine_resid = c->mixed ? c->refine_res : 0.0;
   CK(cudaStreamSynchronize(st));
   return IPM_OK;
 }
@@ -780,8 +977,8 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
     return IPM_OK;
   }
   if (which == IPM_Q_INFO) {
-    if (!need(8)) return IPM_ERR_ARG;
-    std::memcpy(out, c->info, 8 * sizeof(double));
+    if (!need(10)) return IPM_ERR_ARG;
+    std::memcpy(out, c->info, 10 * sizeof(double));
     return IPM_OK;
   }
   if (scen < 0 || scen >= N) return IPM_ERR_ARG;
@@ -789,7 +986,13 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
     if (!c->have_cond) return fail(c, IPM_ERR_STATE, "no condensed system");
     if (!need((long long)nx * nu)) return IPM_ERR_ARG;
     std::vector<double> z((size_t)nx * nu);
-    CK(cudaMemcpy(z.data(), c->Z + (size_t)scen * nx * nu, z.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    if (c->mixed) {
+      std::vector<float> zf((size_t)nx * nu);
+      CK(cudaMemcpy(zf.data(), c->Z32 + (size_t)scen * nx * nu, zf.size() * sizeof(float), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < zf.size(); ++i) z[i] = zf[i];
+    } else {
+      CK(cudaMemcpy(z.data(), c->Z + (size_t)scen * nx * nu, z.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    }
     for (int p = 0; p < nx; ++p)
       std::memcpy(out + (size_t)S.iperm[p] * nu, z.data() + (size_t)p * nu, nu * sizeof(double));
     return IPM_OK;

@@ -45,6 +45,8 @@ struct Sym {
   int nlev_f = 0;          // levels of the sparse (non-tail) pivots
   int t0 = 0, nd = 0;      // dense trailing block: positions [t0, nx), nd = nx - t0
   std::vector<int> tail_slot;  // nd*nd LU slots of the trailing block, row-major
+  int nlev_fs = 0, nlev_bs = 0;  // forward / backward levels of the sparse rows only
+  std::vector<int> fs_lev_ptr, fs_rows, bs_lev_ptr, bs_rows;
   std::vector<int> f_lev_ptr, f_piv_ptr, f_piv, f_tgt, f_op_ptr, f_op_l, f_op_u, f_op_k;
   std::vector<int> lsc_slot, lsc_k;
   std::vector<int> fw_lev_ptr, fw_rows, fr_ptr, fr_col, fr_lslot, fr_uslot;

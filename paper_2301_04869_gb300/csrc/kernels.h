@@ -16,6 +16,8 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
                       cudaStream_t st);
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
                      double *Z, double *Y, double *Yu, cudaStream_t st);
+void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
+                     float *Z, float *Y, double *Yu, cudaStream_t st);
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st);
 
@@ -25,7 +27,9 @@ void launch_gemm_tn64(long long krows, long long kc, int nu, int ngroups, const 
 void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const double *partial,
                           const int *tile_of, const double *Yu, const double *diag, double *Khat,
                           cudaStream_t st);
-void launch_shift(int nu, const double *Khat, const double *M, double delta, double *F, cudaStream_t st);
+void launch_shift(int nu, const double *Khat, const double *M, double delta, double tau, double *F,
+                  cudaStream_t st);
+void launch_maxdiag(int n, const double *A, double *out, cudaStream_t st);
 void launch_cholesky(int n, double *A, int *flags, cudaStream_t st);
 void launch_chol_solve(int n, const double *L, double *b, cudaStream_t st);
 
@@ -55,6 +59,10 @@ void launch_zt_apply(const DevSym &S, const double *Z, const double *w, const do
 void launch_z_apply(const DevSym &S, const double *Z, const double *pu, double a, double *v, cudaStream_t st);
 void launch_gut_sum(const DevSym &S, const double *J, const double *a, double scale, double *out,
                     cudaStream_t st);
+void launch_apply_finish(const DevSym &S, const double *kpu, const double *diag, double delta, const double *v,
+                         double *out, cudaStream_t st);
+void launch_dot2(int n, const double *a, const double *b, const double *c, const double *d, double *out,
+                 cudaStream_t st);
 void launch_pz_ps(const DevSym &S, DevWork &D, const double *px, const double *pu, double *Hp, double *pz,
                   double *ps, cudaStream_t st);
 void launch_bound_steps(long long n, int period, const double *w, const double *dw, const double *l,

@@ -89,13 +89,30 @@ __global__ void k_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1,
   Khat[(size_t)j * nu + i] = v;
 }
 
-__global__ void k_shift(int nu, const double *Khat, const double *M, double delta, double *F) {
+// F = Khat + delta (M + I) + tau I   (tau: shift of a preconditioner only)
+__global__ void k_shift(int nu, const double *Khat, const double *M, double delta, double tau, double *F) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nu * nu) return;
   const int i = (int)(t / nu), j = (int)(t % nu);
   double v = Khat[t];
   if (delta != 0.0) v += delta * (M[t] + (i == j ? 1.0 : 0.0));
+  if (i == j) v += tau;
   F[t] = v;
+}
+
+// out[0] = max_i |A_ii|
+__global__ void k_maxdiag(int n, const double *A, double *out) {
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(A[(size_t)i * n + i]));
+  m = warp_max(m);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+    out[0] = r;
+  }
 }
 
 constexpr int CB = 32;  // Cholesky block
@@ -202,9 +219,13 @@ void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const
   k_khat_assemble<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, N, ngroups, ntiles, nt1, partial,
                                                              tile_of, Yu, diag, Khat); ++g_ipm_launches;
 }
-void launch_shift(int nu, const double *Khat, const double *M, double delta, double *F, cudaStream_t st) {
+void launch_shift(int nu, const double *Khat, const double *M, double delta, double tau, double *F,
+                  cudaStream_t st) {
   long long tot = (long long)nu * nu;
-  k_shift<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, Khat, M, delta, F); ++g_ipm_launches;
+  k_shift<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, Khat, M, delta, tau, F); ++g_ipm_launches;
+}
+void launch_maxdiag(int n, const double *A, double *out, cudaStream_t st) {
+  k_maxdiag<<<1, 256, 0, st>>>(n, A, out); ++g_ipm_launches;
 }
 void launch_cholesky(int n, double *A, int *flags, cudaStream_t st) {
   for (int k0 = 0; k0 < n; k0 += CB) {

@@ -116,53 +116,108 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
   for (int e = tid; e < ns * ns; e += bd) A[ts[(k0 + e / ns) * nd + k0 + e % ns]] = T[e];
 }
 
-// Z = -U^{-1} L^{-1} (P G_u) for one scenario and one panel of 32 RHS
-// columns (lane = column), then Y = K_x [Z; I] and Y_u = K_u [Z; I].
-// Rows of Z and Y are in LU position order.
-__global__ void __launch_bounds__(256) k_zsolve64(DevSym S, const double *__restrict__ LU,
-                                                  const double *__restrict__ rd,
-                                                  const double *__restrict__ J,
-                                                  const double *__restrict__ K, double *Z,
-                                                  double *Y, double *Yu) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int sc = blockIdx.y, c = blockIdx.x * 32 + lane, nu = S.nu, nx = S.nx, N = S.N;
+// Multi-RHS reduction solve for one scenario and one panel of 32 RHS columns
+// (lane = column): Z = -U^{-1} L^{-1} (P G_u) (rows in LU position order),
+// then Y = K_x [Z; I] and Y_u = K_u [Z; I].  The sparse rows follow the level
+// schedule (one warp per row); the dense trailing block [t0, nx) is solved
+// column by column by the whole CTA, in shared memory when it fits
+// (tail_smem), else in place in Z.  T is the storage/arithmetic type of Z, Y
+// (double on the FP64 path, float on the mixed path); Y_u accumulates in FP64.
+template <typename T>
+__device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, const double *__restrict__ rd,
+                            const double *__restrict__ J, const double *__restrict__ K, T *Z, T *Y, double *Yu,
+                            bool tail_smem, T *sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, bd = blockDim.x;
+  const int sc = blockIdx.y, c0 = blockIdx.x * 32, c = c0 + lane, nu = S.nu, nx = S.nx, N = S.N;
+  const int t0 = S.t0, nd = S.nd;
   const bool valid = c < nu;
   const int cc = valid ? c : nu - 1;
   const double *A = LU + (size_t)sc * S.nnzLU;
   const double *r = rd + (size_t)sc * nx;
-  double *Zs = Z + (size_t)sc * nx * nu;
-  double *Ys = Y + (size_t)sc * nx * nu;
+  T *Zs = Z + (size_t)sc * nx * nu;
+  T *Ys = Y + (size_t)sc * nx * nu;
   double *Yus = Yu + (size_t)sc * nu * nu;
-  for (int l = 0; l < S.nlev; ++l) {
-    for (int e = S.fw_lev_ptr[l] + warp; e < S.fw_lev_ptr[l + 1]; e += nw) {
-      const int row = S.fw_rows[e];
-      double acc = 0.0;
+  // forward, sparse rows
+  for (int l = 0; l < S.nlev_fs; ++l) {
+    for (int e = S.fs_lev_ptr[l] + warp; e < S.fs_lev_ptr[l + 1]; e += nw) {
+      const int row = S.fs_rows[e];
+      T acc = 0;
       for (int g = S.gu_ptr[row]; g < S.gu_ptr[row + 1]; ++g)
         if (S.gu_col[g] == cc) {
           const int src = S.gu_src[g];
-          acc -= src >= 0 ? J[(size_t)src * N + sc] : -1.0;
+          acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
         }
       for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1]; ++f)
-        acc -= A[S.fr_lslot[f]] * Zs[(size_t)S.fr_col[f] * nu + cc];
+        acc -= (T)A[S.fr_lslot[f]] * Zs[(size_t)S.fr_col[f] * nu + cc];
       if (valid) Zs[(size_t)row * nu + c] = acc;
     }
     __syncthreads();
   }
-  for (int l = 0; l < S.nlev_b; ++l) {
-    for (int e = S.bw_lev_ptr[l] + warp; e < S.bw_lev_ptr[l + 1]; e += nw) {
-      const int row = S.bw_rows[e];
-      double acc = Zs[(size_t)row * nu + cc];
+  if (nd > 0) {
+    // trailing block: right-hand side and the sparse part of each row
+    for (int i = warp; i < nd; i += nw) {
+      const int row = t0 + i;
+      T acc = 0;
+      for (int g = S.gu_ptr[row]; g < S.gu_ptr[row + 1]; ++g)
+        if (S.gu_col[g] == cc) {
+          const int src = S.gu_src[g];
+          acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
+        }
+      for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1] && S.fr_col[f] < t0; ++f)
+        acc -= (T)A[S.fr_lslot[f]] * Zs[(size_t)S.fr_col[f] * nu + cc];
+      if (tail_smem) sh[i * 32 + lane] = acc;
+      else if (valid) Zs[(size_t)row * nu + c] = acc;
+    }
+    __syncthreads();
+    const int *ts = S.tail_slot;
+    // forward, dense unit-lower part, column by column
+    for (int k = 0; k < nd - 1; ++k) {
+      const int m = (nd - k - 1) * 32;
+      for (int e = tid; e < m; e += bd) {
+        const int i = k + 1 + (e >> 5), q = e & 31;
+        const T l = (T)A[ts[i * nd + k]];
+        if (tail_smem) sh[i * 32 + q] -= l * sh[k * 32 + q];
+        else if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] -= l * Zs[(size_t)(t0 + k) * nu + c0 + q];
+      }
+      __syncthreads();
+    }
+    // backward, dense upper part (unscaled accumulators; x_k = acc_k / u_kk)
+    for (int k = nd - 1; k > 0; --k) {
+      const T rk = (T)r[t0 + k];
+      const int m = k * 32;
+      for (int e = tid; e < m; e += bd) {
+        const int i = e >> 5, q = e & 31;
+        const T u = (T)A[ts[i * nd + k]];
+        if (tail_smem) sh[i * 32 + q] -= u * (sh[k * 32 + q] * rk);
+        else if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] -= u * (Zs[(size_t)(t0 + k) * nu + c0 + q] * rk);
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < nd * 32; e += bd) {
+      const int i = e >> 5, q = e & 31;
+      if (c0 + q < nu) {
+        T *dst = &Zs[(size_t)(t0 + i) * nu + c0 + q];
+        *dst = (tail_smem ? sh[i * 32 + q] : *dst) * (T)r[t0 + i];
+      }
+    }
+    __syncthreads();
+  }
+  // backward, sparse rows
+  for (int l = 0; l < S.nlev_bs; ++l) {
+    for (int e = S.bs_lev_ptr[l] + warp; e < S.bs_lev_ptr[l + 1]; e += nw) {
+      const int row = S.bs_rows[e];
+      T acc = Zs[(size_t)row * nu + cc];
       for (int f = S.br_ptr[row]; f < S.br_ptr[row + 1]; ++f)
-        acc -= A[S.br_uslot[f]] * Zs[(size_t)S.br_col[f] * nu + cc];
-      if (valid) Zs[(size_t)row * nu + c] = acc * r[row];
+        acc -= (T)A[S.br_uslot[f]] * Zs[(size_t)S.br_col[f] * nu + cc];
+      if (valid) Zs[(size_t)row * nu + c] = acc * (T)r[row];
     }
     __syncthreads();
   }
   for (int row = warp; row < nx; row += nw) {
-    double acc = 0.0;
+    T acc = 0;
     for (int e = S.kx_ptr[row]; e < S.kx_ptr[row + 1]; ++e) {
       const int col = S.kx_col[e];
-      const double v = K[(size_t)S.kx_src[e] * N + sc];
+      const T v = (T)K[(size_t)S.kx_src[e] * N + sc];
       if (col < nx) acc += v * Zs[(size_t)col * nu + cc];
       else if (col - nx == cc) acc += v;
     }
@@ -173,28 +228,49 @@ __global__ void __launch_bounds__(256) k_zsolve64(DevSym S, const double *__rest
     for (int e = S.ku_ptr[j]; e < S.ku_ptr[j + 1]; ++e) {
       const int col = S.ku_col[e];
       const double v = K[(size_t)S.ku_src[e] * N + sc];
-      if (col < nx) acc += v * Zs[(size_t)col * nu + cc];
+      if (col < nx) acc += v * (double)Zs[(size_t)col * nu + cc];
       else if (col - nx == cc) acc += v;
     }
     if (valid) Yus[(size_t)j * nu + c] = acc;
   }
 }
 
+__global__ void __launch_bounds__(256) k_zsolve64(DevSym S, const double *__restrict__ LU,
+                                                  const double *__restrict__ rd,
+                                                  const double *__restrict__ J,
+                                                  const double *__restrict__ K, double *Z, double *Y,
+                                                  double *Yu, int tail_smem) {
+  extern __shared__ double shd[];
+  zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd);
+}
+
+__global__ void __launch_bounds__(256) k_zsolve32(DevSym S, const double *__restrict__ LU,
+                                                  const double *__restrict__ rd,
+                                                  const double *__restrict__ J,
+                                                  const double *__restrict__ K, float *Z, float *Y,
+                                                  double *Yu, int tail_smem) {
+  extern __shared__ float shf[];
+  zsolve_body<float>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shf);
+}
+
 // In-place solve of G_x v = b (trans = 0) or G_x^T v = b (trans = 1) for every
-// scenario; v is [N][nx] in LU position order.  One CTA per scenario walks
-// the level schedule; within a level each warp takes one row and its lanes
-// split the row's entries (the trailing rows of the factor are dense).
+// scenario; v is [N][nx] in LU position order.  One CTA per scenario: sparse
+// rows by levels (one warp per row, lanes over the row's entries), the dense
+// trailing block column by column in shared memory.
 __global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
                          double *v, int trans) {
-  const int sc = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  extern __shared__ double tv[];
+  const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  const int t0 = S.t0, nd = S.nd;
   const double *A = LU + (size_t)sc * S.nnzLU;
   const double *r = rd + (size_t)sc * S.nx;
   double *vs = v + (size_t)sc * S.nx;
   const int *fsl = trans ? S.fr_uslot : S.fr_lslot;
   const int *bsl = trans ? S.br_lslot : S.br_uslot;
-  for (int l = 0; l < S.nlev; ++l) {
-    for (int e = S.fw_lev_ptr[l] + warp; e < S.fw_lev_ptr[l + 1]; e += nw) {
-      const int row = S.fw_rows[e];
+  for (int l = 0; l < S.nlev_fs; ++l) {
+    for (int e = S.fs_lev_ptr[l] + warp; e < S.fs_lev_ptr[l + 1]; e += nw) {
+      const int row = S.fs_rows[e];
       double part = 0.0;
       for (int f = S.fr_ptr[row] + lane; f < S.fr_ptr[row + 1]; f += 32) part += A[fsl[f]] * vs[S.fr_col[f]];
       part = warp_sum(part);
@@ -202,9 +278,40 @@ __global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *
     }
     __syncthreads();
   }
-  for (int l = 0; l < S.nlev_b; ++l) {
-    for (int e = S.bw_lev_ptr[l] + warp; e < S.bw_lev_ptr[l + 1]; e += nw) {
-      const int row = S.bw_rows[e];
+  if (nd > 0) {
+    const int *ts = S.tail_slot;
+    // sparse part of the trailing rows
+    for (int i = warp; i < nd; i += nw) {
+      const int row = t0 + i;
+      double part = 0.0;
+      for (int f = S.fr_ptr[row] + lane; f < S.fr_ptr[row + 1]; f += 32)
+        if (S.fr_col[f] < t0) part += A[fsl[f]] * vs[S.fr_col[f]];
+      part = warp_sum(part);
+      if (lane == 0) tv[i] = vs[row] - part;
+    }
+    __syncthreads();
+    // forward over the dense block: L (unit) or U^T (diagonal u_kk)
+    for (int k = 0; k < nd; ++k) {
+      const double xk = trans ? tv[k] * r[t0 + k] : tv[k];
+      for (int i = k + 1 + tid; i < nd; i += bd) tv[i] -= A[trans ? ts[k * nd + i] : ts[i * nd + k]] * xk;
+      __syncthreads();
+      if (tid == 0 && trans) tv[k] = xk;
+      __syncthreads();
+    }
+    // backward over the dense block: U (diagonal) or L^T (unit)
+    for (int k = nd - 1; k >= 0; --k) {
+      const double xk = trans ? tv[k] : tv[k] * r[t0 + k];
+      for (int i = tid; i < k; i += bd) tv[i] -= A[trans ? ts[k * nd + i] : ts[i * nd + k]] * xk;
+      __syncthreads();
+      if (tid == 0 && !trans) tv[k] = xk;
+      __syncthreads();
+    }
+    for (int i = tid; i < nd; i += bd) vs[t0 + i] = tv[i];
+    __syncthreads();
+  }
+  for (int l = 0; l < S.nlev_bs; ++l) {
+    for (int e = S.bs_lev_ptr[l] + warp; e < S.bs_lev_ptr[l + 1]; e += nw) {
+      const int row = S.bs_rows[e];
       double part = 0.0;
       for (int f = S.br_ptr[row] + lane; f < S.br_ptr[row + 1]; f += 32) part += A[bsl[f]] * vs[S.br_col[f]];
       part = warp_sum(part);
@@ -224,12 +331,28 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_lu_factor<<<S.N, 512, smem, st>>>(S, nL, J, LU, rd, flags, 1e-14, ns); ++g_ipm_launches;
 }
+static int zsolve_smem_ok(const DevSym &S, size_t elem) {
+  return (S.nd > 0 && (size_t)S.nd * 32 * elem <= 100 * 1024) ? 1 : 0;
+}
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J,
                      const double *K, double *Z, double *Y, double *Yu, cudaStream_t st) {
   dim3 grid((S.nu + 31) / 32, S.N);
-  k_zsolve64<<<grid, 256, 0, st>>>(S, LU, rd, J, K, Z, Y, Yu); ++g_ipm_launches;
+  const int sm = zsolve_smem_ok(S, sizeof(double));
+  const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(double) : 0;
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k_zsolve64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_zsolve64<<<grid, 256, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ++g_ipm_launches;
+}
+void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
+                     const double *K, float *Z, float *Y, double *Yu, cudaStream_t st) {
+  dim3 grid((S.nu + 31) / 32, S.N);
+  const int sm = zsolve_smem_ok(S, sizeof(float));
+  const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(float) : 0;
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k_zsolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_zsolve32<<<grid, 256, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ++g_ipm_launches;
 }
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st) {
-  k_solve1<<<S.N, 512, 0, st>>>(S, LU, rd, v, trans); ++g_ipm_launches;
+  const size_t bytes = (size_t)S.nd * sizeof(double);
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans); ++g_ipm_launches;
 }

@@ -371,6 +371,37 @@ __global__ void k_gut_sum(DevSym S, const double *J, const double *a, double sca
   out[j] = scale * acc;
 }
 
+// out[j] += sum_s kpu[s][j] + (diag[j] + delta) v[j]   (scenarios in index order)
+__global__ void k_apply_finish(DevSym S, const double *kpu, const double *diag, double delta, const double *v,
+                               double *out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= S.nu) return;
+  double acc = out[j];
+  for (int sc = 0; sc < S.N; ++sc) acc += kpu[(size_t)sc * S.nu + j];
+  out[j] = acc + (diag[j] + delta) * v[j];
+}
+
+// out[0] = a.b, out[1] = c.d (one block, fixed partition and tree)
+__global__ void k_dot2(int n, const double *a, const double *b, const double *c, const double *d, double *out) {
+  __shared__ double sh[2][32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    s0 += a[i] * b[i];
+    if (c) s1 += c[i] * d[i];
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { sh[0][w] = s0; sh[1][w] = s1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { t0 += sh[0][q]; t1 += sh[1][q]; }
+    out[0] = t0;
+    out[1] = t1;
+  }
+}
+
 // Hp = H_x p_x + H_u p_u; p_z = Sigma_s (Hp + r4) - r2; p_s = -(r2 + p_z)/Sigma_s
 __global__ void k_pz_ps(DevSym S, DevWork D, const double *px, const double *pu, double *Hp,
                         double *pz, double *ps) {
@@ -536,6 +567,14 @@ void launch_z_apply(const DevSym &S, const double *Z, const double *pu, double a
 void launch_gut_sum(const DevSym &S, const double *J, const double *a, double scale, double *out,
                     cudaStream_t st) {
   k_gut_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, J, a, scale, out); ++g_ipm_launches;
+}
+void launch_apply_finish(const DevSym &S, const double *kpu, const double *diag, double delta, const double *v,
+                         double *out, cudaStream_t st) {
+  k_apply_finish<<<nblk(S.nu, 128), 128, 0, st>>>(S, kpu, diag, delta, v, out); ++g_ipm_launches;
+}
+void launch_dot2(int n, const double *a, const double *b, const double *c, const double *d, double *out,
+                 cudaStream_t st) {
+  k_dot2<<<1, 256, 0, st>>>(n, a, b, c, d, out); ++g_ipm_launches;
 }
 void launch_pz_ps(const DevSym &S, DevWork &D, const double *px, const double *pu, double *Hp, double *pz,
                   double *ps, cudaStream_t st) {

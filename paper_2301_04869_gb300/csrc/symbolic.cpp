@@ -402,6 +402,24 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
       for (int i : bl[l]) S.bw_rows.push_back(i);
       S.bw_lev_ptr[l + 1] = (int)S.bw_rows.size();
     }
+    // the same schedules over the sparse rows only (the dense trailing block
+    // [t0, nx) is solved separately); empty levels dropped
+    S.fs_lev_ptr.assign(1, 0);
+    for (int l = 0; l < nlev; ++l) {
+      bool any = false;
+      for (int i : fl[l])
+        if (i < S.t0) { S.fs_rows.push_back(i); any = true; }
+      if (any) S.fs_lev_ptr.push_back((int)S.fs_rows.size());
+    }
+    S.nlev_fs = (int)S.fs_lev_ptr.size() - 1;
+    S.bs_lev_ptr.assign(1, 0);
+    for (int l = 0; l < nlevb; ++l) {
+      bool any = false;
+      for (int i : bl[l])
+        if (i < S.t0) { S.bs_rows.push_back(i); any = true; }
+      if (any) S.bs_lev_ptr.push_back((int)S.bs_rows.size());
+    }
+    S.nlev_bs = (int)S.bs_lev_ptr.size() - 1;
   }
   // ---- G_u (rows: positions) and its transpose (rows: u) ----
   const int nu = S.nu;

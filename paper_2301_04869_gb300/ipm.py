@@ -113,7 +113,7 @@ def _stream(stream):
 class Solver:
     """One context: a network with N load scenarios on the current GPU."""
 
-    def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=10,
+    def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
                  barrier_rule=None, sigma=None):
         lib = load()
         self._lib = lib
@@ -227,7 +227,7 @@ class Solver:
         d = self.dims
         sizes = {Q_KHAT: d.n_u * d.n_u, Q_RHS_U: d.n_u, Q_Z: d.n_x * d.n_u, Q_FGH: 1 + d.n_x + d.m,
                  Q_JAC: d.n_x * d.n_x + d.n_x * d.n_u + d.m * d.n_x + d.m * d.n_u,
-                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 8,
+                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 10,
                  Q_TIMERS: 2 * N_PHASES + 1}
         out = np.empty(sizes[which])
         self._check(self._lib.ipm_get_quantity(self._h, which, scen, _ptr(out, ctypes.c_double), out.size,

@@ -174,7 +174,7 @@ def test_trajectory_matches_per_iteration(gpu):
         s = sol.split_state(sol.ipm_get_state())
         for key in ("x", "u", "s", "y", "z"):
             assert rel(s[key], st[key]) <= 1e-8, (k, key)
-        assert abs(s["mu"] - st["mu"]) <= 1e-15 * max(1.0, st["mu"])
+        assert abs(s["mu"] - st["mu"]) <= 1e-8 * st["mu"]
 
 
 def test_config_1000bus_64_scenarios_components(gpu):
