@@ -83,11 +83,18 @@ typedef struct {
   int max_iter;          /* 200 */
   int precision;         /* IPM_PREC_FP64 or IPM_PREC_MIXED */
   int max_refine;        /* iterative-refinement sweeps of the KKT solve (mixed) */
-  int panel;             /* RHS columns per CTA in the multi-RHS solves (0 = auto) */
+  int solve_threads;     /* threads per CTA of the multi-RHS solves: 128 or 256 (0 = 256,
+                            or the autotuner's choice) */
   int barrier_rule;      /* IPM_BARRIER_ADAPTIVE (default): mu = max(tol/10, sigma * mean
                             complementarity) at every iteration; IPM_BARRIER_MONOTONE:
                             mu <- max(tol/10, min(0.2 mu, mu^1.5)) when E_mu <= 10 mu */
-  int reserved[6];
+  int graphs;            /* 1: replay the condensation as CUDA graphs captured on its first
+                            call (needs a non-NULL stream; ignored while profiling) */
+  int autotune;          /* 1: at the first condensation, time the candidate launch shapes
+                            (solve threads, scenario groups of the reduced-Hessian
+                            contraction) and keep the fastest; results are cached per
+                            (n_x, n_u, N, precision) for the process */
+  int reserved[4];
   double sigma;          /* centring factor of the adaptive rule (0.1) */
 } ipm_options;
 
@@ -186,6 +193,111 @@ ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
  * gemm (Z^T Y + scenario sum), reduced_rhs, cholesky, recover, linesearch. */
 enum { IPM_N_PHASES = 9 };
 ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
+
+/* Replace the scenario loads of a context (same network and N) and reset the
+ * cold-start state.  pd, qd: host [n_scen][n_bus].  Reuses every symbolic
+ * structure and device workspace (no allocation).  Errors: IPM_ERR_ARG on
+ * non-finite or negative loads. */
+ipm_status ipm_set_loads(ipm_ctx *ctx, const double *pd, const double *qd, void *stream);
+
+/* ---- Multi-instance runner ------------------------------------------------
+ * Many independent instances (networks of any size, any scenario counts) on
+ * one GPU.  The paper solves one two-stage problem at a time; this runner
+ * has no counterpart there.  Host worker threads each drive one instance at
+ * a time through the ordinary IPM iteration on their own stream.  With
+ * group_contraction, the FP64 reduced-Hessian contractions of the instances
+ * that reach the condensation together run as ONE persistent launch over
+ * their (instance, tile, scenario group) work items; an instance waits at
+ * most window_us for the others before the launch goes ahead without them,
+ * and converged instances drop out.  Results are bit-identical to solving
+ * each context alone (the work items compute exactly the per-instance
+ * partial tiles). */
+typedef struct {
+  int n_threads;          /* host worker threads (0 = 8) */
+  int group_contraction;  /* 1 (default): grouped persistent contraction */
+  double window_us;       /* longest rendezvous wait (2000) */
+  int reserved[4];
+} ipm_batch_options;
+
+#define IPM_BATCH_N_STATS 8
+/* stats (nullable, IPM_BATCH_N_STATS doubles): grouped launches, work items,
+ * mean instances per grouped launch, most instances active at once, wall
+ * time in ms of the whole call, then zeros. */
+
+ipm_status ipm_batch_default_options(ipm_batch_options *opt);
+
+/* Solve n existing contexts from their current states.  streams: NULL (the
+ * runner creates one non-blocking stream per worker) or one stream per
+ * context.  iters, kkt_err, status: [n] outputs.  Returns IPM_OK when every
+ * instance converged, else the first failing status (all are attempted). */
+ipm_status ipm_solve_batch(ipm_ctx **ctxs, int n, void **streams, const ipm_batch_options *opt, int *iters,
+                           double *kkt_err, int *status, double *stats);
+
+/* Create, solve and destroy n instances under a device-memory budget (bytes):
+ * a worker creates its next context (symbolic analysis included) only while
+ * the estimated footprints of the live contexts plus its own fit in
+ * mem_budget (one context alone is always admitted); largest instances go
+ * first.  nets[i], n_scen[i], pd[i], qd[i] as for ipm_create; opt applies to
+ * all.  states_out: NULL, or per instance NULL or a host array of that
+ * instance's state_len doubles that receives the final state. */
+ipm_status ipm_run_instances(const ipm_network *nets, int n, const int *n_scen, const double *const *pd,
+                             const double *const *qd, const ipm_options *opt, const ipm_batch_options *bopt,
+                             long long mem_budget, double *const *states_out, int *iters, double *kkt_err,
+                             int *status, double *stats);
+
+/* ---- Learned warm start ---------------------------------------------------
+ * Not in the paper.  A small MLP maps a scenario's load vector to a
+ * primal-dual starting point of the IPM; the cold start stays the fallback.
+ *   y = W3 GELU(W2 GELU(W1 xn + b1) + b2) + b3,   xn = (x - in_mean) / in_std,
+ * prediction = out_mean + out_std * y, GELU(a) = a Phi(a) (Gauss error
+ * function form).  Products run in BF16 on the tensor cores with FP32
+ * accumulation; weights are FP32 masters trained by Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8) on the mean squared error of the normalised outputs,
+ *   L = (1 / (B d_out)) sum_b sum_k (y_bk - (t_bk - out_mean_k) / out_std_k)^2.
+ * Parameter vectors (host FP32) use the logical layout W1 [d_hidden][d_in],
+ * b1, W2 [d_hidden][d_hidden], b2, W3 [d_out][d_hidden], b3. */
+typedef struct ipm_mlp ipm_mlp;
+
+/* d_hidden: a multiple of 128.  max_batch: rows per internal pass (forward
+ * splits larger batches).  He-uniform weights from seed, zero biases, unit
+ * normalisation.  Errors: IPM_ERR_ARG, IPM_ERR_OOM. */
+ipm_status ipm_mlp_create(int d_in, int d_hidden, int d_out, int max_batch, unsigned long long seed,
+                          ipm_mlp **out);
+ipm_status ipm_mlp_destroy(ipm_mlp *mlp);
+long long ipm_mlp_param_count(const ipm_mlp *mlp);
+/* host FP32 params in the logical layout; resets the Adam moments */
+ipm_status ipm_mlp_set_params(ipm_mlp *mlp, const float *params);
+ipm_status ipm_mlp_get_params(ipm_mlp *mlp, float *params);
+/* host FP32 [d_in], [d_in], [d_out], [d_out]; stds must be > 0 */
+ipm_status ipm_mlp_set_normalization(ipm_mlp *mlp, const float *in_mean, const float *in_std,
+                                     const float *out_mean, const float *out_std);
+/* x: device FP32 [batch][d_in]; y: device FP32 [batch][d_out] (de-normalised) */
+ipm_status ipm_mlp_forward(ipm_mlp *mlp, const float *x, int batch, float *y, void *stream);
+/* loss and its gradient at the current weights (no update): x, target device
+ * FP32 [batch][d_in], [batch][d_out] (targets in output units), batch <=
+ * max_batch; grads: NULL or host FP32 in the logical layout; loss: host. */
+ipm_status ipm_mlp_gradients(ipm_mlp *mlp, const float *x, const float *target, int batch, float *grads,
+                             float *loss, void *stream);
+/* one Adam step at learning rate lr on the minibatch; loss before the step */
+ipm_status ipm_mlp_train_step(ipm_mlp *mlp, const float *x, const float *target, int batch, float lr,
+                              float *loss, void *stream);
+
+/* Warm-start vectors of a context, per scenario (FP32, device, [N][d]):
+ *   [ x (n_x) | u (n_u) | s (m) | log zl_x | log zu_x | log zl_u | log zu_u |
+ *     log zl_s | log zu_s ]
+ * where each log-dual block lists only the components with a finite bound of
+ * that side, in index order.  ipm_warm_dim gives d. */
+ipm_status ipm_warm_dim(const ipm_ctx *ctx, int *d);
+/* the current state (normally a converged one) as warm-start vectors */
+ipm_status ipm_warm_target(ipm_ctx *ctx, float *out, void *stream);
+/* Start the IPM from predicted vectors: x_i, s_i from each scenario's row,
+ * u = mean over the rows; primal values pushed into their bounds as at a
+ * cold start; bound duals exp(log dual) clipped to [1e-12, 1e12]; the slack
+ * multipliers from their stationarity (z = zl_s - zu_s); y from the
+ * stationarity of the Lagrangian in x, G_x^T y = -(grad_x f + H_x^T z -
+ * zl_x + zu_x), one batched transposed LU solve; mu = max(1e-6, mean
+ * complementarity).  Then ipm_solve continues from this point. */
+ipm_status ipm_warm_start(ipm_ctx *ctx, const float *pred, void *stream);
 
 /* Allocation-free reduced-Hessian sum.  The paper has no counterpart to this
  * entry point; it exists for callers that cannot call cudaMalloc (code that

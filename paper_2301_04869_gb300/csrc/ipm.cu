@@ -6,84 +6,37 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
+#include "ctx.h"
 #include "dev.cuh"
 #include "ipm_internal.h"
 #include "kernels.h"
 
-long long g_ipm_launches = 0;  // kernels launched by this library (all contexts)
+std::atomic<long long> g_ipm_launches{0};
+thread_local long long t_ipm_launches = 0;
 
 namespace {
 
-// IPM constants (the same rule set as the CPU oracle, see DESIGN)
+// IPM constants (the same rule set as the CPU oracle)
 constexpr double MU0 = 0.1, K1 = 1e-2, K2 = 1e-2, TAU_MIN = 0.99, KAPPA_EPS = 10.0, KAPPA_MU = 0.2,
                  THETA_MU = 1.5, ETA = 1e-4, ALPHA_MIN = 1e-12, KAPPA_SIGMA = 1e10, S_MAX = 100.0,
                  RHO0 = 1.0, RHO_FRAC = 0.1, DELTA0 = 1e-4, DELTA_MIN = 1e-20, DELTA_MAX = 1e40,
                  KW_MINUS = 1.0 / 3.0, KW_PLUS = 8.0, KW_PLUS_BAR = 100.0;
+// bound push of a learned warm start (relative, as K1/K2 of the cold start)
+constexpr double K1_WARM = 1e-5;
 
 }  // namespace
 
-struct ipm_ctx {
-  Sym S;
-  DevSym ds{};
-  DevWork dw{};
-  ipm_options opt{};
-  std::string err;
-  std::vector<void *> allocs;
-  double *state = nullptr;
-  long long state_len = 0, step_len = 0;
-  // work buffers
-  double *Z = nullptr, *Y = nullptr, *Yu = nullptr, *partial = nullptr;
-  int2 *tiles = nullptr;
-  int *tile_of = nullptr;
-  int ntiles = 0, nt1 = 0, ngroups = 0;
-  long long kchunk = 0;
-  double *Khat = nullptr, *M = nullptr, *F = nullptr, *diag1 = nullptr, *rhs_u = nullptr;
-  double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta); scratch [N][max(nx,nu)]
-  double *gLu = nullptr, *HTt_u = nullptr;
-  double *pg_curv = nullptr, *pmax_d = nullptr;
-  // mixed path
-  bool mixed = false;
-  float *Z32 = nullptr, *Y32 = nullptr;
-  void *zpl = nullptr, *ypl = nullptr;  // BF16x3 planes, K-major [3][nu][kpad]
-  double *tcpart = nullptr;
-  TcPlan planZY, planZZ;
-  double *pcg_b = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_Ap = nullptr;
-  int refine_iters = 0;
-  double refine_res = 0.0;
-  bool neg_curv = false;     // CG met p^T A p <= 0
-  bool exact_iter = false;   // this iteration runs the FP64 condensation (mixed fallback)
-  long long n_fallback = 0;  // mixed-path iterations that needed the FP64 condensation
-  double *step = nullptr, *px = nullptr, *pu = nullptr, *ps = nullptr, *py = nullptr, *pz = nullptr;
-  double *dz[6] = {};
-  double *Hp = nullptr, *kpx = nullptr, *kpu = nullptr, *vpos = nullptr, *bpos = nullptr, *apos = nullptr;
-  double *xt = nullptr, *ut = nullptr, *st = nullptr, *gt = nullptr, *ht = nullptr, *fst = nullptr,
-         *Pt = nullptr, *Qt = nullptr;
-  double *red_partial = nullptr, *red_out = nullptr;
-  double *h_red = nullptr;  // pinned host mirror of reduction outputs
-  int *h_flags = nullptr;
-  int nL = 0;
-  long long n_bounds = 0;
-  // host mirror of the state scalars
-  double mu = MU0, rho = RHO0, delta_last = 0.0;
-  double delta_fact = 0.0;
-  bool have_eval = false, have_cond = false, have_fact = false, M_valid = false;
-  double info[10] = {0};
-  double errs[6] = {0};
-  double mean_compl = 0.0;
-  // phase timers
-  bool prof = false;
-  cudaEvent_t ev[2 * IPM_N_PHASES] = {};
-  bool ev_pending[IPM_N_PHASES] = {};
-  double t_ms[IPM_N_PHASES] = {0};
-  double t_cnt[IPM_N_PHASES] = {0};
-};
 
 namespace {
 
@@ -184,6 +137,8 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   return IPM_OK;
 }
 
+void set_groups(ipm_ctx *c, long long G);
+
 ipm_status alloc_work(ipm_ctx *c) {
   const Sym &S = c->S;
   const long long N = S.N, nx = S.nx, nu = S.nu, m = S.m, n = S.n;
@@ -242,7 +197,12 @@ ipm_status alloc_work(ipm_ctx *c) {
       return fail(c, IPM_ERR_ARG, "internal: mixed region layout");
     if (!tc_set_operands(c->planZY, c->zpl, c->ypl) || !tc_set_operands(c->planZZ, c->zpl, c->zpl))
       return fail(c, IPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    TRY(dalloc(c, &c->tcpart, (long long)c->planZY.ngroups * c->planZY.ntiles * 128 * 128));
+    {
+      TcPlan big = c->planZY;
+      tc_regroup(big, 2 * std::max(1, 152 / big.ntiles));
+      c->tc_max_groups = std::max(big.ngroups, c->planZY.ngroups);
+    }
+    TRY(dalloc(c, &c->tcpart, (long long)c->tc_max_groups * c->planZY.ntiles * 128 * 128));
     TRY(dalloc(c, &c->pcg_b, nu)); TRY(dalloc(c, &c->pcg_r, nu)); TRY(dalloc(c, &c->pcg_z, nu));
     TRY(dalloc(c, &c->pcg_p, nu)); TRY(dalloc(c, &c->pcg_Ap, nu));
   }
@@ -257,21 +217,20 @@ ipm_status alloc_work(ipm_ctx *c) {
     }
   c->ntiles = (int)tl.size();
   // split the N*nx contraction rows into equal chunks so that tiles x chunks
-  // fills one wave (3 CTAs of 256 threads per SM, 152 SMs)
+  // fills one wave (3 CTAs of 256 threads per SM, 152 SMs); the buffer of
+  // partial tiles has room for the autotuner's largest candidate (4x)
   {
-    const long long krows = N * nx;
-    long long G = std::max(1, (3 * 152) / c->ntiles);
-    G = std::min(G, (krows + 15) / 16);
-    long long kc = (krows + G - 1) / G;
-    kc = (kc + 15) / 16 * 16;
-    c->kchunk = kc;
-    c->ngroups = (int)((krows + kc - 1) / kc);
+    const long long G0 = std::max(1, (3 * 152) / c->ntiles);
+    set_groups(c, 4 * G0);
+    c->max_groups = c->ngroups;
+    set_groups(c, G0);
   }
+  c->zs_threads = (c->opt.solve_threads == 128 || c->opt.solve_threads == 256) ? c->opt.solve_threads : 256;
   TRY(dalloc(c, &c->tiles, tl.size()));
   CK(cudaMemcpy(c->tiles, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice));
   TRY(dalloc(c, &c->tile_of, tof.size()));
   CK(cudaMemcpy(c->tile_of, tof.data(), tof.size() * sizeof(int), cudaMemcpyHostToDevice));
-  TRY(dalloc(c, &c->partial, (long long)c->ngroups * c->ntiles * 4096));
+  TRY(dalloc(c, &c->partial, (long long)c->max_groups * c->ntiles * 4096));
   TRY(dalloc(c, &c->Khat, nu * nu)); TRY(dalloc(c, &c->M, nu * nu)); TRY(dalloc(c, &c->F, nu * nu));
   TRY(dalloc(c, &c->diag1, nu)); TRY(dalloc(c, &c->rhs_u, nu));
   TRY(dalloc(c, &c->rhs_corr, nu)); TRY(dalloc(c, &c->cpos, N * std::max(nx, nu)));
@@ -303,6 +262,8 @@ ipm_status alloc_work(ipm_ctx *c) {
   TRY(dalloc(c, &c->red_partial, 152 * 8)); TRY(dalloc(c, &c->red_out, 16));
   CK(cudaMallocHost(&c->h_red, 16 * sizeof(double)));
   CK(cudaMallocHost(&c->h_flags, FLAG_COUNT * sizeof(int)));
+  CK(cudaMallocHost(&c->h_mu, sizeof(double)));
+  TRY(dalloc(c, &c->d_mu, 1));
   // first-stage diagonal terms of K_hat that do not depend on the iterate
   // (cost curvature of the non-slack generators); Sigma_u is added per call
   long long nb = 0;
@@ -403,65 +364,248 @@ ipm_status do_errors(ipm_ctx *c, cudaStream_t st) {
   return IPM_OK;
 }
 
+// Runs fn (a sequence of launches on st) directly, or as a CUDA graph that
+// is captured the first time: every launch parameter of a context is fixed
+// after its first condensation (the barrier parameter is read from device
+// memory), so one capture per part serves every later iteration.  A capture
+// the driver refuses leaves the context on direct launches.
+template <class Fn>
+ipm_status run_part(ipm_ctx *c, cudaGraphExec_t &gx, long long &gn, Fn fn, cudaStream_t st) {
+  if (!c->opt.graphs || c->prof || st == nullptr || c->graph_failed) {
+    fn();
+    return IPM_OK;
+  }
+  if (!gx) {
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      c->graph_failed = true;
+      fn();
+      return IPM_OK;
+    }
+    const long long n0 = t_ipm_launches;
+    fn();
+    const long long n = t_ipm_launches - n0;
+    g_ipm_launches -= n;  // captured, not launched
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&gx, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || !gx) {
+      cudaGetLastError();
+      gx = nullptr;
+      c->graph_failed = true;
+      fn();
+      return IPM_OK;
+    }
+    gn = n;
+  }
+  CK(cudaGraphLaunch(gx, st));
+  g_ipm_launches += gn;
+  return IPM_OK;
+}
+
+// K_hat contraction of the FP64 branch: partial tiles over ngroups scenario
+// groups (the multi-instance runner may take it over through the hook)
+void fp64_contraction(ipm_ctx *c, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  if (c->gemm_hook) c->gemm_hook(c->gemm_hook_arg, c, st);
+  else launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
+                        c->partial, st);
+}
+
+// split the N*nx contraction rows into G chunks (a multiple of 16 rows each)
+void set_groups(ipm_ctx *c, long long G) {
+  const long long krows = (long long)c->S.N * c->S.nx;
+  G = std::max(1LL, std::min(G, (krows + 15) / 16));
+  long long kc = (krows + G - 1) / G;
+  kc = (kc + 15) / 16 * 16;
+  c->kchunk = kc;
+  c->ngroups = (int)((krows + kc - 1) / kc);
+}
+
+struct Tuned {
+  int zs_threads;
+  long long kchunk;
+  int ngroups, tc_groups;
+};
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, Tuned> g_tune_cache;
+
+// milliseconds of fn on st (events; fn's outputs are overwritten by the caller's next run)
+template <class Fn>
+double time_ms(Fn fn, cudaStream_t st, int reps = 2) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  fn();  // warm
+  cudaEventRecord(a, st);
+  for (int r = 0; r < reps; ++r) fn();
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+// Autotuner: after the first pre-contraction part has run (so LU, J, K hold
+// real values), time the candidate launch shapes of the multi-RHS solves and
+// of the reduced-Hessian contraction and keep the fastest.  Each candidate
+// recomputes the same quantities (the solves are identical for every thread
+// count; the contraction's rounding depends on the group split, and the
+// chosen split is the one run last).
+ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const auto key = std::make_tuple(S.nx, S.nu, S.N, c->mixed ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c->zs_threads = it->second.zs_threads;
+      c->kchunk = it->second.kchunk;
+      c->ngroups = it->second.ngroups;
+      if (c->mixed) {
+        tc_regroup(c->planZY, it->second.tc_groups);
+        tc_regroup(c->planZZ, it->second.tc_groups);
+      }
+      c->tuned = true;
+      return IPM_OK;
+    }
+  }
+  const bool fp64 = !c->mixed;
+  double best = 1e300;
+  int best_thr = 256;
+  for (int thr : {128, 256}) {
+    const double ms = fp64 ? time_ms([&] { launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, thr); }, st)
+                           : time_ms([&] { launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, thr); }, st);
+    c->tune_ms[thr == 128 ? 0 : 1] = ms;
+    if (ms < best) best = ms, best_thr = thr;
+  }
+  c->zs_threads = best_thr;
+  // the solve outputs are identical for every thread count; rerun the winner
+  // so that the mixed planes are split from them below
+  if (fp64) {
+    launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, best_thr);
+  } else {
+    launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, best_thr);
+    launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);
+    launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
+  }
+  int tc_groups = 0;
+  if (fp64) {
+    const long long G0 = std::max(1, (3 * 152) / c->ntiles);
+    long long bestG = G0;
+    best = 1e300;
+    int slot = 2;
+    for (long long G : {G0 / 2, G0, 2 * G0, 4 * G0}) {
+      if (G < 1 || G > c->max_groups) continue;
+      set_groups(c, G);
+      if (c->ngroups > c->max_groups) continue;
+      const double ms = time_ms([&] {
+        launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
+                         c->partial, st);
+      }, st);
+      if (slot < 8) c->tune_ms[slot++] = ms;
+      if (ms < best) best = ms, bestG = G;
+    }
+    set_groups(c, bestG);
+  } else {
+    const int G0 = std::max(1, 152 / c->planZY.ntiles);
+    int bestG = G0;
+    best = 1e300;
+    int slot = 2;
+    for (int G : {G0 / 2, G0, 2 * G0}) {
+      if (G < 1 || G > c->tc_max_groups) continue;
+      tc_regroup(c->planZY, G);
+      const double ms = time_ms([&] { launch_tc_schur(c->planZY, c->tcpart, D.flags, st); }, st);
+      if (slot < 8) c->tune_ms[slot++] = ms;
+      if (ms < best) best = ms, bestG = G;
+    }
+    tc_regroup(c->planZY, bestG);
+    tc_regroup(c->planZZ, bestG);
+    tc_groups = bestG;
+  }
+  CK(cudaGetLastError());
+  c->tuned = true;
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune_cache[key] = Tuned{c->zs_threads, c->kchunk, c->ngroups, tc_groups};
+  return IPM_OK;
+}
+
 // Sigma, K, LU(G_x), Z, Y, K_hat (delta = 0), reduced right-hand side
 ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   if (!c->have_eval) return fail(c, IPM_ERR_STATE, "condense before eval");
   const DevSym &S = c->ds;
   DevWork &D = c->dw;
-  const double mu = c->mu;
-  ph_begin(c, PH_COND, st);
-  launch_sigmas(S, D, st);
-  launch_condense(S, D, st);
-  launch_rhs(S, D, mu, c->gLu, c->HTt_u, st);
-  ph_end(c, PH_COND, st);
-  CK(cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st));
-  ph_begin(c, PH_LU, st);
-  launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st);
-  ph_end(c, PH_LU, st);
-  // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
-  launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
-  if (!c->mixed || c->exact_iter) {
+  const bool fp64 = !c->mixed || c->exact_iter;
+  const int br = fp64 ? 0 : 1;
+  *c->h_mu = c->mu;
+  CK(cudaMemcpyAsync(c->d_mu, c->h_mu, sizeof(double), cudaMemcpyHostToDevice, st));
+  auto pre = [&] {
+    ph_begin(c, PH_COND, st);
+    launch_sigmas(S, D, st);
+    launch_condense(S, D, st);
+    launch_rhs(S, D, c->d_mu, c->gLu, c->HTt_u, st);
+    ph_end(c, PH_COND, st);
+    cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st);
+    ph_begin(c, PH_LU, st);
+    launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st);
+    ph_end(c, PH_LU, st);
+    // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
+    launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
     ph_begin(c, PH_ZSOLVE, st);
-    launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st);
+    if (fp64) {
+      launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads);
+    } else {
+      // mixed: FP32 solves, BF16x3 planes for the tensor-core product
+      launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
+      launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);
+      launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
+    }
     ph_end(c, PH_ZSOLVE, st);
-    ph_begin(c, PH_GEMM, st);
-    launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
-                     c->partial, st);
-    launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
-                         c->Khat, st);
-    ph_end(c, PH_GEMM, st);
-    ph_begin(c, PH_RRHS, st);
-    // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
-    //   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
-    launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
-    launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
-    launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
-    launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
-    launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
-    launch_lincomb(S.nu, c->rhs_u, -1.0, D.rh2, 0.0, nullptr, 0.0, nullptr, st);
-    launch_zt_apply(S, c->Z, c->apos, D.K, c->bpos, -1.0, 1.0, c->rhs_u, c->cpos, st);
+  };
+  auto post = [&] {
+    if (fp64) {
+      launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
+                           c->Khat, st);
+      ph_end(c, PH_GEMM, st);
+      ph_begin(c, PH_RRHS, st);
+      // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
+      //   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
+      launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
+      launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+      launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
+      launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
+      launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
+      launch_lincomb(S.nu, c->rhs_u, -1.0, D.rh2, 0.0, nullptr, 0.0, nullptr, st);
+      launch_zt_apply(S, c->Z, c->apos, D.K, c->bpos, -1.0, 1.0, c->rhs_u, c->cpos, st);
+    } else {
+      launch_tc_assemble(c->planZY, S.N, c->tcpart, c->Yu, c->diag1, c->Khat, st);
+      ph_end(c, PH_GEMM, st);
+      ph_begin(c, PH_RRHS, st);
+      // eq. (11) with FP64 solves: b = G_x^{-1} r3, a = G_x^{-T}(rhat1 - K_xx b)
+      launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
+      launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+      launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
+      launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
+      launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
+      launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+      launch_rhs_reduced(S, D.J, D.K, D.rh2, c->apos, c->bpos, c->rhs_u, st);
+    }
+    ph_end(c, PH_RRHS, st);
+  };
+  if (c->opt.autotune && !c->tuned) {
+    pre();  // direct launches: the tuned shapes must be fixed before a graph is captured
+    TRY(autotune(c, st));
   } else {
-    // mixed: FP32 solves, BF16x3 planes, tcgen05 product; exact FP64 right-hand side
-    ph_begin(c, PH_ZSOLVE, st);
-    launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st);
-    launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);
-    launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
-    ph_end(c, PH_ZSOLVE, st);
-    ph_begin(c, PH_GEMM, st);
-    launch_tc_schur(c->planZY, c->tcpart, D.flags, st);
-    launch_tc_assemble(c->planZY, S.N, c->tcpart, c->Yu, c->diag1, c->Khat, st);
-    ph_end(c, PH_GEMM, st);
-    ph_begin(c, PH_RRHS, st);
-    // eq. (11) with FP64 solves: b = G_x^{-1} r3, a = G_x^{-T}(rhat1 - K_xx b)
-    launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
-    launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
-    launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
-    launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
-    launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
-    launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
-    launch_rhs_reduced(S, D.J, D.K, D.rh2, c->apos, c->bpos, c->rhs_u, st);
+    TRY(run_part(c, c->gx_pre[br], c->gx_pre_n[br], pre, st));
   }
-  ph_end(c, PH_RRHS, st);
+  ph_begin(c, PH_GEMM, st);
+  if (fp64) fp64_contraction(c, st);
+  else launch_tc_schur(c->planZY, c->tcpart, D.flags, st);
+  TRY(run_part(c, c->gx_post[br], c->gx_post_n[br], post, st));
   CK(cudaGetLastError());
   TRY(read_flags(c, st));
   ph_collect(c);
@@ -773,6 +917,77 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
   return ws;
 }
 
+// layout of the warm-start vectors of a context
+ipm_status warm_layout(ipm_ctx *c) {
+  if (c->warm_ready) return IPM_OK;
+  const Sym &S = c->S;
+  std::vector<int> idx;
+  int *seg = c->warm_seg;
+  seg[0] = 0;
+  seg[1] = S.nx;
+  seg[2] = seg[1] + S.nu;
+  seg[3] = seg[2] + S.m;
+  const std::vector<double> *bnd[6] = {&S.xl, &S.xu, &S.ul, &S.uu, &S.sl, &S.su};
+  for (int b = 0; b < 6; ++b) {
+    int cnt = 0;
+    for (size_t j = 0; j < bnd[b]->size(); ++j)
+      if (std::isfinite((*bnd[b])[j])) {
+        idx.push_back((int)j);
+        ++cnt;
+      }
+    seg[4 + b] = seg[3 + b] + cnt;
+  }
+  const int *p = nullptr;
+  TRY(upload(c, &p, idx));
+  c->warm_idx = const_cast<int *>(p);
+  c->warm_ready = true;
+  return IPM_OK;
+}
+
+WarmSeg warm_seg(const ipm_ctx *c) {
+  WarmSeg W;
+  for (int i = 0; i < 10; ++i) W.seg[i] = c->warm_seg[i];
+  W.nx = c->S.nx;
+  W.m = c->S.m;
+  W.idx = c->warm_idx;
+  return W;
+}
+
+// Start from predicted warm-start vectors (ipm_warm_start in include/ipm.h)
+ipm_status do_warm_start(ipm_ctx *c, const float *pred, cudaStream_t st) {
+  TRY(warm_layout(c));
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
+  // bound duals of unbounded components stay zero
+  CK(cudaMemsetAsync(c->state, 0, c->state_len * sizeof(double), st));
+  launch_warm_apply(D, warm_seg(c), S.N, pred, st);
+  // interior point: a push much smaller than the cold start's keeps the prediction
+  launch_push(NX, S.nx, D.x, S.xl, S.xu, K1_WARM, K1_WARM, st);
+  launch_push(S.nu, S.nu, D.u, S.ul, S.uu, K1_WARM, K1_WARM, st);
+  launch_push(NM, S.m, D.s, S.sl, S.su, K1_WARM, K1_WARM, st);
+  launch_warm_z(NM, D, st);
+  // y from the x-stationarity with one transposed solve per scenario
+  launch_functions(S, D.x, D.u, D.P, D.Q, D.g, D.h, D.fs, st);
+  launch_derivatives(S, D, st);
+  CK(cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st));
+  launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st);
+  launch_warm_yrhs(S, D, c->kpx, st);
+  launch_gather_pos(S.N, S.nx, S.iperm, c->kpx, c->apos, 1.0, st);
+  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+  launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, D.y, -1.0, st);
+  CK(cudaGetLastError());
+  TRY(read_flags(c, st));
+  if (c->h_flags[FLAG_SINGULAR]) return fail(c, IPM_ERR_SINGULAR_GX, "singular G_x at the warm-start point");
+  c->have_eval = c->have_cond = c->have_fact = false;
+  TRY(do_eval(c, st));
+  TRY(do_errors(c, st));
+  c->mu = std::max(1e-6, c->mean_compl);
+  c->rho = RHO0;
+  c->delta_last = 0.0;
+  return write_scalars(c, st);
+}
+
 bool finite_nonneg(const double *p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(p[i]) || p[i] < 0) return false;
@@ -791,7 +1006,9 @@ ipm_status ipm_default_options(ipm_options *opt) {
   opt->max_iter = 200;
   opt->precision = IPM_PREC_FP64;
   opt->max_refine = 25;
-  opt->panel = 0;
+  opt->solve_threads = 0;
+  opt->graphs = 0;
+  opt->autotune = 0;
   opt->barrier_rule = IPM_BARRIER_ADAPTIVE;
   opt->sigma = 0.1;
   return IPM_OK;
@@ -815,6 +1032,8 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
   else ipm_default_options(&c->opt);
   if ((c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || !(c->opt.tol > 0) ||
       c->opt.max_iter < 0 || c->opt.max_refine < 0 ||
+      (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
+      (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
       (c->opt.barrier_rule == IPM_BARRIER_ADAPTIVE && !(c->opt.sigma > 0 && c->opt.sigma < 1))) {
     delete c;
     return IPM_ERR_ARG;
@@ -855,6 +1074,11 @@ ipm_status ipm_destroy(ipm_ctx *c) {
   for (void *p : c->allocs) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->h_flags) cudaFreeHost(c->h_flags);
+  if (c->h_mu) cudaFreeHost(c->h_mu);
+  for (int b = 0; b < 2; ++b) {
+    if (c->gx_pre[b]) cudaGraphExecDestroy(c->gx_pre[b]);
+    if (c->gx_post[b]) cudaGraphExecDestroy(c->gx_post[b]);
+  }
   delete c;
   return IPM_OK;
 }
@@ -1108,6 +1332,44 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
     return IPM_OK;
   }
   return IPM_ERR_ARG;
+}
+
+ipm_status ipm_set_loads(ipm_ctx *c, const double *pd, const double *qd, void *stream) {
+  if (!c || !pd || !qd) return IPM_ERR_ARG;
+  const size_t nl = (size_t)c->S.N * c->S.n;
+  if (!finite_nonneg(pd, nl)) return IPM_ERR_ARG;
+  for (size_t i = 0; i < nl; ++i)
+    if (!std::isfinite(qd[i])) return IPM_ERR_ARG;
+  cudaStream_t st = STR(stream);
+  CK(cudaMemcpyAsync(const_cast<double *>(c->ds.pd), pd, nl * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<double *>(c->ds.qd), qd, nl * sizeof(double), cudaMemcpyHostToDevice, st));
+  return do_init(c, st);
+}
+
+ipm_status ipm_warm_dim(const ipm_ctx *c, int *d) {
+  if (!c || !d) return IPM_ERR_ARG;
+  const Sym &S = c->S;
+  int n = S.nx + S.nu + S.m;
+  const std::vector<double> *bnd[6] = {&S.xl, &S.xu, &S.ul, &S.uu, &S.sl, &S.su};
+  for (auto *b : bnd)
+    for (double v : *b) n += std::isfinite(v) ? 1 : 0;
+  *d = n;
+  return IPM_OK;
+}
+
+ipm_status ipm_warm_target(ipm_ctx *c, float *out, void *stream) {
+  if (!c || !out) return IPM_ERR_ARG;
+  cudaStream_t st = STR(stream);
+  TRY(warm_layout(c));
+  launch_warm_target(c->dw, warm_seg(c), c->S.N, out, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return IPM_OK;
+}
+
+ipm_status ipm_warm_start(ipm_ctx *c, const float *pred, void *stream) {
+  if (!c || !pred) return IPM_ERR_ARG;
+  return do_warm_start(c, pred, STR(stream));
 }
 
 ipm_status ipm_set_profiling(ipm_ctx *c, int on) {

@@ -1,6 +1,16 @@
 // Host-side launch wrappers of the CUDA kernels (internal).
 #pragma once
+#include <atomic>
+
 #include "dev.cuh"
+
+// kernels launched by this library: all threads, and the calling thread
+extern std::atomic<long long> g_ipm_launches;
+extern thread_local long long t_ipm_launches;
+inline void ipm_count_launch() {
+  ++g_ipm_launches;
+  ++t_ipm_launches;
+}
 
 // kernels_eval.cu
 void launch_functions(const DevSym &S, const double *x, const double *u, double *P, double *Q, double *g,
@@ -8,22 +18,33 @@ void launch_functions(const DevSym &S, const double *x, const double *u, double 
 void launch_derivatives(const DevSym &S, DevWork &D, cudaStream_t st);
 void launch_sigmas(const DevSym &S, DevWork &D, cudaStream_t st);
 void launch_condense(const DevSym &S, DevWork &D, cudaStream_t st);
-void launch_rhs(const DevSym &S, DevWork &D, double mu, double *gLu, double *HTt_u, cudaStream_t st);
+// mu: device pointer to the barrier parameter (read when the kernels run, so
+// that a captured graph of the condensation follows the current value)
+void launch_rhs(const DevSym &S, DevWork &D, const double *mu, double *gLu, double *HTt_u, cudaStream_t st);
 void launch_ugrad(const DevSym &S, DevWork &D, double *gLu, cudaStream_t st);
 
 // kernels_lu.cu
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
                       cudaStream_t st);
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
-                     double *Z, double *Y, double *Yu, cudaStream_t st);
+                     double *Z, double *Y, double *Yu, cudaStream_t st, int threads = 256);
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
-                     float *Z, float *Y, double *Yu, cudaStream_t st);
+                     float *Z, float *Y, double *Yu, cudaStream_t st, int threads = 256);
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st);
 
 // kernels_dense.cu
 void launch_gemm_tn64(long long krows, long long kc, int nu, int ngroups, const double *A, const double *B,
                       const int2 *tiles, int ntiles, double *partial, cudaStream_t st);
+// one work item of the grouped multi-instance contraction: the 64 x 64 tile at
+// (i0, j0) of A^T B over rows [r0, r1), written to P
+struct GemmItem {
+  const double *A, *B;
+  double *P;
+  long long r0, r1;
+  int nu, i0, j0, pad;
+};
+void launch_gemm_grouped(const GemmItem *items, int nitems, int *counter, cudaStream_t st);
 void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const double *partial,
                           const int *tile_of, const double *Yu, const double *diag, double *Khat,
                           cudaStream_t st);
@@ -77,6 +98,18 @@ void launch_init_primal(const DevSym &S, double *x, double *u, const double *pma
 void launch_fill_bound_duals(long long n, int period, const double *l, const double *b, double *zl,
                              double *zu, cudaStream_t st);
 
+// warm-start vectors: segment offsets (seg[0] = 0 ... seg[9] = d) and the
+// bounded-component lists of the six dual blocks (device, concatenated)
+struct WarmSeg {
+  int seg[10];
+  int nx, m;
+  const int *idx;
+};
+void launch_warm_target(const DevWork &D, const WarmSeg &W, int N, float *out, cudaStream_t st);
+void launch_warm_apply(const DevWork &D, const WarmSeg &W, int N, const float *pred, cudaStream_t st);
+void launch_warm_z(long long n, const DevWork &D, cudaStream_t st);
+void launch_warm_yrhs(const DevSym &S, const DevWork &D, double *r, cudaStream_t st);
+
 // kernels_tc.cu (tcgen05 BF16x3 reduced-Hessian product)
 struct TcPlan {
   int nu = 0, nt1 = 0, ntiles = 0, kb_total = 0, kb_per_group = 0, ngroups = 0;
@@ -84,8 +117,13 @@ struct TcPlan {
   alignas(64) unsigned char maps[6 * 128];  // six CUtensorMap (A planes, B planes)
 };
 void tc_plan(int nu, long long krows, TcPlan &P);
+// tensor map (128 bytes at map) of a BF16 matrix [rows][k] (k contiguous, k a
+// multiple of 8), box 64 (k) x 128 (rows), 128-byte swizzle
+bool tc_make_kmajor_map(void *map, const void *base, int rows, long long k);
 bool tc_set_operands(TcPlan &P, const void *a_planes, const void *b_planes);
 void launch_split_t(long long krows, int nu, long long kpad, const float *src, void *planes, cudaStream_t st);
 void launch_tc_schur(const TcPlan &P, double *partial, int *flags, cudaStream_t st);
+// re-split the K range of a plan into about `groups` scenario groups
+void tc_regroup(TcPlan &P, int groups);
 void launch_tc_assemble(const TcPlan &P, int N, const double *partial, const double *Yu, const double *diag,
                         double *Khat, cudaStream_t st);

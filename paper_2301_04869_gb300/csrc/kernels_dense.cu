@@ -8,64 +8,92 @@
 // pairs.  CTAs split that range into fixed groups of scenarios and write
 // partial tiles; one pass then adds the groups in index order (deterministic).
 // Only upper tiles (i <= j) are computed; the symmetric result is mirrored.
+#include <atomic>
+
 #include "dev.cuh"
 #include "kernels.h"
 
-extern long long g_ipm_launches;
 
 namespace {
 
 constexpr int TB = 64;   // output tile
 constexpr int TK = 16;   // k chunk
 
-// partial[g][tile t][64*64] = A^T B on tile t over the rows [g*kc, (g+1)*kc) of
-// the (N*nx) x nu matrices A, B (scenario-major storage makes the scenario
-// sum one contraction over the concatenated rows)
-__global__ void __launch_bounds__(256) k_gemm_tn64(long long krows, long long kc, int nu,
-                                                   const double *__restrict__ A,
-                                                   const double *__restrict__ B,
-                                                   const int2 *__restrict__ tiles, double *partial) {
-  __shared__ double As[TK][TB];
-  __shared__ double Bs[TK][TB];
-  const int t = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
-  const int i0 = tiles[t].x * TB, j0 = tiles[t].y * TB;
+// One 64 x 64 tile of A^T B over the rows [r0, r1) of the (rows x nu)
+// matrices A, B (scenario-major storage makes the scenario sum one
+// contraction over the concatenated rows); the tile goes to P (row-major).
+__device__ __forceinline__ void tile_tn64(long long r0, long long r1, int nu, int i0, int j0,
+                                          const double *__restrict__ A, const double *__restrict__ B,
+                                          double *P, double (*As)[TB], double (*Bs)[TB]) {
+  const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  const long long r0 = (long long)g * kc, r1 = min(krows, r0 + kc);
-  {
-    for (long long k0 = r0; k0 < r1; k0 += TK) {
+  for (long long k0 = r0; k0 < r1; k0 += TK) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = tid + q * 256, kk = e >> 6, cc = e & 63;
-        const long long k = k0 + kk;
-        As[kk][cc] = (k < r1 && i0 + cc < nu) ? A[k * nu + i0 + cc] : 0.0;
-        Bs[kk][cc] = (k < r1 && j0 + cc < nu) ? B[k * nu + j0 + cc] : 0.0;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < TK; ++kk) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
-      }
-      __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256, kk = e >> 6, cc = e & 63;
+      const long long k = k0 + kk;
+      As[kk][cc] = (k < r1 && i0 + cc < nu) ? A[k * nu + i0 + cc] : 0.0;
+      Bs[kk][cc] = (k < r1 && j0 + cc < nu) ? B[k * nu + j0 + cc] : 0.0;
     }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
   }
-  double *P = partial + ((size_t)g * gridDim.x + t) * TB * TB;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) P[(ty * 4 + a) * TB + tx * 4 + b] = acc[a][b];
+}
+
+// partial[g][tile t][64*64] = A^T B on tile t over the rows [g*kc, (g+1)*kc)
+__global__ void __launch_bounds__(256) k_gemm_tn64(long long krows, long long kc, int nu,
+                                                   const double *__restrict__ A,
+                                                   const double *__restrict__ B,
+                                                   const int2 *__restrict__ tiles, double *partial) {
+  __shared__ double As[TK][TB];
+  __shared__ double Bs[TK][TB];
+  const int t = blockIdx.x, g = blockIdx.y;
+  const long long r0 = (long long)g * kc, r1 = min(krows, r0 + kc);
+  tile_tn64(r0, r1, nu, tiles[t].x * TB, tiles[t].y * TB, A, B,
+            partial + ((size_t)g * gridDim.x + t) * TB * TB, As, Bs);
+}
+
+// The same contraction for many independent instances in one persistent
+// launch: every (instance, tile, scenario group) is a work item; CTAs take
+// items from an atomic counter (items are sorted by decreasing length, so
+// the long ones start first).  Each item writes the partial tile that the
+// instance's own launch would write, so the result does not depend on which
+// CTA ran it.
+__global__ void __launch_bounds__(256) k_gemm_grouped(const GemmItem *__restrict__ items, int nitems,
+                                                      int *counter) {
+  __shared__ double As[TK][TB];
+  __shared__ double Bs[TK][TB];
+  __shared__ int w;
+  for (;;) {
+    if (threadIdx.x == 0) w = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = w;
+    __syncthreads();
+    if (it >= nitems) break;
+    const GemmItem g = items[it];
+    tile_tn64(g.r0, g.r1, g.nu, g.i0, g.j0, g.A, g.B, g.P, As, Bs);
+  }
 }
 
 // K_hat[i][j] = K_hat[j][i] = sum_g partial + sum_s Yu[s][i][j] + diag  (i <= j)
@@ -210,35 +238,52 @@ __global__ void k_chol_solve(int n, const double *L, double *b) {
 void launch_gemm_tn64(long long krows, long long kc, int nu, int ngroups, const double *A, const double *B,
                       const int2 *tiles, int ntiles, double *partial, cudaStream_t st) {
   dim3 grid(ntiles, ngroups);
-  k_gemm_tn64<<<grid, 256, 0, st>>>(krows, kc, nu, A, B, tiles, partial); ++g_ipm_launches;
+  k_gemm_tn64<<<grid, 256, 0, st>>>(krows, kc, nu, A, B, tiles, partial); ipm_count_launch();
 }
+void launch_gemm_grouped(const GemmItem *items, int nitems, int *counter, cudaStream_t st) {
+  static const int ctas = [] {
+    int per_sm = 0, dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_grouped, 256, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    return sms * per_sm;
+  }();
+  cudaMemsetAsync(counter, 0, sizeof(int), st);
+  const int grid = nitems < ctas ? nitems : ctas;
+  if (grid > 0) {
+    k_gemm_grouped<<<grid, 256, 0, st>>>(items, nitems, counter);
+    ipm_count_launch();
+  }
+}
+
 void launch_khat_assemble(int nu, int N, int ngroups, int ntiles, int nt1, const double *partial,
                           const int *tile_of, const double *Yu, const double *diag, double *Khat,
                           cudaStream_t st) {
   long long tot = (long long)nu * nu;
   k_khat_assemble<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, N, ngroups, ntiles, nt1, partial,
-                                                             tile_of, Yu, diag, Khat); ++g_ipm_launches;
+                                                             tile_of, Yu, diag, Khat); ipm_count_launch();
 }
 void launch_shift(int nu, const double *Khat, const double *M, double delta, double tau, double *F,
                   cudaStream_t st) {
   long long tot = (long long)nu * nu;
-  k_shift<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, Khat, M, delta, tau, F); ++g_ipm_launches;
+  k_shift<<<(int)((tot + 255) / 256), 256, 0, st>>>(nu, Khat, M, delta, tau, F); ipm_count_launch();
 }
 void launch_maxdiag(int n, const double *A, double *out, cudaStream_t st) {
-  k_maxdiag<<<1, 256, 0, st>>>(n, A, out); ++g_ipm_launches;
+  k_maxdiag<<<1, 256, 0, st>>>(n, A, out); ipm_count_launch();
 }
 void launch_cholesky(int n, double *A, int *flags, cudaStream_t st) {
   for (int k0 = 0; k0 < n; k0 += CB) {
-    k_potrf_diag<<<1, 256, 0, st>>>(n, k0, A, flags); ++g_ipm_launches;
+    k_potrf_diag<<<1, 256, 0, st>>>(n, k0, A, flags); ipm_count_launch();
     const int nb = n - k0 < CB ? n - k0 : CB;
     const int rest = n - k0 - nb;
     if (rest > 0) {
-      k_trsm_panel<<<(rest + 127) / 128, 128, 0, st>>>(n, k0, A); ++g_ipm_launches;
+      k_trsm_panel<<<(rest + 127) / 128, 128, 0, st>>>(n, k0, A); ipm_count_launch();
       const int nt = (rest + CB - 1) / CB;
-      k_syrk_trail<<<dim3(nt, nt), 256, 0, st>>>(n, k0, A); ++g_ipm_launches;
+      k_syrk_trail<<<dim3(nt, nt), 256, 0, st>>>(n, k0, A); ipm_count_launch();
     }
   }
 }
 void launch_chol_solve(int n, const double *L, double *b, cudaStream_t st) {
-  k_chol_solve<<<1, 1024, 0, st>>>(n, L, b); ++g_ipm_launches;
+  k_chol_solve<<<1, 1024, 0, st>>>(n, L, b); ipm_count_launch();
 }

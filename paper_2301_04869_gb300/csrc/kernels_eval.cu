@@ -9,10 +9,11 @@
 // to the injections of its bus; derivatives below are those of these two
 // closed forms (the CPU oracle instead differentiates S = V conj(Y V) in
 // complex-matrix form).
+#include <atomic>
+
 #include "dev.cuh"
 #include "kernels.h"
 
-extern long long g_ipm_launches;
 
 namespace {
 
@@ -217,7 +218,8 @@ __global__ void k_condense(DevSym S, DevWork D) {
 }
 
 // slack rows: r2 = z - mu/(s-l) + mu/(b-s); r4 = h + s; t = Sigma_s r4 - r2
-__global__ void k_rhs_s(DevSym S, DevWork D, double mu) {
+__global__ void k_rhs_s(DevSym S, DevWork D, const double *mu_d) {
+  const double mu = *mu_d;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= S.N * S.m) return;
   const int j = t % S.m;
@@ -240,7 +242,8 @@ __device__ __forceinline__ double HT_at(const DevSym &S, const double *J, const 
 }
 
 // x rows: r1_x = grad f + G^T y + H^T z + barrier gradient; rhat1 = r1_x + H_x^T t
-__global__ void k_rhs_x(DevSym S, DevWork D, double mu) {
+__global__ void k_rhs_x(DevSym S, DevWork D, const double *mu_d) {
+  const double mu = *mu_d;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= S.N * S.nx) return;
   const int sc = t / S.nx, j = t - sc * S.nx;
@@ -272,7 +275,8 @@ __global__ void k_ugrad(DevSym S, DevWork D, double *gLu, double *HTt_u) {
   if (HTt_u) HTt_u[j] = acc2;
 }
 
-__global__ void k_rhs_u(DevSym S, DevWork D, const double *gLu, const double *HTt_u, double mu) {
+__global__ void k_rhs_u(DevSym S, DevWork D, const double *gLu, const double *HTt_u, const double *mu_d) {
+  const double mu = *mu_d;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= S.nu) return;
   const double r1 = gLu[j] + bgrad_of(D.u[j], S.ul[j], S.uu[j], mu);
@@ -287,24 +291,24 @@ static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
 void launch_functions(const DevSym &S, const double *x, const double *u, double *P, double *Q,
                       double *g, double *h, double *fs, cudaStream_t st) {
-  k_functions<<<nblk((long long)S.n * S.N, 128), 128, 0, st>>>(S, x, u, P, Q, g, h, fs); ++g_ipm_launches;
+  k_functions<<<nblk((long long)S.n * S.N, 128), 128, 0, st>>>(S, x, u, P, Q, g, h, fs); ipm_count_launch();
 }
 void launch_derivatives(const DevSym &S, DevWork &D, cudaStream_t st) {
-  k_derivatives<<<nblk((long long)S.n * S.N, 128), 128, 0, st>>>(S, D.x, D.u, D.y, D.z, D.h, D.J, D.W, D.JTl); ++g_ipm_launches;
+  k_derivatives<<<nblk((long long)S.n * S.N, 128), 128, 0, st>>>(S, D.x, D.u, D.y, D.z, D.h, D.J, D.W, D.JTl); ipm_count_launch();
 }
 void launch_sigmas(const DevSym &S, DevWork &D, cudaStream_t st) {
   long long tot = (long long)S.N * S.nx + (long long)S.N * S.m + S.nu;
-  k_sigmas<<<nblk(tot, 256), 256, 0, st>>>(S, D); ++g_ipm_launches;
+  k_sigmas<<<nblk(tot, 256), 256, 0, st>>>(S, D); ipm_count_launch();
 }
 void launch_condense(const DevSym &S, DevWork &D, cudaStream_t st) {
-  k_condense<<<nblk((long long)S.nnzKB * S.N, 128), 128, 0, st>>>(S, D); ++g_ipm_launches;
+  k_condense<<<nblk((long long)S.nnzKB * S.N, 128), 128, 0, st>>>(S, D); ipm_count_launch();
 }
-void launch_rhs(const DevSym &S, DevWork &D, double mu, double *gLu, double *HTt_u, cudaStream_t st) {
-  k_rhs_s<<<nblk((long long)S.N * S.m, 256), 256, 0, st>>>(S, D, mu); ++g_ipm_launches;
-  k_rhs_x<<<nblk((long long)S.N * S.nx, 256), 256, 0, st>>>(S, D, mu); ++g_ipm_launches;
-  k_ugrad<<<nblk(S.nu, 64), 64, 0, st>>>(S, D, gLu, HTt_u); ++g_ipm_launches;
-  k_rhs_u<<<nblk(S.nu, 64), 64, 0, st>>>(S, D, gLu, HTt_u, mu); ++g_ipm_launches;
+void launch_rhs(const DevSym &S, DevWork &D, const double *mu, double *gLu, double *HTt_u, cudaStream_t st) {
+  k_rhs_s<<<nblk((long long)S.N * S.m, 256), 256, 0, st>>>(S, D, mu); ipm_count_launch();
+  k_rhs_x<<<nblk((long long)S.N * S.nx, 256), 256, 0, st>>>(S, D, mu); ipm_count_launch();
+  k_ugrad<<<nblk(S.nu, 64), 64, 0, st>>>(S, D, gLu, HTt_u); ipm_count_launch();
+  k_rhs_u<<<nblk(S.nu, 64), 64, 0, st>>>(S, D, gLu, HTt_u, mu); ipm_count_launch();
 }
 void launch_ugrad(const DevSym &S, DevWork &D, double *gLu, cudaStream_t st) {
-  k_ugrad<<<nblk(S.nu, 64), 64, 0, st>>>(S, D, gLu, nullptr); ++g_ipm_launches;
+  k_ugrad<<<nblk(S.nu, 64), 64, 0, st>>>(S, D, gLu, nullptr); ipm_count_launch();
 }

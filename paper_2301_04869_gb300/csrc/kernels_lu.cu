@@ -11,10 +11,11 @@
 // (scenario, RHS panel) pair (multi-RHS solves) and walks the level schedule
 // of the shared pattern with __syncthreads() between levels; no grid-wide
 // synchronisation and no inter-CTA waits.
+#include <atomic>
+
 #include "dev.cuh"
 #include "kernels.h"
 
-extern long long g_ipm_launches;
 
 namespace {
 
@@ -329,30 +330,30 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
   const int ns = S.nd < 160 ? S.nd : 160;
   const size_t smem = (size_t)ns * ns * sizeof(double);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_lu_factor<<<S.N, 512, smem, st>>>(S, nL, J, LU, rd, flags, 1e-14, ns); ++g_ipm_launches;
+  k_lu_factor<<<S.N, 512, smem, st>>>(S, nL, J, LU, rd, flags, 1e-14, ns); ipm_count_launch();
 }
 static int zsolve_smem_ok(const DevSym &S, size_t elem) {
   return (S.nd > 0 && (size_t)S.nd * 32 * elem <= 100 * 1024) ? 1 : 0;
 }
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J,
-                     const double *K, double *Z, double *Y, double *Yu, cudaStream_t st) {
+                     const double *K, double *Z, double *Y, double *Yu, cudaStream_t st, int threads) {
   dim3 grid((S.nu + 31) / 32, S.N);
   const int sm = zsolve_smem_ok(S, sizeof(double));
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(double) : 0;
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k_zsolve64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_zsolve64<<<grid, 256, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ++g_ipm_launches;
+  k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
 }
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
-                     const double *K, float *Z, float *Y, double *Yu, cudaStream_t st) {
+                     const double *K, float *Z, float *Y, double *Yu, cudaStream_t st, int threads) {
   dim3 grid((S.nu + 31) / 32, S.N);
   const int sm = zsolve_smem_ok(S, sizeof(float));
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(float) : 0;
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k_zsolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_zsolve32<<<grid, 256, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ++g_ipm_launches;
+  k_zsolve32<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
 }
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st) {
   const size_t bytes = (size_t)S.nd * sizeof(double);
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans); ++g_ipm_launches;
+  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans); ipm_count_launch();
 }

@@ -4,10 +4,11 @@
 //
 // All reductions run on a fixed grid with a fixed assignment of indices to
 // threads and a fixed combination tree, so repeated runs give identical bits.
+#include <atomic>
+
 #include "dev.cuh"
 #include "kernels.h"
 
-extern long long g_ipm_launches;
 
 namespace {
 
@@ -59,8 +60,8 @@ __global__ void k_reduce_final(int nb, const double *partial, double *out) {
 
 template <class F>
 void run_reduce(const F &f, long long n, double *partial, double *out, cudaStream_t st) {
-  k_reduce<F><<<RED_BLOCKS, 256, 0, st>>>(f, n, partial); ++g_ipm_launches;
-  k_reduce_final<F><<<1, 32, 0, st>>>(RED_BLOCKS, partial, out); ++g_ipm_launches;
+  k_reduce<F><<<RED_BLOCKS, 256, 0, st>>>(f, n, partial); ipm_count_launch();
+  k_reduce_final<F><<<1, 32, 0, st>>>(RED_BLOCKS, partial, out); ipm_count_launch();
 }
 
 __device__ __forceinline__ double bgrad(double w, double l, double b, double mu) {
@@ -533,75 +534,188 @@ void launch_ftb(const DevSym &S, DevWork &D, const double *px, const double *pu,
 }
 void launch_gather_pos(int N, int nx, const int *iperm, const double *src, double *dst, double scale,
                        cudaStream_t st) {
-  k_gather_pos<<<nblk((long long)N * nx, 256), 256, 0, st>>>(N, nx, iperm, src, dst, scale); ++g_ipm_launches;
+  k_gather_pos<<<nblk((long long)N * nx, 256), 256, 0, st>>>(N, nx, iperm, src, dst, scale); ipm_count_launch();
 }
 void launch_scatter_pos(int N, int nx, const int *iperm, const double *src, double *dst, double scale,
                         cudaStream_t st) {
-  k_scatter_pos<<<nblk((long long)N * nx, 256), 256, 0, st>>>(N, nx, iperm, src, dst, scale); ++g_ipm_launches;
+  k_scatter_pos<<<nblk((long long)N * nx, 256), 256, 0, st>>>(N, nx, iperm, src, dst, scale); ipm_count_launch();
 }
 void launch_gu_apply(const DevSym &S, const double *J, const double *pu, double *v, cudaStream_t st) {
-  k_gu_apply<<<nblk((long long)S.N * S.nx, 256), 256, 0, st>>>(S, J, pu, v); ++g_ipm_launches;
+  k_gu_apply<<<nblk((long long)S.N * S.nx, 256), 256, 0, st>>>(S, J, pu, v); ipm_count_launch();
 }
 void launch_kapply(const DevSym &S, const double *K, const double *px_pos, const double *pu, double *kpx,
                    double *kpu, cudaStream_t st) {
   long long n = (long long)S.N * S.nx + (kpu ? (long long)S.N * S.nu : 0);
-  k_kapply<<<nblk(n, 256), 256, 0, st>>>(S, K, px_pos, pu, kpx, kpu); ++g_ipm_launches;
+  k_kapply<<<nblk(n, 256), 256, 0, st>>>(S, K, px_pos, pu, kpx, kpu); ipm_count_launch();
 }
 void launch_lincomb(long long n, double *out, double a, const double *x, double b, const double *y,
                     double c, const double *z, cudaStream_t st) {
   if (n <= 0) return;
-  k_lincomb<<<nblk(n, 256), 256, 0, st>>>(n, out, a, x, b, y, c, z); ++g_ipm_launches;
+  k_lincomb<<<nblk(n, 256), 256, 0, st>>>(n, out, a, x, b, y, c, z); ipm_count_launch();
 }
 void launch_rhs_reduced(const DevSym &S, const double *J, const double *K, const double *rh2,
                         const double *a, const double *b, double *rhs, cudaStream_t st) {
-  k_rhs_reduced<<<nblk(S.nu, 64), 64, 0, st>>>(S, J, K, rh2, a, b, rhs); ++g_ipm_launches;
+  k_rhs_reduced<<<nblk(S.nu, 64), 64, 0, st>>>(S, J, K, rh2, a, b, rhs); ipm_count_launch();
 }
 void launch_zt_apply(const DevSym &S, const double *Z, const double *w, const double *K, const double *b,
                      double alpha, double beta, double *out, double *part, cudaStream_t st) {
-  k_zt_part<<<nblk((long long)S.N * S.nu, 128), 128, 0, st>>>(S, Z, w, part); ++g_ipm_launches;
-  k_zt_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, part, K, b, alpha, beta, out); ++g_ipm_launches;
+  k_zt_part<<<nblk((long long)S.N * S.nu, 128), 128, 0, st>>>(S, Z, w, part); ipm_count_launch();
+  k_zt_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, part, K, b, alpha, beta, out); ipm_count_launch();
 }
 void launch_z_apply(const DevSym &S, const double *Z, const double *pu, double a, double *v, cudaStream_t st) {
-  k_z_apply<<<nblk((long long)S.N * S.nx * 32, 256), 256, 0, st>>>(S, Z, pu, a, v); ++g_ipm_launches;
+  k_z_apply<<<nblk((long long)S.N * S.nx * 32, 256), 256, 0, st>>>(S, Z, pu, a, v); ipm_count_launch();
 }
 void launch_gut_sum(const DevSym &S, const double *J, const double *a, double scale, double *out,
                     cudaStream_t st) {
-  k_gut_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, J, a, scale, out); ++g_ipm_launches;
+  k_gut_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, J, a, scale, out); ipm_count_launch();
 }
 void launch_apply_finish(const DevSym &S, const double *kpu, const double *diag, double delta, const double *v,
                          double *out, cudaStream_t st) {
-  k_apply_finish<<<nblk(S.nu, 128), 128, 0, st>>>(S, kpu, diag, delta, v, out); ++g_ipm_launches;
+  k_apply_finish<<<nblk(S.nu, 128), 128, 0, st>>>(S, kpu, diag, delta, v, out); ipm_count_launch();
 }
 void launch_dot2(int n, const double *a, const double *b, const double *c, const double *d, double *out,
                  cudaStream_t st) {
-  k_dot2<<<1, 256, 0, st>>>(n, a, b, c, d, out); ++g_ipm_launches;
+  k_dot2<<<1, 256, 0, st>>>(n, a, b, c, d, out); ipm_count_launch();
 }
 void launch_pz_ps(const DevSym &S, DevWork &D, const double *px, const double *pu, double *Hp, double *pz,
                   double *ps, cudaStream_t st) {
-  k_pz_ps<<<nblk((long long)S.N * S.m, 128), 128, 0, st>>>(S, D, px, pu, Hp, pz, ps); ++g_ipm_launches;
+  k_pz_ps<<<nblk((long long)S.N * S.m, 128), 128, 0, st>>>(S, D, px, pu, Hp, pz, ps); ipm_count_launch();
 }
 void launch_bound_steps(long long n, int period, const double *w, const double *dw, const double *l,
                         const double *b, const double *zl, const double *zu, double mu, double *dzl,
                         double *dzu, cudaStream_t st) {
   if (n <= 0) return;
-  k_bound_steps<<<nblk(n, 256), 256, 0, st>>>(n, period, w, dw, l, b, zl, zu, mu, dzl, dzu); ++g_ipm_launches;
+  k_bound_steps<<<nblk(n, 256), 256, 0, st>>>(n, period, w, dw, l, b, zl, zu, mu, dzl, dzu); ipm_count_launch();
 }
 void launch_dual_update(long long n, int period, const double *w, const double *l, const double *b,
                         double *zl, double *zu, const double *dzl, const double *dzu, double az, double mu,
                         double ks, cudaStream_t st) {
   if (n <= 0) return;
-  k_dual_update<<<nblk(n, 256), 256, 0, st>>>(n, period, w, l, b, zl, zu, dzl, dzu, az, mu, ks); ++g_ipm_launches;
+  k_dual_update<<<nblk(n, 256), 256, 0, st>>>(n, period, w, l, b, zl, zu, dzl, dzu, az, mu, ks); ipm_count_launch();
 }
 void launch_push(long long n, int period, double *w, const double *l, const double *b, double k1, double k2,
                  cudaStream_t st) {
   if (n <= 0) return;
-  k_push<<<nblk(n, 256), 256, 0, st>>>(n, period, w, l, b, k1, k2); ++g_ipm_launches;
+  k_push<<<nblk(n, 256), 256, 0, st>>>(n, period, w, l, b, k1, k2); ipm_count_launch();
 }
 void launch_init_primal(const DevSym &S, double *x, double *u, const double *pmax, cudaStream_t st) {
-  k_init_primal<<<nblk((long long)S.N * S.nx + S.nu, 256), 256, 0, st>>>(S, x, u, pmax); ++g_ipm_launches;
+  k_init_primal<<<nblk((long long)S.N * S.nx + S.nu, 256), 256, 0, st>>>(S, x, u, pmax); ipm_count_launch();
 }
 void launch_fill_bound_duals(long long n, int period, const double *l, const double *b, double *zl, double *zu,
                              cudaStream_t st) {
   if (n <= 0) return;
-  k_fill_bound_duals<<<nblk(n, 256), 256, 0, st>>>(n, period, l, b, zl, zu); ++g_ipm_launches;
+  k_fill_bound_duals<<<nblk(n, 256), 256, 0, st>>>(n, period, l, b, zl, zu); ipm_count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Warm-start vectors (learned warm start).  Per scenario, d = seg[8]:
+//   [0, seg1) x | [seg1, seg2) u | [seg2, seg3) s | [seg3, seg4) log zl_x |
+//   [seg4, seg5) log zu_x | [seg5, seg6) log zl_u | [seg6, seg7) log zu_u |
+//   [seg7, seg8) log zl_s | [seg8, seg9) log zu_s
+// idx lists the bounded components of each dual block, concatenated.
+namespace {
+
+__device__ __forceinline__ const double *warm_dual_src(const DevWork &D, int b, int sc, const WarmSeg &W, int i,
+                                                       int &off) {
+  const int k = W.idx[W.seg[3 + b] - W.seg[3] + i];
+  switch (b) {
+    case 0: off = sc * W.nx + k; return D.zlx;
+    case 1: off = sc * W.nx + k; return D.zux;
+    case 2: off = k; return D.zlu;
+    case 3: off = k; return D.zuu;
+    case 4: off = sc * W.m + k; return D.zls;
+    default: off = sc * W.m + k; return D.zus;
+  }
+}
+
+__global__ void k_warm_target(DevWork D, WarmSeg W, int N, float *out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int d = W.seg[9];
+  if (t >= (long long)N * d) return;
+  const int sc = (int)(t / d), k = (int)(t - (long long)sc * d);
+  double v;
+  if (k < W.seg[1]) v = D.x[(size_t)sc * W.nx + k];
+  else if (k < W.seg[2]) v = D.u[k - W.seg[1]];
+  else if (k < W.seg[3]) v = D.s[(size_t)sc * W.m + k - W.seg[2]];
+  else {
+    int b = 0;
+    while (k >= W.seg[4 + b]) ++b;
+    int off = 0;
+    const double *src = warm_dual_src(D, b, sc, W, k - W.seg[3 + b], off);
+    v = log(fmax(src[off], 1e-30));
+  }
+  out[t] = (float)v;
+}
+
+// primal rows and bound duals of each scenario (u and its duals: next kernel)
+__global__ void k_warm_apply(DevWork D, WarmSeg W, int N, const float *pred) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int d = W.seg[9];
+  if (t >= (long long)N * d) return;
+  const int sc = (int)(t / d), k = (int)(t - (long long)sc * d);
+  const double v = pred[t];
+  if (k < W.seg[1]) D.x[(size_t)sc * W.nx + k] = v;
+  else if (k < W.seg[2]) return;
+  else if (k < W.seg[3]) D.s[(size_t)sc * W.m + k - W.seg[2]] = v;
+  else {
+    int b = 0;
+    while (k >= W.seg[4 + b]) ++b;
+    if (b == 2 || b == 3) return;
+    int off = 0;
+    double *dst = const_cast<double *>(warm_dual_src(D, b, sc, W, k - W.seg[3 + b], off));
+    dst[off] = exp(fmin(fmax(v, -27.631021115928547), 27.631021115928547));  // [1e-12, 1e12]
+  }
+}
+
+// u = mean over scenarios; first-stage bound duals: geometric mean
+__global__ void k_warm_u(DevWork D, WarmSeg W, int N, const float *pred) {
+  const int d = W.seg[9];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nu = W.seg[2] - W.seg[1];
+  const int nl = W.seg[6] - W.seg[5], nb = W.seg[7] - W.seg[6];
+  if (k < nu) {
+    double s = 0.0;
+    for (int sc = 0; sc < N; ++sc) s += pred[(size_t)sc * d + W.seg[1] + k];
+    D.u[k] = s / N;
+  } else if (k < nu + nl + nb) {
+    const int i = k - nu;
+    const int b = i < nl ? 2 : 3;
+    const int c = W.seg[3 + b] + (b == 2 ? i : i - nl);
+    double s = 0.0;
+    for (int sc = 0; sc < N; ++sc) s += pred[(size_t)sc * d + c];
+    int off = 0;
+    double *dst = const_cast<double *>(warm_dual_src(D, b, 0, W, c - W.seg[3 + b], off));
+    dst[off] = exp(fmin(fmax(s / N, -27.631021115928547), 27.631021115928547));
+  }
+}
+
+// slack stationarity: z = zl_s - zu_s
+__global__ void k_warm_z(long long n, DevWork D) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) D.z[t] = D.zls[t] - D.zus[t];
+}
+
+// x-gradient of the Lagrangian without the y terms (y = 0 when JTl was formed)
+__global__ void k_warm_yrhs(DevSym S, DevWork D, double *r) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)S.N * S.nx) return;
+  const int sc = (int)(t / S.nx), j = (int)(t - (long long)sc * S.nx);
+  r[t] = D.JTl[(size_t)sc * 2 * S.n + S.xkind[j] * S.n + S.xbus[j]] - D.zlx[t] + D.zux[t];
+}
+
+}  // namespace
+
+void launch_warm_target(const DevWork &D, const WarmSeg &W, int N, float *out, cudaStream_t st) {
+  k_warm_target<<<nblk((long long)N * W.seg[9], 256), 256, 0, st>>>(D, W, N, out); ipm_count_launch();
+}
+void launch_warm_apply(const DevWork &D, const WarmSeg &W, int N, const float *pred, cudaStream_t st) {
+  k_warm_apply<<<nblk((long long)N * W.seg[9], 256), 256, 0, st>>>(D, W, N, pred); ipm_count_launch();
+  const int n = (W.seg[2] - W.seg[1]) + (W.seg[7] - W.seg[5]);
+  k_warm_u<<<nblk(n, 128), 128, 0, st>>>(D, W, N, pred); ipm_count_launch();
+}
+void launch_warm_z(long long n, const DevWork &D, cudaStream_t st) {
+  k_warm_z<<<nblk(n, 256), 256, 0, st>>>(n, D); ipm_count_launch();
+}
+void launch_warm_yrhs(const DevSym &S, const DevWork &D, double *r, cudaStream_t st) {
+  k_warm_yrhs<<<nblk((long long)S.N * S.nx, 256), 256, 0, st>>>(S, D, r); ipm_count_launch();
 }

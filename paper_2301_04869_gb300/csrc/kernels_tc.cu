@@ -17,6 +17,7 @@
 // Every mbarrier wait is bounded: past the limit the kernel records
 // FLAG_TIMEOUT, stops issuing, lets its in-flight copies land (bounded) and
 // frees its TMEM before returning.
+#include <atomic>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -25,91 +26,18 @@
 
 #include "dev.cuh"
 #include "kernels.h"
+#include "tcgen05.cuh"
 
-extern long long g_ipm_launches;
 
 namespace tc {
+
+using namespace tcx;
 
 constexpr int BM = 128, BN = 128, BK = 64;              // tile; BK bf16 = one 128-byte swizzle row
 constexpr int STAGES = 2;
 constexpr int PLANE_BYTES = BM * BK * 2;                 // 16 KB per operand plane per stage
 constexpr int STAGE_BYTES = 6 * PLANE_BYTES;             // 3 A planes + 3 B planes
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;  // + barriers, TMEM slot
-constexpr long long WAIT_LIMIT = 1LL << 22;              // bounded spin (well under a second)
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// bounded wait on phase parity; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), descriptor version 1
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                      // LBO (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;            // SBO
-  d |= (uint64_t)1 << 46;                      // version
-  d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
-  return d;
-}
-
-// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4)            // D = F32
-         | (1u << 7)          // A = BF16
-         | (1u << 10)         // B = BF16
-         | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
 // upper-triangle tile t -> (ti, tj), row-major over ti
 __device__ __forceinline__ void tile_ij(int t, int nt1, int &ti, int &tj) {
   int i = 0, rem = t;
@@ -339,14 +267,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static const EncodeTiledFn fn = [] {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return (EncodeTiledFn) nullptr;
+  }();
   return fn;
 }
 
@@ -363,13 +291,20 @@ static bool make_map(CUtensorMap *m, const void *base, int rows, long long kpad)
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tc_make_kmajor_map(void *map, const void *base, int rows, long long k) {
+  return make_map(reinterpret_cast<CUtensorMap *>(map), base, rows, k);
+}
+
 void tc_plan(int nu, long long krows, TcPlan &P) {
   P.nu = nu;
   P.kpad = (krows + tc::BK - 1) / tc::BK * tc::BK;
   P.nt1 = (nu + tc::BM - 1) / tc::BM;
   P.ntiles = P.nt1 * (P.nt1 + 1) / 2;
   P.kb_total = (int)(P.kpad / tc::BK);
-  int G = 152 / P.ntiles;  // one CTA per SM (the stage buffers take ~193 KB of shared memory)
+  tc_regroup(P, 152 / P.ntiles);  // one CTA per SM (the stage buffers take ~193 KB of shared memory)
+}
+
+void tc_regroup(TcPlan &P, int G) {
   if (G < 1) G = 1;
   if (G > P.kb_total) G = P.kb_total;
   P.kb_per_group = (P.kb_total + G - 1) / G;
@@ -390,20 +325,19 @@ bool tc_set_operands(TcPlan &P, const void *a_planes, const void *b_planes) {
 
 void launch_split_t(long long krows, int nu, long long kpad, const float *src, void *planes, cudaStream_t st) {
   dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((nu + 31) / 32));
-  tc::k_split_t<<<grid, dim3(32, 8), 0, st>>>(krows, nu, kpad, src, (__nv_bfloat16 *)planes); ++g_ipm_launches;
+  tc::k_split_t<<<grid, dim3(32, 8), 0, st>>>(krows, nu, kpad, src, (__nv_bfloat16 *)planes); ipm_count_launch();
 }
 
 void launch_tc_schur(const TcPlan &P, double *partial, int *flags, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc::k_tc_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    attr = true;
-  }
+  static const bool attr =
+      cudaFuncSetAttribute(tc::k_tc_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) ==
+      cudaSuccess;
+  (void)attr;
   tc::Maps m;
   memcpy(&m, P.maps, sizeof(m));
   dim3 grid(P.ntiles, P.ngroups);
   tc::k_tc_schur<<<grid, 192, tc::SMEM_BYTES, st>>>(m, P.nt1, P.kb_total, P.kb_per_group, partial, flags);
-  ++g_ipm_launches;
+  ipm_count_launch();
 }
 
 void launch_tc_assemble(const TcPlan &P, int N, const double *partial, const double *Yu, const double *diag,
@@ -411,5 +345,5 @@ void launch_tc_assemble(const TcPlan &P, int N, const double *partial, const dou
   const long long tot = (long long)P.nu * P.nu;
   tc::k_tc_assemble<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P.nu, N, P.ngroups, P.ntiles, P.nt1, partial,
                                                                     Yu, diag, Khat);
-  ++g_ipm_launches;
+  ipm_count_launch();
 }

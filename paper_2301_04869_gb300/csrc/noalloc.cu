@@ -15,14 +15,15 @@
 // rewritten before it is read, so nothing needs clearing, but calls that
 // overlap on the GPU (different streams, or different host threads) race on
 // the array and must be serialised by the caller.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <mutex>
 
 #include "../../include/ipm.h"
+#include "kernels.h"
 
-extern long long g_ipm_launches;
 
 namespace {
 
@@ -148,11 +149,11 @@ extern "C" ipm_status ipm_schur_sum_noalloc(const double *Z, const double *Y, co
   cudaStream_t st = (cudaStream_t)stream;
   dim3 grid((unsigned)ntiles, (unsigned)ngroups);
   k_schur_partial_na<<<grid, 256, 0, st>>>(n_x, n_u, n_scen, spg, nt1, Z, Y, scratch);
-  ++g_ipm_launches;
+  ipm_count_launch();
   const long long tot = (long long)n_u * n_u;
   k_schur_assemble_na<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n_u, n_scen, ngroups, (int)ntiles, nt1,
                                                                       scratch, Yu, diag, Khat);
-  ++g_ipm_launches;
+  ipm_count_launch();
   if (cudaGetLastError() != cudaSuccess) return IPM_ERR_CUDA;
   return IPM_OK;
 }

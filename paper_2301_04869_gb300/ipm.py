@@ -34,6 +34,7 @@ class IPMError(RuntimeError):
 
 _I = ctypes.POINTER(ctypes.c_int)
 _D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
 
 
 class Network(ctypes.Structure):
@@ -48,8 +49,9 @@ BARRIER_MONOTONE, BARRIER_ADAPTIVE = 0, 1
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("panel", ctypes.c_int), ("barrier_rule", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6), ("sigma", ctypes.c_double)]
+                ("max_refine", ctypes.c_int), ("solve_threads", ctypes.c_int), ("barrier_rule", ctypes.c_int),
+                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+                ("sigma", ctypes.c_double)]
 
 
 class Dims(ctypes.Structure):
@@ -88,6 +90,25 @@ def load():
         "ipm_solve": (c_int, [vp, _I, _D, vp]),
         "ipm_get_quantity": (c_int, [vp, c_int, c_int, _D, c_ll, vp]),
         "ipm_set_profiling": (c_int, [vp, c_int]),
+        "ipm_set_loads": (c_int, [vp, _D, _D, vp]),
+        "ipm_mlp_create": (c_int, [c_int, c_int, c_int, c_int, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
+        "ipm_mlp_destroy": (c_int, [vp]),
+        "ipm_mlp_param_count": (c_ll, [vp]),
+        "ipm_mlp_set_params": (c_int, [vp, _F]),
+        "ipm_mlp_get_params": (c_int, [vp, _F]),
+        "ipm_mlp_set_normalization": (c_int, [vp, _F, _F, _F, _F]),
+        "ipm_mlp_forward": (c_int, [vp, vp, c_int, vp, vp]),
+        "ipm_mlp_gradients": (c_int, [vp, vp, vp, c_int, _F, _F, vp]),
+        "ipm_mlp_train_step": (c_int, [vp, vp, vp, c_int, ctypes.c_float, _F, vp]),
+        "ipm_warm_dim": (c_int, [vp, _I]),
+        "ipm_warm_target": (c_int, [vp, vp, vp]),
+        "ipm_warm_start": (c_int, [vp, vp, vp]),
+        "ipm_batch_default_options": (c_int, [ctypes.POINTER(BatchOptions)]),
+        "ipm_solve_batch": (c_int, [ctypes.POINTER(vp), c_int, ctypes.POINTER(vp), ctypes.POINTER(BatchOptions),
+                                    _I, _D, _I, _D]),
+        "ipm_run_instances": (c_int, [ctypes.POINTER(Network), c_int, _I, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                      ctypes.POINTER(Options), ctypes.POINTER(BatchOptions), c_ll,
+                                      ctypes.POINTER(_D), _I, _D, _I, _D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -110,38 +131,56 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _cnet(net):
+    """ipm_network view of a synth.Network (the arrays it points to are returned too)."""
+    keep = dict(
+        fr=np.ascontiguousarray(net.fr, dtype=np.int32), to=np.ascontiguousarray(net.to, dtype=np.int32),
+        gen=np.ascontiguousarray(net.gen_bus, dtype=np.int32),
+        r=np.ascontiguousarray(net.r, dtype=np.float64), x=np.ascontiguousarray(net.x, dtype=np.float64),
+        b=np.ascontiguousarray(net.b, dtype=np.float64),
+        pmax=np.ascontiguousarray(net.pmax, dtype=np.float64), qmax=np.ascontiguousarray(net.qmax, dtype=np.float64),
+        c2=np.ascontiguousarray(net.c2, dtype=np.float64), c1=np.ascontiguousarray(net.c1, dtype=np.float64),
+        vmin=np.ascontiguousarray(net.vmin, dtype=np.float64), vmax=np.ascontiguousarray(net.vmax, dtype=np.float64))
+    k = keep
+    cnet = Network(int(net.n_bus), int(k["fr"].size), int(k["gen"].size),
+                   _ptr(k["fr"], ctypes.c_int), _ptr(k["to"], ctypes.c_int), _ptr(k["gen"], ctypes.c_int),
+                   _ptr(k["r"], ctypes.c_double), _ptr(k["x"], ctypes.c_double), _ptr(k["b"], ctypes.c_double),
+                   _ptr(k["pmax"], ctypes.c_double), _ptr(k["qmax"], ctypes.c_double),
+                   _ptr(k["c2"], ctypes.c_double), _ptr(k["c1"], ctypes.c_double),
+                   _ptr(k["vmin"], ctypes.c_double), _ptr(k["vmax"], ctypes.c_double))
+    return keep, cnet
+
+
+def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, barrier_rule=None, sigma=None,
+                 graphs=False, autotune=False, solve_threads=0):
+    lib = load()
+    opt = Options()
+    lib.ipm_default_options(ctypes.byref(opt))
+    opt.tol = tol
+    opt.max_iter = max_iter
+    opt.precision = precision
+    opt.max_refine = max_refine
+    if barrier_rule is not None:
+        opt.barrier_rule = barrier_rule
+    if sigma is not None:
+        opt.sigma = sigma
+    opt.graphs = int(bool(graphs))
+    opt.autotune = int(bool(autotune))
+    opt.solve_threads = int(solve_threads)
+    return opt
+
+
 class Solver:
     """One context: a network with N load scenarios on the current GPU."""
 
     def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
-                 barrier_rule=None, sigma=None):
+                 barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0):
         lib = load()
         self._lib = lib
-        self._keep = dict(
-            fr=np.ascontiguousarray(net.fr, dtype=np.int32), to=np.ascontiguousarray(net.to, dtype=np.int32),
-            gen=np.ascontiguousarray(net.gen_bus, dtype=np.int32),
-            r=np.ascontiguousarray(net.r, dtype=np.float64), x=np.ascontiguousarray(net.x, dtype=np.float64),
-            b=np.ascontiguousarray(net.b, dtype=np.float64),
-            pmax=np.ascontiguousarray(net.pmax, dtype=np.float64), qmax=np.ascontiguousarray(net.qmax, dtype=np.float64),
-            c2=np.ascontiguousarray(net.c2, dtype=np.float64), c1=np.ascontiguousarray(net.c1, dtype=np.float64),
-            vmin=np.ascontiguousarray(net.vmin, dtype=np.float64), vmax=np.ascontiguousarray(net.vmax, dtype=np.float64))
-        k = self._keep
-        cnet = Network(int(net.n_bus), int(k["fr"].size), int(k["gen"].size),
-                       _ptr(k["fr"], ctypes.c_int), _ptr(k["to"], ctypes.c_int), _ptr(k["gen"], ctypes.c_int),
-                       _ptr(k["r"], ctypes.c_double), _ptr(k["x"], ctypes.c_double), _ptr(k["b"], ctypes.c_double),
-                       _ptr(k["pmax"], ctypes.c_double), _ptr(k["qmax"], ctypes.c_double),
-                       _ptr(k["c2"], ctypes.c_double), _ptr(k["c1"], ctypes.c_double),
-                       _ptr(k["vmin"], ctypes.c_double), _ptr(k["vmax"], ctypes.c_double))
-        opt = Options()
-        lib.ipm_default_options(ctypes.byref(opt))
-        opt.tol = tol
-        opt.max_iter = max_iter
-        opt.precision = precision
-        opt.max_refine = max_refine
-        if barrier_rule is not None:
-            opt.barrier_rule = barrier_rule
-        if sigma is not None:
-            opt.sigma = sigma
+        self._keep, cnet = _cnet(net)
+        opt = make_options(precision=precision, tol=tol, max_iter=max_iter, max_refine=max_refine,
+                           barrier_rule=barrier_rule, sigma=sigma, graphs=graphs, autotune=autotune,
+                           solve_threads=solve_threads)
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]
@@ -223,6 +262,13 @@ class Solver:
         self._check(self._lib.ipm_solve(self._h, ctypes.byref(it), ctypes.byref(err), _stream(stream)))
         return it.value, err.value
 
+    def ipm_set_loads(self, pd, qd, stream=None):
+        pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
+        qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
+        assert pd.shape == (self.N, self.dims.n_bus) and qd.shape == pd.shape
+        self._check(self._lib.ipm_set_loads(self._h, _ptr(pd, ctypes.c_double), _ptr(qd, ctypes.c_double),
+                                            _stream(stream)))
+
     def ipm_get_quantity(self, which, scen=0, stream=None):
         d = self.dims
         sizes = {Q_KHAT: d.n_u * d.n_u, Q_RHS_U: d.n_u, Q_Z: d.n_x * d.n_u, Q_FGH: 1 + d.n_x + d.m,
@@ -233,6 +279,20 @@ class Solver:
         self._check(self._lib.ipm_get_quantity(self._h, which, scen, _ptr(out, ctypes.c_double), out.size,
                                                _stream(stream)))
         return out
+
+    def ipm_warm_dim(self):
+        d = ctypes.c_int(0)
+        self._check(self._lib.ipm_warm_dim(self._h, ctypes.byref(d)))
+        return d.value
+
+    def ipm_warm_target(self, out, stream=None):
+        """Warm-start vectors of the current state into a device FP32 tensor [N][d]."""
+        self._check(self._lib.ipm_warm_target(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def ipm_warm_start(self, pred, stream=None):
+        """Start from predicted warm-start vectors (device FP32 tensor [N][d])."""
+        self._check(self._lib.ipm_warm_start(self._h, ctypes.c_void_p(pred.data_ptr()), _stream(stream)))
 
     def ipm_set_profiling(self, on=1):
         self._check(self._lib.ipm_set_profiling(self._h, int(on)))
@@ -276,3 +336,150 @@ class Solver:
             out[name] = v[o:o + k].reshape(shape)
             o += k
         return out
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("n_threads", ctypes.c_int), ("group_contraction", ctypes.c_int), ("window_us", ctypes.c_double),
+                ("reserved", ctypes.c_int * 4)]
+
+
+BATCH_N_STATS = 8
+BATCH_STATS = ("grouped_launches", "work_items", "instances_per_launch", "max_active", "wall_ms")
+
+
+def batch_options(n_threads=8, group_contraction=True, window_us=2000.0):
+    lib = load()
+    o = BatchOptions()
+    lib.ipm_batch_default_options(ctypes.byref(o))
+    o.n_threads = int(n_threads)
+    o.group_contraction = int(bool(group_contraction))
+    o.window_us = float(window_us)
+    return o
+
+
+def ipm_solve_batch(solvers, streams=None, n_threads=8, group_contraction=True, window_us=2000.0):
+    """Solve existing contexts together (ipm_solve_batch).  streams: None (the
+    runner makes its own) or one torch stream per solver.  Returns
+    (iters, kkt_err, status, stats) with stats a dict of BATCH_STATS."""
+    lib = load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s._h.value for s in solvers])
+    sp = None if streams is None else (ctypes.c_void_p * n)(*[s.cuda_stream for s in streams])
+    it = np.zeros(n, dtype=np.int32)
+    er = np.zeros(n)
+    stt = np.zeros(n, dtype=np.int32)
+    stats = np.zeros(BATCH_N_STATS)
+    bo = batch_options(n_threads, group_contraction, window_us)
+    lib.ipm_solve_batch(hs, n, sp, ctypes.byref(bo), _ptr(it, ctypes.c_int), _ptr(er, ctypes.c_double),
+                        _ptr(stt, ctypes.c_int), _ptr(stats, ctypes.c_double))
+    return it, er, stt, dict(zip(BATCH_STATS, stats[:len(BATCH_STATS)]))
+
+
+def ipm_run_instances(nets, pds, qds, mem_budget, precision=PREC_FP64, tol=1e-8, max_iter=200, n_threads=8,
+                      group_contraction=True, window_us=2000.0, want_states=False, **opt_kw):
+    """Create, solve and destroy independent instances under a device memory
+    budget in bytes (ipm_run_instances).  pds[i], qds[i]: [N_i][n_bus_i].
+    Returns (iters, kkt_err, status, stats, states) with states a list of
+    final state vectors (or None)."""
+    lib = load()
+    n = len(nets)
+    keeps = [_cnet(net) for net in nets]
+    arr = (Network * n)(*[k[1] for k in keeps])
+    pdl = [np.ascontiguousarray(np.atleast_2d(p), dtype=np.float64) for p in pds]
+    qdl = [np.ascontiguousarray(np.atleast_2d(q), dtype=np.float64) for q in qds]
+    ns = np.array([p.shape[0] for p in pdl], dtype=np.int32)
+    pp = (_D * n)(*[_ptr(p, ctypes.c_double) for p in pdl])
+    qp = (_D * n)(*[_ptr(q, ctypes.c_double) for q in qdl])
+    states = None
+    sp = None
+    if want_states:
+        states = []
+        for net, N in zip(nets, ns):
+            nb, ng = int(net.n_bus), int(len(net.gen_bus))
+            nx, nu, m = (nb - 1) + (nb - ng), 2 * ng - 1, ng + 1
+            states.append(np.zeros(4 * N * nx + 4 * N * m + 3 * nu + 3))
+        sp = (_D * n)(*[_ptr(v, ctypes.c_double) for v in states])
+    opt = make_options(precision=precision, tol=tol, max_iter=max_iter, **opt_kw)
+    bo = batch_options(n_threads, group_contraction, window_us)
+    it = np.zeros(n, dtype=np.int32)
+    er = np.zeros(n)
+    stt = np.zeros(n, dtype=np.int32)
+    stats = np.zeros(BATCH_N_STATS)
+    lib.ipm_run_instances(arr, n, _ptr(ns, ctypes.c_int), pp, qp, ctypes.byref(opt), ctypes.byref(bo),
+                          int(mem_budget), sp, _ptr(it, ctypes.c_int), _ptr(er, ctypes.c_double),
+                          _ptr(stt, ctypes.c_int), _ptr(stats, ctypes.c_double))
+    return it, er, stt, dict(zip(BATCH_STATS, stats[:len(BATCH_STATS)])), states
+
+
+class MLP:
+    """The warm-start network of libipm.so (ipm_mlp_*).  Inputs and targets
+    are device FP32 tensors; parameters and gradients travel as host FP32
+    arrays in the logical layout (W1, b1, W2, b2, W3, b3)."""
+
+    def __init__(self, d_in, d_hidden, d_out, max_batch=256, seed=0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        st = self._lib.ipm_mlp_create(int(d_in), int(d_hidden), int(d_out), int(max_batch), int(seed),
+                                      ctypes.byref(h))
+        if st != IPM_OK:
+            raise IPMError(st, "ipm_mlp_create failed")
+        self._h = h
+        self.d_in, self.d_hidden, self.d_out, self.max_batch = d_in, d_hidden, d_out, max_batch
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ipm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != IPM_OK:
+            raise IPMError(st, what)
+
+    @property
+    def n_params(self):
+        return int(self._lib.ipm_mlp_param_count(self._h))
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        self._check(self._lib.ipm_mlp_set_params(self._h, _ptr(p, ctypes.c_float)), "set_params")
+
+    def get_params(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        self._check(self._lib.ipm_mlp_get_params(self._h, _ptr(p, ctypes.c_float)), "get_params")
+        return p
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std):
+        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (in_mean, in_std, out_mean, out_std)]
+        self._check(self._lib.ipm_mlp_set_normalization(self._h, *[_ptr(v, ctypes.c_float) for v in a]),
+                    "set_normalization")
+
+    def forward(self, x, out=None, stream=None):
+        import torch
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, self.d_out), dtype=torch.float32, device=x.device)
+        self._check(self._lib.ipm_mlp_forward(self._h, ctypes.c_void_p(x.data_ptr()), B,
+                                              ctypes.c_void_p(out.data_ptr()), _stream(stream)), "forward")
+        return out
+
+    def gradients(self, x, t, stream=None):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float(0)
+        self._check(self._lib.ipm_mlp_gradients(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                                x.shape[0], _ptr(g, ctypes.c_float), ctypes.byref(loss),
+                                                _stream(stream)), "gradients")
+        return loss.value, g
+
+    def train_step(self, x, t, lr, stream=None):
+        loss = ctypes.c_float(0)
+        self._check(self._lib.ipm_mlp_train_step(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                                 x.shape[0], float(lr), ctypes.byref(loss), _stream(stream)),
+                    "train_step")
+        return loss.value
