@@ -37,7 +37,7 @@ METRIC = "scenario condensations/s & s per IPM iter (mixed vs FP64 path, 1e-8 KK
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per launch from one ncu capture of the kernel as it stands (profiles/); None once the
 # kernel changes until it is captured again.
-TRAFFIC = {"k_gemm_tn64": None}
+TRAFFIC = {"k_gemm_tn64": None, "k_zsolve64": None, "k_emu_schur": None}
 UNIT = "scenario condensations/s"
 
 
@@ -90,26 +90,51 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
-def roofline(phases, dims, peaks, peak_kind):
+def emu_issued_flops(nu, krows):
+    """BF16 tensor-core flops one emulated contraction issues: 36 slice products
+    over every 128 x 64 upper tile and every (512-row padded) contraction row."""
+    ntm, ntn = -(-nu // 128), -(-nu // 64)
+    ntiles = sum(1 for a in range(ntm) for b in range(ntn) if a * 128 <= b * 64 + 63)
+    kpad = -(-krows // 512) * 512
+    return 36 * 2.0 * kpad * 128 * 64 * ntiles
+
+
+def roofline(phases, dims, peaks, peak_kind, precision):
     """Roofline entry for the dominant kernel phase (device time share)."""
     name = max(phases, key=lambda k: phases[k][0])
     ms, calls = phases[name]
     N, nx, nu = dims.n_scen, dims.n_x, dims.n_u
     per_call_s = ms / 1e3 / max(calls, 1)
     fp64_peak = FP64_PEAK_TFLOPS
+    # algorithmic flops of K_hat: the upper triangle of sum_i Z_i^T Y_i (symmetric)
+    kflops = 2.0 * nx * (nu * (nu + 1) / 2.0) * N
+    if name == "gemm" and precision == "fp64_tc":
+        issued = emu_issued_flops(nu, N * nx)
+        ach = issued / per_call_s / 1e12
+        pk = peaks["bf16_tflops_sustained"]
+        return {"kernel": "k_emu_schur (FP64-grade Z^T Y from exact BF16 slices, tcgen05)", "bound": "tensor",
+                "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": TRAFFIC.get("k_emu_schur"),
+                "algorithmic": f"{issued:.4g} BF16 flop/launch issued (36 slice products); "
+                               f"{kflops:.4g} FP64 flop/launch of the contraction itself",
+                "fp64_equivalent_tflops": kflops / per_call_s / 1e12}
+    if name == "gemm" and precision == "mixed":
+        return {"kernel": "k_tc_schur (BF16x3, tcgen05)", "bound": "tensor",
+                "achieved": 6 * kflops / per_call_s / 1e12, "peak": peaks["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "frac": 6 * kflops / per_call_s / 1e12 / peaks["bf16_tflops_sustained"],
+                "traffic": None, "algorithmic": f"{6 * kflops:.4g} BF16 flop/launch (6 split products)"}
     if name == "gemm":
-        # algorithmic flops: the upper triangle of sum_i Z_i^T Y_i (symmetric K_hat)
-        flops = 2.0 * nx * (nu * (nu + 1) / 2.0) * N
-        ach = flops / per_call_s / 1e12
+        ach = kflops / per_call_s / 1e12
         return {"kernel": "k_gemm_tn64 (FP64 Z^T Y + scenario sum)", "bound": "alu", "achieved": ach,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
                 "traffic": TRAFFIC.get("k_gemm_tn64"),
-                "algorithmic": f"{flops:.4g} flop/launch"}
+                "algorithmic": f"{kflops:.4g} flop/launch"}
     if name == "zsolve":
         flops = 2.0 * dims.nnz_lu * nu * N
         ach = flops / per_call_s / 1e12
         return {"kernel": "k_zsolve64 (FP64 multi-RHS solves + SpMM)", "bound": "alu", "achieved": ach,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": TRAFFIC.get("k_zsolve64"),
                 "algorithmic": f"{flops:.4g} flop/launch"}
     if name == "lu":
         return {"kernel": "k_lu_factor", "bound": "alu", "achieved": None, "peak": fp64_peak,
@@ -185,7 +210,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     net, pd, qd = synth.workload(args.workload)
-    prec = ipm.PREC_MIXED if args.precision == "mixed" else ipm.PREC_FP64
+    prec = {"fp64": ipm.PREC_FP64, "mixed": ipm.PREC_MIXED, "fp64_tc": ipm.PREC_FP64_TC}[args.precision]
     sol = ipm.Solver(net, pd, qd, precision=prec)
     dims = sol.dims
     N = dims.n_scen
@@ -257,14 +282,15 @@ def run_ours(args):
     if rank != 0:
         return
     peaks, pk = load_peaks()
-    rl = roofline(phases, dims, peaks, pk)
+    rl = roofline(phases, dims, peaks, pk, args.precision)
     rl["peak_source"] = ("FP64 unit count x clock (2 FMA/clk/SM x 152 SMs x 2.07 GHz)" if rl["bound"] == "alu"
-                         else f"{pk} MEASURED_PEAKS.json")
+                         else (f"{pk} MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
+                               if rl["bound"] == "tensor" else f"{pk} MEASURED_PEAKS.json hbm_gbs"))
     cb = cpu_baseline(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == ipm.PREC_FP64 else "bf16x3+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "bf16x3+f64", "fp64_tc": "f64 (bf16 slices)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "n_bus": dims.n_bus, "n_scen": N, "n_x": dims.n_x, "n_u": dims.n_u,
                    "path": args.precision, "l2": "flushed between steps (256 MB write)",
@@ -290,7 +316,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="opf1000_n64", choices=list(synth.CONFIGS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp64_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

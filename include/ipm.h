@@ -21,7 +21,15 @@
  * the mixed-precision factor.  When that factor is not positive definite or
  * the refinement meets non-positive curvature (K_hat ill-conditioned near
  * the solution), the iteration is condensed again in FP64 and the inertia
- * decision is taken on the exact K_hat.
+ * decision is taken on the exact K_hat.  IPM_PREC_FP64_TC is the FP64 path
+ * with the Z^T Y contraction emulated on the BF16 tensor cores: per 512
+ * contraction rows and column, FP64 operands (rows balanced by powers of
+ * two) are scaled by a power of two and split into eight 7-bit integer
+ * slices; the 36 slice products that matter are accumulated exactly (integer
+ * sums of at most 2^24 in FP32), combined into one exact 64-bit integer per
+ * group and accumulated in FP64; each row's product is off by about 2^-52 of
+ * the product of the group's largest entries of the two columns; a
+ * non-finite result falls back to the FP64 units.
  *
  * Conventions (all entry points):
  *  - Every call returns an ipm_status; nothing aborts or traps.  On error,
@@ -74,14 +82,14 @@ typedef struct {
   const double *vmin, *vmax;   /* [n_bus] */
 } ipm_network;
 
-enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1 };
+enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1, IPM_PREC_FP64_TC = 2 };
 
 enum { IPM_BARRIER_MONOTONE = 0, IPM_BARRIER_ADAPTIVE = 1 };
 
 typedef struct {
   double tol;            /* KKT residual E_0 target (1e-8) */
   int max_iter;          /* 200 */
-  int precision;         /* IPM_PREC_FP64 or IPM_PREC_MIXED */
+  int precision;         /* IPM_PREC_FP64, IPM_PREC_MIXED or IPM_PREC_FP64_TC */
   int max_refine;        /* iterative-refinement sweeps of the KKT solve (mixed) */
   int solve_threads;     /* threads per CTA of the multi-RHS solves: 128 or 256 (0 = 256,
                             or the autotuner's choice) */
@@ -169,6 +177,8 @@ ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
 
 /* Diagnostics for tests: copy an internal quantity to host memory.
  * which: IPM_Q_KHAT (n_u*n_u, row-major, before factorization, delta = 0),
+ *        IPM_Q_ZTZ (n_u*n_u: sum_i Z_i^T Z_i of the inertia correction, after
+ *        a factorization with delta_w > 0),
  *        IPM_Q_RHS_U (n_u), IPM_Q_Z (scenario scen, n_x*n_u row-major, rows in
  *        the x order of the state vector), IPM_Q_FGH (scen: f, g[n_x], h[m]),
  *        IPM_Q_JAC (scen: dense G_x, G_u, H_x, H_u row-major, concatenated),
@@ -182,7 +192,7 @@ ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
  *        if cap allows, is the total number of kernels the library launched).
  * cap: capacity of host_out in doubles. */
 enum { IPM_Q_KHAT = 0, IPM_Q_RHS_U = 1, IPM_Q_Z = 2, IPM_Q_FGH = 3, IPM_Q_JAC = 4,
-       IPM_Q_HESS = 5, IPM_Q_ERRS = 6, IPM_Q_INFO = 7, IPM_Q_TIMERS = 8 };
+       IPM_Q_HESS = 5, IPM_Q_ERRS = 6, IPM_Q_INFO = 7, IPM_Q_TIMERS = 8, IPM_Q_ZTZ = 9 };
 ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
                             long long cap, void *stream);
 
@@ -298,6 +308,15 @@ ipm_status ipm_warm_target(ipm_ctx *ctx, float *out, void *stream);
  * zl_x + zu_x), one batched transposed LU solve; mu = max(1e-6, mean
  * complementarity).  Then ipm_solve continues from this point. */
 ipm_status ipm_warm_start(ipm_ctx *ctx, const float *pred, void *stream);
+
+/* The emulated FP64 contraction of IPM_PREC_FP64_TC on caller-owned device
+ * matrices: Khat [n_u][n_u] = sum_s Z_s^T Y_s, with Z, Y device FP64
+ * [n_scen][n_x][n_u] (row-major).  Allocates its scratch, synchronises the
+ * stream before returning.  IPM_ERR_ARG also when the result is not finite.
+ * For checking the kernel on
+ * arbitrary data; the paper has no counterpart (it is GB300 specific). */
+ipm_status ipm_schur_sum_tc(const double *Z, const double *Y, int n_scen, int n_x, int n_u, double *Khat,
+                            void *stream);
 
 /* Allocation-free reduced-Hessian sum.  The paper has no counterpart to this
  * entry point; it exists for callers that cannot call cudaMalloc (code that

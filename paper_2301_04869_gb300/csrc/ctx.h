@@ -36,6 +36,16 @@ struct ipm_ctx {
   double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta); scratch [N][max(nx,nu)]
   double *gLu = nullptr, *HTt_u = nullptr;
   double *pg_curv = nullptr, *pmax_d = nullptr;
+  // FP64 contraction emulated on the tensor cores (IPM_PREC_FP64_TC)
+  bool emu = false;
+  EmuPlan emuZY, emuZZ;
+  void *zplE = nullptr, *yplE = nullptr;
+  int *expZ = nullptr, *expY = nullptr, *emu_rs = nullptr;
+  int2 *emu_tiles = nullptr;
+  int *emu_tile_of = nullptr;
+  double *emupart = nullptr;
+  int emu_max_groups = 0;
+  long long n_emu_fallback = 0;
   // mixed path
   bool mixed = false;
   float *Z32 = nullptr, *Y32 = nullptr;

@@ -173,9 +173,33 @@ ipm_status alloc_work(ipm_ctx *c) {
   CK(cudaMemset(D.flags, 0, FLAG_COUNT * sizeof(int)));
   c->mixed = c->opt.precision == IPM_PREC_MIXED;
   TRY(dalloc(c, &c->Yu, N * nu * nu));
+  c->emu = c->opt.precision == IPM_PREC_FP64_TC;
   if (!c->mixed) {
     TRY(dalloc(c, &c->Z, N * nx * nu));
     TRY(dalloc(c, &c->Y, N * nx * nu));
+    if (c->emu) {
+      const long long krows = N * nx;
+      const size_t pb = emu_planes_bytes((int)nu, krows);
+      const long long ngr = emu_kpad(krows) / 512;
+      unsigned char *pz = nullptr, *py = nullptr;
+      TRY(dalloc(c, &pz, pb));
+      TRY(dalloc(c, &py, pb));
+      c->zplE = pz;
+      c->yplE = py;
+      TRY(dalloc(c, &c->expZ, ngr * nu));
+      TRY(dalloc(c, &c->emu_rs, krows));
+      TRY(dalloc(c, &c->expY, ngr * nu));
+      const long long nt = ((nu + 127) / 128) * ((nu + 63) / 64);
+      TRY(dalloc(c, &c->emu_tiles, nt));
+      TRY(dalloc(c, &c->emu_tile_of, nt));
+      if (!emu_plan(c->emuZY, (int)nu, krows, c->zplE, c->yplE, c->expZ, c->expY, c->emu_tiles, c->emu_tile_of) ||
+          !emu_plan(c->emuZZ, (int)nu, krows, c->zplE, c->zplE, c->expZ, c->expZ, c->emu_tiles, c->emu_tile_of))
+        return fail(c, IPM_ERR_CUDA, "tensor maps of the emulated contraction");
+      EmuPlan big = c->emuZY;
+      emu_regroup(big, 2 * std::max(1, 152 / big.ntiles));
+      c->emu_max_groups = std::max(big.ngroups, c->emuZY.ngroups);
+      TRY(dalloc(c, &c->emupart, (long long)emu_partial_doubles(c->emuZY, c->emu_max_groups)));
+    }
   } else {
     // one region holds either the mixed operands (FP32 Z, Y and the BF16x3
     // planes) or, in an iteration that falls back, the FP64 Z and Y
@@ -408,7 +432,8 @@ ipm_status run_part(ipm_ctx *c, cudaGraphExec_t &gx, long long &gn, Fn fn, cudaS
 // groups (the multi-instance runner may take it over through the hook)
 void fp64_contraction(ipm_ctx *c, cudaStream_t st) {
   const DevSym &S = c->ds;
-  if (c->gemm_hook) c->gemm_hook(c->gemm_hook_arg, c, st);
+  if (c->emu) launch_emu_schur(c->emuZY, c->emupart, c->dw.flags, st);
+  else if (c->gemm_hook) c->gemm_hook(c->gemm_hook_arg, c, st);
   else launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
                         c->partial, st);
 }
@@ -458,7 +483,7 @@ double time_ms(Fn fn, cudaStream_t st, int reps = 2) {
 ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
   const DevSym &S = c->ds;
   DevWork &D = c->dw;
-  const auto key = std::make_tuple(S.nx, S.nu, S.N, c->mixed ? 1 : 0);
+  const auto key = std::make_tuple(S.nx, S.nu, S.N, c->mixed ? 1 : (c->emu ? 2 : 0));
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tune_cache.find(key);
@@ -466,6 +491,10 @@ ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
       c->zs_threads = it->second.zs_threads;
       c->kchunk = it->second.kchunk;
       c->ngroups = it->second.ngroups;
+      if (c->emu) {
+        emu_regroup(c->emuZY, it->second.tc_groups);
+        emu_regroup(c->emuZZ, it->second.tc_groups);
+      }
       if (c->mixed) {
         tc_regroup(c->planZY, it->second.tc_groups);
         tc_regroup(c->planZZ, it->second.tc_groups);
@@ -494,7 +523,25 @@ ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
     launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
   }
   int tc_groups = 0;
-  if (fp64) {
+  if (fp64 && c->emu) {
+    const int G0 = std::max(1, 152 / c->emuZY.ntiles);
+    int bestG = G0;
+    best = 1e300;
+    int slot = 2;
+    for (int G : {G0 / 2, G0, 2 * G0}) {
+      if (G < 1) continue;
+      EmuPlan trial = c->emuZY;
+      emu_regroup(trial, G);
+      if (trial.ngroups > c->emu_max_groups) continue;
+      c->emuZY = trial;
+      const double ms = time_ms([&] { launch_emu_schur(c->emuZY, c->emupart, D.flags, st); }, st);
+      if (slot < 8) c->tune_ms[slot++] = ms;
+      if (ms < best) best = ms, bestG = G;
+    }
+    emu_regroup(c->emuZY, bestG);
+    emu_regroup(c->emuZZ, bestG);
+    tc_groups = bestG;
+  } else if (fp64) {
     const long long G0 = std::max(1, (3 * 152) / c->ntiles);
     long long bestG = G0;
     best = 1e300;
@@ -558,6 +605,11 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     ph_begin(c, PH_ZSOLVE, st);
     if (fp64) {
       launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads);
+      if (c->emu) {
+        launch_emu_rowscale(c->emuZY, c->Z, c->Y, c->emu_rs, st);
+        launch_emu_split(c->emuZY, c->Z, false, c->emu_rs, st);
+        launch_emu_split(c->emuZY, c->Y, true, c->emu_rs, st);
+      }
     } else {
       // mixed: FP32 solves, BF16x3 planes for the tensor-core product
       launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
@@ -568,8 +620,9 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   };
   auto post = [&] {
     if (fp64) {
-      launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
-                           c->Khat, st);
+      if (c->emu) launch_emu_assemble(c->emuZY, S.N, c->emupart, c->Yu, c->diag1, c->Khat, st);
+      else launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
+                                c->Khat, st);
       ph_end(c, PH_GEMM, st);
       ph_begin(c, PH_RRHS, st);
       // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
@@ -611,6 +664,16 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   ph_collect(c);
   if (c->h_flags[FLAG_SINGULAR]) return fail(c, IPM_ERR_SINGULAR_GX, "singular pivot in the LU of G_x");
   if (c->h_flags[FLAG_TIMEOUT]) return fail(c, IPM_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (fp64 && c->emu && c->h_flags[FLAG_NONFINITE]) {
+    // the emulated contraction gave a non-finite value: redo it on the FP64 units
+    ++c->n_emu_fallback;
+    launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
+                     c->partial, st);
+    launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
+                         c->Khat, st);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(D.flags + FLAG_NONFINITE, 0, sizeof(int), st));
+  }
   c->have_cond = true;
   c->have_fact = false;
   c->M_valid = false;
@@ -625,10 +688,24 @@ ipm_status do_factor(ipm_ctx *c, double delta, int *is_pd, cudaStream_t st, doub
     // eq. (11) contains K_xx: with K_xx + delta I the reduced right-hand side
     // gains -delta sum_i G_u^T G_x^{-T} b_i = delta sum_i Z_i^T b_i
     if (!c->mixed || c->exact_iter) {
-      launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Z, c->tiles, c->ntiles,
-                       c->partial, st);
-      launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, nullptr, nullptr,
-                           c->M, st);
+      bool done = false;
+      if (c->emu) {
+        CK(cudaMemsetAsync(c->dw.flags + FLAG_NONFINITE, 0, sizeof(int), st));
+        // Z^T Z: both operands from one unbalanced split of Z (K_hat is done,
+        // so the balanced planes are no longer needed)
+        launch_emu_split(c->emuZZ, c->Z, false, nullptr, st);
+        launch_emu_schur(c->emuZZ, c->emupart, c->dw.flags, st);
+        launch_emu_assemble(c->emuZZ, S.N, c->emupart, nullptr, nullptr, c->M, st);
+        TRY(read_flags(c, st));
+        done = !c->h_flags[FLAG_NONFINITE];
+        if (!done) ++c->n_emu_fallback;
+      }
+      if (!done) {
+        launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Z, c->tiles, c->ntiles,
+                         c->partial, st);
+        launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, nullptr, nullptr,
+                             c->M, st);
+      }
       launch_zt_apply(S, c->Z, c->bpos, nullptr, nullptr, 1.0, 0.0, c->rhs_corr, c->cpos, st);
     } else {
       launch_tc_schur(c->planZZ, c->tcpart, c->dw.flags, st);
@@ -1030,7 +1107,8 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
   ipm_ctx *c = new ipm_ctx();
   if (opt) c->opt = *opt;
   else ipm_default_options(&c->opt);
-  if ((c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || !(c->opt.tol > 0) ||
+  if ((c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED &&
+       c->opt.precision != IPM_PREC_FP64_TC) || !(c->opt.tol > 0) ||
       c->opt.max_iter < 0 || c->opt.max_refine < 0 ||
       (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
       (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
@@ -1176,6 +1254,12 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
     if (!c->have_cond) return fail(c, IPM_ERR_STATE, "no condensed system");
     if (!need((long long)nu * nu)) return IPM_ERR_ARG;
     CK(cudaMemcpy(out, c->Khat, (size_t)nu * nu * sizeof(double), cudaMemcpyDeviceToHost));
+    return IPM_OK;
+  }
+  if (which == IPM_Q_ZTZ) {
+    if (!c->have_cond || !c->M_valid) return fail(c, IPM_ERR_STATE, "no inertia-correction product");
+    if (!need((long long)nu * nu)) return IPM_ERR_ARG;
+    CK(cudaMemcpy(out, c->M, (size_t)nu * nu * sizeof(double), cudaMemcpyDeviceToHost));
     return IPM_OK;
   }
   if (which == IPM_Q_RHS_U) {

@@ -120,6 +120,34 @@ void tc_plan(int nu, long long krows, TcPlan &P);
 // tensor map (128 bytes at map) of a BF16 matrix [rows][k] (k contiguous, k a
 // multiple of 8), box 64 (k) x 128 (rows), 128-byte swizzle
 bool tc_make_kmajor_map(void *map, const void *base, int rows, long long k);
+// the same with a box of box_rows rows (64 or 128)
+bool tc_make_kmajor_map_box(void *map, const void *base, int rows, long long k, int box_rows);
+
+// kernels_emu.cu (FP64-grade K_hat from exact BF16 slices on the tensor cores)
+struct EmuPlan {
+  int nu = 0, ntm = 0, ntn = 0, ntiles = 0, kb_total = 0, kb_per_group = 0, ngroups = 0;
+  long long krows = 0, kpad = 0;
+  int2 *tiles = nullptr;
+  int *tile_of = nullptr;
+  const void *a_planes = nullptr, *b_planes = nullptr;
+  int *exp_a = nullptr, *exp_b = nullptr;
+  alignas(64) unsigned char maps[16 * 128];  // eight A-plane and eight B-plane CUtensorMap
+};
+// bytes of the slice planes of one operand; exponents take (kpad / 512) * nu ints
+size_t emu_planes_bytes(int nu, long long krows);
+long long emu_kpad(long long krows);
+// tiles_dev: room for ceil(nu/128) * ceil(nu/64) int2; tile_of_dev: the same count of ints
+bool emu_plan(EmuPlan &P, int nu, long long krows, const void *a_planes, const void *b_planes, int *exp_a,
+              int *exp_b, int2 *tiles_dev, int *tile_of_dev);
+void emu_regroup(EmuPlan &P, int groups);
+size_t emu_partial_doubles(const EmuPlan &P, int max_groups);
+// power-of-two row balancing of Z, Y (rs: one int per contraction row)
+void launch_emu_rowscale(const EmuPlan &P, const double *Z, const double *Y, int *rs, cudaStream_t st);
+// split one operand (A: scaled by 2^rs, B: by 2^-rs; rs may be null)
+void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st);
+void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st);
+void launch_emu_assemble(const EmuPlan &P, int N, const double *partial, const double *Yu, const double *diag,
+                         double *Khat, cudaStream_t st);
 bool tc_set_operands(TcPlan &P, const void *a_planes, const void *b_planes);
 void launch_split_t(long long krows, int nu, long long kpad, const float *src, void *planes, cudaStream_t st);
 void launch_tc_schur(const TcPlan &P, double *partial, int *flags, cudaStream_t st);

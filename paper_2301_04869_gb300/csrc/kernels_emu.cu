@@ -1,0 +1,518 @@
+// K6 on the tensor cores at FP64 grade: K_hat = sum_i Z_i^T Y_i with FP64
+// operands, computed by BF16 tcgen05 products of exact integer slices.
+//
+// GB300 runs FP64 at ~1.25 TFLOP/s but BF16 at ~2 PFLOP/s, so the FP64
+// contraction is emulated (an Ozaki-type error-free splitting).  For every
+// group of 512 contraction rows and every column j, an operand column is
+// scaled by a power of two 2^-e (e = ilogb(max |.|) + 2, so |x| 2^-e < 1/2),
+// rounded to a multiple of 2^-56 and written as eight 7-bit integer slices,
+//     x 2^-e = sum_{t=1..8} q_t 2^-7t + r,   q_t integer, |q_t| <= 64,
+//     |r| <= 2^-57,
+// each exact in BF16.  A product of slices q_t q'_u is an integer of at most
+// 2^12; the pairs with t + u = L + 2 (L = 0..7, 36 pairs in all) accumulate
+// in their own FP32 TMEM accumulator ("level" L), whose partial sums over
+// 512 rows stay integers of at most 8 * 2^12 * 512 = 2^24 and are therefore
+// exact.  The dropped pairs and the remainders weigh about 2^-52 of the
+// product of the group's largest entries of the two columns, per row; rows
+// are balanced first (k_emu_rowscale) so that those largest entries belong
+// to the same rows as far as a power-of-two row scaling can arrange.  After
+// each group the epilogue combines the eight levels into two exact 64-bit
+// integers (levels 0-5 and levels 6-7), converts their sum to FP64 (two
+// roundings) and accumulates it, scaled by 2^(e_A + e_B - 49), in FP64.
+//
+// Tiles are 128 (rows of K_hat) x 64 (columns), upper part only; one stage
+// of operands (8 x 16 KB + 8 x 8 KB); TMEM holds the eight 64-column level
+// accumulators (all 512 columns).  Warp 0 issues the TMA loads, warp 1 the MMAs, warps 2-9
+// drain the levels (lane quarter x column half); every wait is bounded as in
+// the BF16x3 kernel (kernels_tc.cu).  A non-finite sum raises FLAG_NONFINITE and
+// the caller redoes the contraction on the FP64 units.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/ipm.h"
+#include "dev.cuh"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace emu {
+
+using namespace tcx;
+
+constexpr int NS = 8;                      // slices per operand
+constexpr int BM = 128, BN = 64, BK = 64;  // tile
+constexpr int GROUP = 512;                 // rows per exact level sum
+constexpr int KB_PER_GROUP = GROUP / BK;
+constexpr int A_PLANE = BM * BK * 2;  // 16 KB
+constexpr int B_PLANE = BN * BK * 2;  // 8 KB
+constexpr int STAGE_BYTES = NS * (A_PLANE + B_PLANE);
+constexpr int SMEM_BYTES = STAGE_BYTES + 1024 + 256;
+
+struct Maps {
+  CUtensorMap a[NS], b[NS];
+};
+
+// ---------------------------------------------------------------------------
+// Splitting, in integer arithmetic on the FP64 bit patterns (the FP64 units
+// of GB300 are too slow for ~30 operations per element).  Inputs below
+// 2^-1022 (subnormal) count as zero.
+//
+// FP64 bits -> (biased exponent E, 53-bit integer mantissa m), |x| = m 2^(E-1075)
+__device__ __forceinline__ void dsplit_bits(double x, int &E, long long &m, bool &neg) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  neg = (b >> 63) != 0;
+  E = (int)((b >> 52) & 0x7FF);
+  m = (long long)(b & 0xFFFFFFFFFFFFFull) | (1ll << 52);
+  if (E == 0) m = 0;  // zero and subnormals
+}
+
+// The group-and-column scaled operand as a fixed-point integer:
+// X = round-half-away(|x| 2^(56 - e)) with the sign of x, |X| <= 2^55, where
+// the balanced biased exponent is E + shift_rows.
+__device__ __forceinline__ long long fixed56(int E, long long m, bool neg, int e) {
+  if (m == 0) return 0;
+  const int sh = E - 1019 - e;  // (E - 1075) + 56 - e
+  long long X;
+  if (sh >= 0) X = m << sh;     // sh <= 2 because |x| < 2^(e - 1)
+  else if (sh <= -63) X = 0;
+  else X = (m + (1ll << (-sh - 1))) >> (-sh);
+  return neg ? -X : X;
+}
+
+// FP64 [krows][nu] -> NS BF16 slice planes [NS][nu][kpad] (K-major) and the
+// exponents [kpad / GROUP][nu].  Row k is first scaled by 2^(rsign rs[k])
+// (row balancing; rs may be null).  Column exponent of a row group:
+// e = ilogb(max |x|) + 2.  Digits of X in base 2^7, rounded half up:
+//   R = X; q_t = floor((R + 2^(s-1)) / 2^s), R -= q_t 2^s, s = 56 - 7t
+// (t = 1..8; q_8 = R), so |q_t| <= 64 and x 2^-e = sum_t q_t 2^-7t up to
+// the rounding of X (2^-57).  CTA: one row group x 32 columns.
+__global__ void __launch_bounds__(256) k_emu_split(long long krows, int nu, long long kpad,
+                                                   const double *__restrict__ src, const int *__restrict__ rs,
+                                                   int rsign, __nv_bfloat16 *planes, int *exps) {
+  __shared__ int es[32];
+  __shared__ __nv_bfloat16 sl[NS][32][34];
+  const long long g = blockIdx.x;
+  const int j0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const long long r0 = g * GROUP;
+  const int j = j0 + tx;
+  // largest balanced magnitude: compare (biased exponent, mantissa) as one
+  // unsigned key; balanced exponents outside 1..2047 count as zero / clamp
+  unsigned long long key = 0;
+  for (int r = ty; r < GROUP; r += 8) {
+    const long long k = r0 + r;
+    if (k < krows && j < nu) {
+      int E;
+      long long m;
+      bool neg;
+      dsplit_bits(src[k * nu + j], E, m, neg);
+      if (m) {
+        E += rs ? rsign * rs[k] : 0;
+        if (E > 0) key = max(key, ((unsigned long long)min(E, 2047) << 53) | (unsigned long long)m);
+      }
+    }
+  }
+  __shared__ unsigned long long kred[8][32];
+  kred[ty][tx] = key;
+  __syncthreads();
+  if (ty == 0) {
+    unsigned long long kk = kred[0][tx];
+    for (int q = 1; q < 8; ++q) kk = max(kk, kred[q][tx]);
+    const int e = kk > 0 ? (int)(kk >> 53) - 1023 + 2 : 0;
+    es[tx] = e;
+    if (j < nu) exps[g * nu + j] = e;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)nu * kpad;
+  for (int c = 0; c < GROUP; c += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const long long k = r0 + c + r;
+      long long R = 0;
+      if (k < krows && j < nu) {
+        int E;
+        long long m;
+        bool neg;
+        dsplit_bits(src[k * nu + j], E, m, neg);
+        if (m) R = fixed56(E + (rs ? rsign * rs[k] : 0), m, neg, es[tx]);
+      }
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int sh = 49 - 7 * t;
+        const long long q = sh > 0 ? (R + (1ll << (sh - 1))) >> sh : R;
+        R -= q << sh;
+        sl[t][tx][r] = __int2bfloat16_rn((int)q);
+      }
+    }
+    __syncthreads();
+    for (int jj = ty; jj < 32; jj += 8) {
+      const int jc = j0 + jj;
+      if (jc < nu) {
+#pragma unroll
+        for (int t = 0; t < NS; ++t) planes[t * plane + (size_t)jc * kpad + r0 + c + tx] = sl[t][jj][tx];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Row balancing: Z^T Y = (D Z)^T (D^-1 Y) for any diagonal D; with
+// D_kk = 2^a_k, a_k = (ilogb max_j |Y_kj| - ilogb max_j |Z_kj|) / 2 (C
+// division), the two operands' rows meet halfway, so a row whose Y is large
+// because of a large barrier term no longer sets the scale of the whole row
+// group of Y alone.  One warp per row; exponents from the bit patterns.
+__global__ void k_emu_rowscale(long long krows, int nu, const double *__restrict__ Z, const double *__restrict__ Y,
+                               int *rs) {
+  const long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= krows) return;
+  int ez = 0, ey = 0;  // largest biased exponents (0: no normal entry)
+  for (int j = lane; j < nu; j += 32) {
+    ez = max(ez, (int)(((unsigned long long)__double_as_longlong(Z[k * nu + j]) >> 52) & 0x7FF));
+    ey = max(ey, (int)(((unsigned long long)__double_as_longlong(Y[k * nu + j]) >> 52) & 0x7FF));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ez = max(ez, __shfl_down_sync(0xffffffffu, ez, o));
+    ey = max(ey, __shfl_down_sync(0xffffffffu, ey, o));
+  }
+  if (lane == 0) rs[k] = (ez > 0 && ey > 0) ? (ey - ez) / 2 : 0;
+}
+
+__device__ __forceinline__ void tile_of_index(const int2 *tiles, int t, int &ti, int &tj) {
+  const int2 v = tiles[t];
+  ti = v.x;
+  tj = v.y;
+}
+
+__global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Maps maps, const int2 *tiles,
+                                                      int nu, int kb_total, int kb_per_group,
+                                                      const int *__restrict__ expA, const int *__restrict__ expB,
+                                                      double *partial, int *flags) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGE_BYTES);
+  uint64_t *empty = full + 1;
+  uint64_t *acc_full = empty + 1;
+  uint64_t *acc_empty = acc_full + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int ti, tj;
+  tile_of_index(tiles, blockIdx.x, ti, tj);
+  const int kb0 = blockIdx.y * kb_per_group;
+  const int kb1 = min(kb_total, kb0 + kb_per_group);
+  const int nkb = kb1 - kb0;               // a multiple of KB_PER_GROUP
+  const int ngr = nkb / KB_PER_GROUP;
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(empty, 1);
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 8);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {  // TMEM: eight 64-column FP32 level accumulators (all 512 columns)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  int issued = 0;
+
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nkb; ++i) {
+      if (i >= 1 && !mbar_wait(empty, (i - 1) & 1)) {
+        flags[FLAG_TIMEOUT] = 1;
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      mbar_expect_tx(full, STAGE_BYTES);
+      const int kx = (kb0 + i) * BK;
+      for (int p = 0; p < NS; ++p) tma_load_2d(smem + p * A_PLANE, &maps.a[p], full, kx, ti * BM);
+      for (int p = 0; p < NS; ++p) tma_load_2d(smem + NS * A_PLANE + p * B_PLANE, &maps.b[p], full, kx, tj * BN);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    const uint32_t abase = smem_u32(smem), bbase = abase + NS * A_PLANE;
+    for (int i = 0; i < nkb; ++i) {
+      const int d = i / KB_PER_GROUP, kbi = i % KB_PER_GROUP;
+      if (kbi == 0 && d >= 1 && !mbar_wait(acc_empty, (d - 1) & 1)) {
+        flags[FLAG_TIMEOUT] = 1;
+        *abort_flag = 1;
+        break;
+      }
+      if (!mbar_wait(full, i & 1)) {
+        flags[FLAG_TIMEOUT] = 1;
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+        for (int L = 0; L < NS; ++L) {
+#pragma unroll
+          for (int t = 0; t <= L; ++t) {
+            const int u = L - t;
+            const uint32_t acc = (kbi > 0 || kk > 0 || t > 0) ? 1u : 0u;
+            mma_bf16(tmem + (uint32_t)(L * BN), sdesc(abase + t * A_PLANE + kk * 32),
+                     sdesc(bbase + u * B_PLANE + kk * 32), idesc, acc);
+          }
+        }
+      }
+      mma_commit(empty);
+      if (kbi == KB_PER_GROUP - 1) mma_commit(acc_full);
+    }
+  } else if (warp >= 2) {
+    // eight epilogue warps: lane quarter q (the TMEM lanes a warp may read)
+    // and column half h of the 64-column tile
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const int gi = ti * BM + row;  // row of K_hat
+    constexpr int HC = BN / 2;
+    double acc[HC];
+#pragma unroll
+    for (int c = 0; c < HC; ++c) acc[c] = 0.0;
+    bool bad = false;
+    for (int d = 0; d < ngr; ++d) {
+      if (!mbar_wait(acc_full, d & 1)) {
+        flags[FLAG_TIMEOUT] = 1;
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const long long g = (kb0 / KB_PER_GROUP) + d;
+      const int ea = gi < nu ? expA[g * nu + gi] : 0;
+#pragma unroll
+      for (int c0 = 0; c0 < HC; c0 += 16) {
+        // the group's value in units of 2^(e_A + e_B - 49):
+        // V = sum_{L <= 5} acc_L 2^(7 (5 - L)) (an exact integer of at most
+        // 2^60) plus W 2^-14, W = acc_6 2^7 + acc_7 (exact)
+        long long V[16], W[16];
+#pragma unroll
+        for (int L = 0; L < NS; ++L) {
+          uint32_t v[16];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(L * BN + h * HC + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const long long a = (long long)__float2ll_rn(__uint_as_float(v[e]));  // exact: an integer
+            if (L == 0) V[e] = a;
+            else if (L <= 5) V[e] = (V[e] << 7) + a;
+            else if (L == 6) W[e] = a << 7;
+            else W[e] += a;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int gj = tj * BN + h * HC + c0 + e;
+          const int eb = gj < nu ? expB[g * nu + gj] : 0;
+          // V + W 2^-14 with one rounding of V and one of the sum
+          const double t = fma(__ll2double_rn(W[e]), 0x1p-14, __ll2double_rn(V[e]));
+          const int x = ea + eb - 49;
+          const double sc = (x > -1023 && x < 1024) ? __hiloint2double((x + 1023) << 20, 0) : ldexp(1.0, x);
+          acc[c0 + e] = fma(t, sc, acc[c0 + e]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty)) : "memory");
+    }
+    double *out = partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * BM * BN + (size_t)row * BN + h * HC;
+#pragma unroll
+    for (int c = 0; c < HC; ++c) {
+      bad |= !isfinite(acc[c]);
+      out[c] = acc[c];
+    }
+    if (bad) flags[FLAG_NONFINITE] = 1;
+  }
+  if (warp == 0 && lane == 0 && *abort_flag && issued > 0) (void)mbar_wait(full, (issued - 1) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// K_hat[i][j] = K_hat[j][i] = sum_g partial + sum_s Yu[s] + diag  (i <= j)
+__global__ void k_emu_assemble(int nu, int N, int ngroups, int ntiles, int ntn, const double *__restrict__ partial,
+                               const int *__restrict__ tile_of, const double *__restrict__ Yu,
+                               const double *__restrict__ diag, double *Khat) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nu * nu) return;
+  const int i = (int)(t / nu), j = (int)(t % nu);
+  if (i > j) return;
+  const int ti = i / BM, tj = j / BN;
+  const int tt = tile_of[ti * ntn + tj];
+  double v = 0.0;
+  for (int g = 0; g < ngroups; ++g) v += partial[((size_t)g * ntiles + tt) * BM * BN + (i - ti * BM) * BN + (j - tj * BN)];
+  if (Yu)
+    for (int s = 0; s < N; ++s) v += Yu[(size_t)s * nu * nu + (size_t)i * nu + j];
+  if (diag && i == j) v += diag[i];
+  Khat[(size_t)i * nu + j] = v;
+  Khat[(size_t)j * nu + i] = v;
+}
+
+}  // namespace emu
+
+size_t emu_planes_bytes(int nu, long long krows) {
+  const long long kpad = (krows + emu::GROUP - 1) / emu::GROUP * emu::GROUP;
+  return (size_t)emu::NS * nu * kpad * 2;
+}
+
+bool emu_plan(EmuPlan &P, int nu, long long krows, const void *a_planes, const void *b_planes, int *exp_a,
+              int *exp_b, int2 *tiles_dev, int *tile_of_dev) {
+  P.nu = nu;
+  P.krows = krows;
+  P.kpad = (krows + emu::GROUP - 1) / emu::GROUP * emu::GROUP;
+  P.kb_total = (int)(P.kpad / emu::BK);
+  P.ntm = (nu + emu::BM - 1) / emu::BM;
+  P.ntn = (nu + emu::BN - 1) / emu::BN;
+  std::vector<int2> tl;
+  std::vector<int> tof((size_t)P.ntm * P.ntn, -1);
+  for (int a = 0; a < P.ntm; ++a)
+    for (int b = 0; b < P.ntn; ++b)
+      if (a * emu::BM <= b * emu::BN + emu::BN - 1) {
+        tof[(size_t)a * P.ntn + b] = (int)tl.size();
+        tl.push_back(make_int2(a, b));
+      }
+  P.ntiles = (int)tl.size();
+  P.tiles = tiles_dev;
+  P.tile_of = tile_of_dev;
+  if (cudaMemcpy(tiles_dev, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+  if (cudaMemcpy(tile_of_dev, tof.data(), tof.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  emu_regroup(P, 152 / P.ntiles);
+  P.a_planes = a_planes;
+  P.b_planes = b_planes;
+  P.exp_a = exp_a;
+  P.exp_b = exp_b;
+  emu::Maps m;
+  const size_t plane = (size_t)nu * P.kpad * 2;
+  for (int p = 0; p < emu::NS; ++p) {
+    if (!tc_make_kmajor_map_box(&m.a[p], (const char *)a_planes + p * plane, nu, P.kpad, emu::BM)) return false;
+    if (!tc_make_kmajor_map_box(&m.b[p], (const char *)b_planes + p * plane, nu, P.kpad, emu::BN)) return false;
+  }
+  static_assert(sizeof(emu::Maps) <= sizeof(P.maps), "map storage");
+  memcpy(P.maps, &m, sizeof(m));
+  return true;
+}
+
+void emu_regroup(EmuPlan &P, int G) {
+  const int ngr = P.kb_total / emu::KB_PER_GROUP;  // row groups
+  if (G < 1) G = 1;
+  if (G > ngr) G = ngr;
+  const int gpg = (ngr + G - 1) / G;  // row groups per CTA
+  P.kb_per_group = gpg * emu::KB_PER_GROUP;
+  P.ngroups = (ngr + gpg - 1) / gpg;
+}
+
+long long emu_kpad(long long krows) { return (krows + emu::GROUP - 1) / emu::GROUP * emu::GROUP; }
+
+void launch_emu_rowscale(const EmuPlan &P, const double *Z, const double *Y, int *rs, cudaStream_t st) {
+  const long long thr = P.krows * 32;
+  emu::k_emu_rowscale<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(P.krows, P.nu, Z, Y, rs);
+  ipm_count_launch();
+}
+
+void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st) {
+  dim3 grid((unsigned)(P.kpad / emu::GROUP), (unsigned)((P.nu + 31) / 32));
+  emu::k_emu_split<<<grid, dim3(32, 8), 0, st>>>(P.krows, P.nu, P.kpad, src, rs, b_side ? -1 : 1,
+                                                 (__nv_bfloat16 *)(b_side ? P.b_planes : P.a_planes),
+                                                 b_side ? P.exp_b : P.exp_a);
+  ipm_count_launch();
+}
+
+void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st) {
+  static const bool attr = cudaFuncSetAttribute(emu::k_emu_schur, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                emu::SMEM_BYTES) == cudaSuccess;
+  (void)attr;
+  emu::Maps m;
+  memcpy(&m, P.maps, sizeof(m));
+  dim3 grid(P.ntiles, P.ngroups);
+  emu::k_emu_schur<<<grid, 320, emu::SMEM_BYTES, st>>>(m, P.tiles, P.nu, P.kb_total, P.kb_per_group, P.exp_a,
+                                                      P.exp_b, partial, flags);
+  ipm_count_launch();
+}
+
+void launch_emu_assemble(const EmuPlan &P, int N, const double *partial, const double *Yu, const double *diag,
+                         double *Khat, cudaStream_t st) {
+  const long long tot = (long long)P.nu * P.nu;
+  emu::k_emu_assemble<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P.nu, N, P.ngroups, P.ntiles, P.ntn, partial,
+                                                                      P.tile_of, Yu, diag, Khat);
+  ipm_count_launch();
+}
+
+size_t emu_partial_doubles(const EmuPlan &P, int max_groups) {
+  return (size_t)max_groups * P.ntiles * emu::BM * emu::BN;
+}
+
+// ---------------------------------------------------------------------------
+// Stand-alone entry point (include/ipm.h): the emulated contraction on
+// caller-owned device matrices, for checking the kernel on arbitrary data.
+extern "C" ipm_status ipm_schur_sum_tc(const double *Z, const double *Y, int n_scen, int n_x, int n_u,
+                                       double *Khat, void *stream) {
+  if (!Z || !Y || !Khat || n_scen < 1 || n_x < 1 || n_u < 1) return IPM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long krows = (long long)n_scen * n_x;
+  const size_t pb = emu_planes_bytes(n_u, krows);
+  const long long ngr = emu_kpad(krows) / emu::GROUP;
+  const long long nt = (long long)((n_u + emu::BM - 1) / emu::BM) * ((n_u + emu::BN - 1) / emu::BN);
+  void *pa = nullptr, *pbp = nullptr, *part = nullptr;
+  int *ea = nullptr, *eb = nullptr, *tof = nullptr, *flags = nullptr, *rsd = nullptr;
+  int2 *tiles = nullptr;
+  ipm_status rc = IPM_OK;
+  EmuPlan P;
+  int hf[FLAG_COUNT] = {0};
+  if (cudaMalloc(&pa, pb) != cudaSuccess || cudaMalloc(&pbp, pb) != cudaSuccess ||
+      cudaMalloc(&ea, ngr * n_u * sizeof(int)) != cudaSuccess || cudaMalloc(&eb, ngr * n_u * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&tiles, nt * sizeof(int2)) != cudaSuccess || cudaMalloc(&tof, nt * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&flags, FLAG_COUNT * sizeof(int)) != cudaSuccess) {
+    rc = IPM_ERR_OOM;
+    goto done;
+  }
+  if (!emu_plan(P, n_u, krows, pa, pbp, ea, eb, tiles, tof)) {
+    rc = IPM_ERR_CUDA;
+    goto done;
+  }
+  if (cudaMalloc(&part, emu_partial_doubles(P, P.ngroups) * sizeof(double)) != cudaSuccess) {
+    rc = IPM_ERR_OOM;
+    goto done;
+  }
+  if (cudaMalloc(&rsd, krows * sizeof(int)) != cudaSuccess) {
+    rc = IPM_ERR_OOM;
+    goto done;
+  }
+  cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st);
+  launch_emu_rowscale(P, Z, Y, rsd, st);
+  launch_emu_split(P, Z, false, rsd, st);
+  launch_emu_split(P, Y, true, rsd, st);
+  launch_emu_schur(P, (double *)part, flags, st);
+  launch_emu_assemble(P, n_scen, (const double *)part, nullptr, nullptr, Khat, st);
+  if (cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    rc = IPM_ERR_CUDA;
+    goto done;
+  }
+  if (hf[FLAG_TIMEOUT]) rc = IPM_ERR_TIMEOUT;
+  else if (hf[FLAG_NONFINITE]) rc = IPM_ERR_ARG;
+done:
+  cudaStreamSynchronize(st);
+  for (void *p : {pa, pbp, part, (void *)ea, (void *)eb, (void *)tof, (void *)flags, (void *)tiles, (void *)rsd})
+    if (p) cudaFree(p);
+  return rc;
+}

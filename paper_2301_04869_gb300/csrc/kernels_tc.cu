@@ -278,13 +278,13 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-// tensor map of one BF16 plane [rows][kpad], box 64 (K) x 128 (rows), 128-byte swizzle
-static bool make_map(CUtensorMap *m, const void *base, int rows, long long kpad) {
+// tensor map of one BF16 plane [rows][kpad], box 64 (K) x box_rows, 128-byte swizzle
+static bool make_map(CUtensorMap *m, const void *base, int rows, long long kpad, int box_rows = tc::BM) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-  cuuint32_t box[2] = {tc::BK, tc::BM};
+  cuuint32_t box[2] = {tc::BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -293,6 +293,10 @@ static bool make_map(CUtensorMap *m, const void *base, int rows, long long kpad)
 
 bool tc_make_kmajor_map(void *map, const void *base, int rows, long long k) {
   return make_map(reinterpret_cast<CUtensorMap *>(map), base, rows, k);
+}
+
+bool tc_make_kmajor_map_box(void *map, const void *base, int rows, long long k, int box_rows) {
+  return make_map(reinterpret_cast<CUtensorMap *>(map), base, rows, k, box_rows);
 }
 
 void tc_plan(int nu, long long krows, TcPlan &P) {

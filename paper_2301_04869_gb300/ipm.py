@@ -19,8 +19,8 @@ IPM_OK = 0
 STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_CUDA", 3: "IPM_ERR_OOM",
           4: "IPM_ERR_SINGULAR_GX", 5: "IPM_ERR_NOT_PD", 6: "IPM_ERR_LINESEARCH",
           7: "IPM_ERR_MAXITER", 8: "IPM_ERR_TIMEOUT", 9: "IPM_ERR_STATE"}
-PREC_FP64, PREC_MIXED = 0, 1
-Q_KHAT, Q_RHS_U, Q_Z, Q_FGH, Q_JAC, Q_HESS, Q_ERRS, Q_INFO, Q_TIMERS = range(9)
+PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
+Q_KHAT, Q_RHS_U, Q_Z, Q_FGH, Q_JAC, Q_HESS, Q_ERRS, Q_INFO, Q_TIMERS, Q_ZTZ = range(10)
 N_PHASES = 9
 PHASES = ("eval", "condense_K", "lu", "zsolve", "gemm", "reduced_rhs", "cholesky", "recover", "linesearch")
 
@@ -100,6 +100,8 @@ def load():
         "ipm_mlp_forward": (c_int, [vp, vp, c_int, vp, vp]),
         "ipm_mlp_gradients": (c_int, [vp, vp, vp, c_int, _F, _F, vp]),
         "ipm_mlp_train_step": (c_int, [vp, vp, vp, c_int, ctypes.c_float, _F, vp]),
+        "ipm_schur_sum_tc": (c_int, [vp, vp, c_int, c_int, c_int, vp, vp]),
+        "ipm_schur_sum_noalloc": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, vp, vp]),
         "ipm_warm_dim": (c_int, [vp, _I]),
         "ipm_warm_target": (c_int, [vp, vp, vp]),
         "ipm_warm_start": (c_int, [vp, vp, vp]),
@@ -274,7 +276,7 @@ class Solver:
         sizes = {Q_KHAT: d.n_u * d.n_u, Q_RHS_U: d.n_u, Q_Z: d.n_x * d.n_u, Q_FGH: 1 + d.n_x + d.m,
                  Q_JAC: d.n_x * d.n_x + d.n_x * d.n_u + d.m * d.n_x + d.m * d.n_u,
                  Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 10,
-                 Q_TIMERS: 2 * N_PHASES + 1}
+                 Q_TIMERS: 2 * N_PHASES + 1, Q_ZTZ: d.n_u * d.n_u}
         out = np.empty(sizes[which])
         self._check(self._lib.ipm_get_quantity(self._h, which, scen, _ptr(out, ctypes.c_double), out.size,
                                                _stream(stream)))

@@ -53,9 +53,10 @@ def case(name):
     return _cache[name]
 
 
-def solver_at(gpu, name):
+def solver_at(gpu, name, precision="fp64"):
     net, pd, qd, M, st = case(name)
-    sol = gpu.Solver(net, pd, qd)
+    prec = {"fp64": gpu.PREC_FP64, "fp64_tc": gpu.PREC_FP64_TC}[precision]
+    sol = gpu.Solver(net, pd, qd, precision=prec)
     sol.ipm_set_state(sol.pack_state(st))
     return sol
 
@@ -83,10 +84,16 @@ def test_eval_parity(gpu, name):
         assert rel(jac[o3:].reshape(m, nu), o["Hu"].toarray()) <= TOL
 
 
+# fp64_tc: the same FP64 path with the K_hat contraction emulated on the
+# tensor cores (exact BF16 slices); it must meet the same FP64 bar
+PRECS = ["fp64", "fp64_tc"]
+
+
+@pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_condense_parity(gpu, name):
+def test_condense_parity(gpu, name, precision):
     net, pd, qd, M, st = case(name)
-    sol = solver_at(gpu, name)
+    sol = solver_at(gpu, name, precision)
     sol.ipm_eval_derivatives()
     sol.ipm_condense_scenarios()
     D = kkt.eval_all(M, st)
@@ -110,12 +117,13 @@ def test_condense_parity(gpu, name):
     assert np.array_equal(K, K2)
 
 
+@pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("delta", [0.0, 0.37])
-def test_newton_step_parity(gpu, name, delta):
+def test_newton_step_parity(gpu, name, delta, precision):
     import torch
     net, pd, qd, M, st = case(name)
-    sol = solver_at(gpu, name)
+    sol = solver_at(gpu, name, precision)
     sol.ipm_eval_derivatives()
     sol.ipm_condense_scenarios()
     assert sol.ipm_factor_schur(delta)
@@ -130,11 +138,12 @@ def test_newton_step_parity(gpu, name, delta):
         assert rel(g[k], p[k]) <= 1e-9, k
 
 
-def test_full_solve_same_iterations_30(gpu):
+@pytest.mark.parametrize("precision", PRECS)
+def test_full_solve_same_iterations_30(gpu, precision):
     net, pd, qd = synth.workload("opf30_n1")
     M = opf.Model(net, pd, qd)
     st_o, k_o, log = oipm.solve(M)
-    sol = gpu.Solver(net, pd, qd)
+    sol = gpu.Solver(net, pd, qd, precision=gpu.PREC_FP64 if precision == "fp64" else gpu.PREC_FP64_TC)
     k_g, e_g = sol.ipm_solve()
     assert k_g == k_o
     assert e_g <= 1e-8
@@ -143,11 +152,12 @@ def test_full_solve_same_iterations_30(gpu):
     np.testing.assert_allclose(s["x"], st_o["x"], rtol=0, atol=1e-8)
 
 
-def test_full_solve_same_iterations_1000_N4(gpu):
+@pytest.mark.parametrize("precision", PRECS)
+def test_full_solve_same_iterations_1000_N4(gpu, precision):
     net, pd, qd = synth.workload("opf1000_n64", n_scen=4)
     M = opf.Model(net, pd, qd)
     st_o, k_o, _ = oipm.solve(M)
-    sol = gpu.Solver(net, pd, qd)
+    sol = gpu.Solver(net, pd, qd, precision=gpu.PREC_FP64 if precision == "fp64" else gpu.PREC_FP64_TC)
     k_g, e_g = sol.ipm_solve()
     assert k_g == k_o
     assert e_g <= 1e-8
