@@ -2,11 +2,16 @@
 
 Metric: scenario condensations per second (one scenario condensed and reduced
 at one interior-point iteration = one condensation) and seconds per IPM
-iteration, on the 1000-bus / 64-scenario two-stage OPF workload (FP64 path).
-A step is one full IPM iteration (evaluation, condensation, reduction,
-Cholesky with inertia correction, step recovery, line search) over all
-scenarios; the states cycle through complete solves from the cold start
-(re-initialised, untimed, whenever a solve converges).
+iteration, on the 1000-bus / 64-scenario two-stage OPF workload.  A step is
+one full IPM iteration (evaluation, condensation, reduction, Cholesky with
+inertia correction, step recovery, line search) over all scenarios; the
+states cycle through complete solves from the cold start (re-initialised,
+untimed, whenever a solve converges).
+
+The headline path is --precision (default fp64_tc: FP64 results, the K_hat
+contraction emulated on the BF16 tensor cores); the other two paths (fp64 on
+the FP64 units, mixed BF16x3 with FP64 refinement) are timed too and reported
+under "paths" unless --no-compare.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -198,6 +203,90 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush, want_e2e=True):
+    """Time `steps` IPM iterations of one precision path (device events per step,
+    L2 flushed between steps; graphs and autotuned launch shapes on), then the
+    same number again with the phase timers on, and the end-to-end variant."""
+    import torch
+    prec = {"fp64": ipm.PREC_FP64, "mixed": ipm.PREC_MIXED, "fp64_tc": ipm.PREC_FP64_TC}[precision]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = ipm.Solver(net, pd, qd, precision=prec, graphs=True, autotune=True)
+        dims = sol.dims
+        N = dims.n_scen
+
+        def step():
+            conv, _ = sol.ipm_step(stream=stream)
+            if conv:  # a converged check takes no step: restart (untimed) and redo
+                sol.ipm_init_state(stream=stream)
+                conv, _ = sol.ipm_step(stream=stream)
+
+        for _ in range(warmup):
+            step()
+        _, launches0 = sol.timers()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            for k in range(steps):
+                flush.fill_(float(k))  # larger than L2: evicts the previous step's data
+                ev[k][0].record(stream)
+                conv, _ = sol.ipm_step(stream=stream)
+                ev[k][1].record(stream)
+                if conv:
+                    sol.ipm_init_state(stream=stream)
+                    flush.fill_(float(k))
+                    ev[k][0].record(stream)
+                    sol.ipm_step(stream=stream)
+                    ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        _, launches1 = sol.timers()
+        tot_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if world > 1:
+            t = torch.tensor([tot_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot_ms = float(t.item())
+        # phase breakdown (events between phases; graphs are off while profiling)
+        sol.ipm_set_profiling(2)
+        for k in range(steps):
+            flush.fill_(float(k))
+            step()
+        torch.cuda.synchronize()
+        phases, _ = sol.timers()
+        sol.ipm_set_profiling(0)
+        e2e_val = None
+        if want_e2e:
+            # end to end through the C ABI with host buffers: state in from pinned
+            # host memory, one IPM iteration, state out to host memory, every step
+            host = torch.empty(dims.state_len, dtype=torch.float64, pin_memory=True)
+            hnp = host.numpy()
+            sol.ipm_get_state(hnp, stream=stream)
+            e2e = []
+            for k in range(max(3, steps // 2)):
+                flush.fill_(float(k))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sol.ipm_set_state(hnp, stream=stream)
+                conv, _ = sol.ipm_step(stream=stream)
+                sol.ipm_get_state(hnp, stream=stream)
+                torch.cuda.synchronize()
+                e2e.append(time.perf_counter() - t0)
+                if conv:
+                    sol.ipm_init_state(stream=stream)
+                    sol.ipm_get_state(hnp, stream=stream)
+            e2e_val = world * N * len(e2e) / sum(e2e)
+    per = {p: phases[p][0] / steps for p in phases}
+    cond = ("condense_K", "lu", "zsolve", "split", "gemm", "reduced_rhs")
+    cond_ms = sum(per[p] for p in cond)
+    return dict(sol=sol, dims=dims, N=N, tot_ms=tot_ms, value=world * N * steps / (tot_ms / 1e3),
+                ms_per_step=tot_ms / steps, phases=phases, phases_ms_per_step=per,
+                condense_only=N / (cond_ms / 1e3) if cond_ms > 0 else None,
+                launches=launches1 - launches0, clocks=clk.summary(), e2e=e2e_val)
+
+
 def run_ours(args):
     import torch
     from paper_2301_04869_gb300 import ipm
@@ -210,101 +299,52 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     net, pd, qd = synth.workload(args.workload)
-    prec = {"fp64": ipm.PREC_FP64, "mixed": ipm.PREC_MIXED, "fp64_tc": ipm.PREC_FP64_TC}[args.precision]
-    sol = ipm.Solver(net, pd, qd, precision=prec)
-    dims = sol.dims
-    N = dims.n_scen
-    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def one_step():
-        conv, err = sol.ipm_step()
-        if conv:
-            sol.ipm_init_state()
-            conv, err = sol.ipm_step()
-        return conv
-
-    for _ in range(args.warmup):
-        one_step()
-    sol.ipm_set_profiling(2)
-    _, launches0 = sol.timers()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))  # larger than L2: evicts the previous step's data
-            ev[k][0].record(stream)
-            conv, _ = sol.ipm_step()
-            ev[k][1].record(stream)
-            if conv:  # a converged check takes no step: restart (untimed) and redo
-                sol.ipm_init_state()
-                flush.fill_(float(k))
-                ev[k][0].record(stream)
-                sol.ipm_step()
-                ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    phases, launches1 = sol.timers()
-    sol.ipm_set_profiling(0)
-    value = world * N * args.steps / (tot_ms / 1e3)
-    cond_ms = sum(phases[p][0] for p in ("condense_K", "lu", "zsolve", "gemm", "reduced_rhs"))
-    cond_calls = max(phases["lu"][1], 1)
-
-    # end to end through the C ABI with host buffers: state in from pinned host
-    # memory, one IPM iteration, state out to host memory, every step
-    host = torch.empty(dims.state_len, dtype=torch.float64, pin_memory=True)
-    hnp = host.numpy()
-    sol.ipm_get_state(hnp)
-    e2e = []
-    for k in range(max(3, args.steps // 2)):
-        flush.fill_(float(k))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sol.ipm_set_state(hnp)
-        conv, _ = sol.ipm_step()
-        sol.ipm_get_state(hnp)
-        torch.cuda.synchronize()
-        e2e.append(time.perf_counter() - t0)
-        if conv:
-            sol.ipm_init_state()
-            sol.ipm_get_state(hnp)
-    e2e_val = world * N * len(e2e) / sum(e2e)
-
+    main = measure_path(ipm, net, pd, qd, args.precision, args.steps, args.warmup, world, local, flush)
+    others = {}
+    if not args.no_compare:
+        for p in ("fp64", "fp64_tc", "mixed"):
+            if p != args.precision:
+                r = measure_path(ipm, net, pd, qd, p, max(5, args.steps // 2), args.warmup, world, local, flush,
+                                 want_e2e=False)
+                others[p] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                             "condense_only": r["condense_only"],
+                             "phases_ms_per_step": {k: round(v, 3) for k, v in r["phases_ms_per_step"].items()},
+                             "clocks": r["clocks"]}
+                del r
     if rank != 0:
         return
+    dims, N = main["dims"], main["N"]
     peaks, pk = load_peaks()
-    rl = roofline(phases, dims, peaks, pk, args.precision)
+    rl = roofline(main["phases"], dims, peaks, pk, args.precision)
     rl["peak_source"] = ("FP64 unit count x clock (2 FMA/clk/SM x 152 SMs x 2.07 GHz)" if rl["bound"] == "alu"
                          else (f"{pk} MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
                                if rl["bound"] == "tensor" else f"{pk} MEASURED_PEAKS.json hbm_gbs"))
     cb = cpu_baseline(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
+    paths = {args.precision: {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"],
+                              "condense_only": main["condense_only"]}}
+    paths.update(others)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "bf16x3+f64", "fp64_tc": "f64 (bf16 slices)"}[args.precision],
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "bf16x3+f64", "fp64_tc": "f64 (bf16 slices)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "n_bus": dims.n_bus, "n_scen": N, "n_x": dims.n_x, "n_u": dims.n_u,
                    "path": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "graphs": True, "autotune": True,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "s_per_ipm_iter": tot_ms / args.steps / 1e3,
-        "condense_only": {"value": N * cond_calls / (cond_ms / 1e3) if cond_ms > 0 else None, "unit": UNIT,
-                          "phases": ["condense_K", "lu", "zsolve", "gemm", "reduced_rhs"]},
-        "phases_ms_per_step": {p: phases[p][0] / args.steps for p in phases},
+        "s_per_ipm_iter": main["ms_per_step"] / 1e3,
+        "condense_only": {"value": main["condense_only"], "unit": UNIT,
+                          "phases": ["condense_K", "lu", "zsolve", "split", "gemm", "reduced_rhs"]},
+        "phases_ms_per_step": {k: round(v, 3) for k, v in main["phases_ms_per_step"].items()},
+        "paths": paths,
         "roofline": rl,
         "cpu_baseline": cb,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * dims.state_len,
+        "e2e": {"value": main["e2e"], "unit": UNIT, "h2d_bytes_per_step": 8 * dims.state_len,
                 "d2h_bytes_per_step": 8 * dims.state_len},
-        "gpu_launches": launches1 - launches0,
-        "clocks": clk.summary(),
+        "gpu_launches": main["launches"],
+        "clocks": main["clocks"],
     }
     print(json.dumps(line))
 
@@ -316,8 +356,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="opf1000_n64", choices=list(synth.CONFIGS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp64_tc"])
+    ap.add_argument("--precision", default="fp64_tc", choices=["fp64", "mixed", "fp64_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision paths")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

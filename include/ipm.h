@@ -200,8 +200,9 @@ ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
  * stream around each phase of the path and the elapsed device time is
  * accumulated; on = 2 also resets the accumulators.  Phases, in order:
  * eval, condense_K (Sigma, K, right-hand sides), lu, zsolve (Z and Y),
- * gemm (Z^T Y + scenario sum), reduced_rhs, cholesky, recover, linesearch. */
-enum { IPM_N_PHASES = 9 };
+ * gemm (Z^T Y + scenario sum), reduced_rhs, cholesky, recover, linesearch,
+ * split (the tensor-core operands of Z and Y: BF16 slices or planes). */
+enum { IPM_N_PHASES = 10 };
 ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
 
 /* Replace the scenario loads of a context (same network and N) and reset the

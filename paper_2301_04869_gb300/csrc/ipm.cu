@@ -308,7 +308,7 @@ ipm_status read_red(ipm_ctx *c, int nv, cudaStream_t st) {
 }
 
 
-enum { PH_EVAL = 0, PH_COND, PH_LU, PH_ZSOLVE, PH_GEMM, PH_RRHS, PH_CHOL, PH_RECOVER, PH_LS };
+enum { PH_EVAL = 0, PH_COND, PH_LU, PH_ZSOLVE, PH_GEMM, PH_RRHS, PH_CHOL, PH_RECOVER, PH_LS, PH_SPLIT };
 
 inline void ph_begin(ipm_ctx *c, int p, cudaStream_t st) {
   if (c->prof) cudaEventRecord(c->ev[2 * p], st);
@@ -410,8 +410,14 @@ ipm_status run_part(ipm_ctx *c, cudaGraphExec_t &gx, long long &gn, Fn fn, cudaS
     fn();
     const long long n = t_ipm_launches - n0;
     g_ipm_launches -= n;  // captured, not launched
+    const cudaError_t le = cudaGetLastError();  // a launch the capture refused
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (le != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return fail(c, IPM_ERR_CUDA, "kernel launch while capturing the condensation", le);
+    }
     if (e == cudaSuccess && g) e = cudaGraphInstantiate(&gx, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess || !gx) {
@@ -457,6 +463,7 @@ std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int, int>, Tuned> g_tune_cache;
 
 // milliseconds of fn on st (events; fn's outputs are overwritten by the caller's next run)
+// (a candidate whose launch fails reports +infinity and is not chosen)
 template <class Fn>
 double time_ms(Fn fn, cudaStream_t st, int reps = 2) {
   cudaEvent_t a, b;
@@ -471,6 +478,7 @@ double time_ms(Fn fn, cudaStream_t st, int reps = 2) {
   cudaEventElapsedTime(&ms, a, b);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (cudaGetLastError() != cudaSuccess) return std::numeric_limits<double>::infinity();
   return ms / reps;
 }
 
@@ -603,20 +611,21 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
     launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
     ph_begin(c, PH_ZSOLVE, st);
-    if (fp64) {
-      launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads);
-      if (c->emu) {
-        launch_emu_rowscale(c->emuZY, c->Z, c->Y, c->emu_rs, st);
-        launch_emu_split(c->emuZY, c->Z, false, c->emu_rs, st);
-        launch_emu_split(c->emuZY, c->Y, true, c->emu_rs, st);
-      }
-    } else {
-      // mixed: FP32 solves, BF16x3 planes for the tensor-core product
-      launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
+    if (fp64) launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads);
+    else launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
+    ph_end(c, PH_ZSOLVE, st);
+    ph_begin(c, PH_SPLIT, st);
+    if (fp64 && c->emu) {
+      // exact BF16 slices of the row-balanced Z and Y for the tensor cores
+      launch_emu_rowscale(c->emuZY, c->Z, c->Y, c->emu_rs, st);
+      launch_emu_split(c->emuZY, c->Z, false, c->emu_rs, st);
+      launch_emu_split(c->emuZY, c->Y, true, c->emu_rs, st);
+    } else if (!fp64) {
+      // mixed: BF16x3 planes of the FP32 Z and Y
       launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);
       launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
     }
-    ph_end(c, PH_ZSOLVE, st);
+    ph_end(c, PH_SPLIT, st);
   };
   auto post = [&] {
     if (fp64) {

@@ -213,24 +213,66 @@ __global__ void k_syrk_trail(int n, int k0, double *A) {
   }
 }
 
-// solve L L^T x = b in place (one CTA)
-__global__ void k_chol_solve(int n, const double *L, double *b) {
-  const int tid = threadIdx.x;
-  for (int k = 0; k < n; ++k) {
-    __syncthreads();
-    const double xk = b[k] / L[(size_t)k * n + k];
-    __syncthreads();
-    if (tid == 0) b[k] = xk;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) b[i] -= L[(size_t)i * n + k] * xk;
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    __syncthreads();
-    const double xk = b[k] / L[(size_t)k * n + k];
-    __syncthreads();
-    if (tid == 0) b[k] = xk;
-    for (int i = tid; i < k; i += blockDim.x) b[i] -= L[(size_t)k * n + i] * xk;
-  }
+// solve L L^T x = b in place (one CTA; x in shared memory).  Blocked by 32:
+// one warp solves each 32 x 32 diagonal block with shuffles, then all
+// threads apply the block's columns to the remaining rows (forward: rows of
+// L, contiguous per thread; backward: rows of L read across threads).
+__global__ void __launch_bounds__(256) k_chol_solve(int n, const double *__restrict__ L, double *b) {
+  extern __shared__ double x[];
+  __shared__ double blk[32][33];
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += bd) x[i] = b[i];
   __syncthreads();
+  for (int kb = 0; kb < n; kb += 32) {
+    const int w = min(32, n - kb);
+    for (int e = tid; e < 32 * 32; e += bd) {
+      const int r = e >> 5, c = e & 31;
+      blk[r][c] = (r < w && c <= r) ? L[(size_t)(kb + r) * n + kb + c] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double v = lane < w ? x[kb + lane] : 0.0;
+      for (int jj = 0; jj < w; ++jj) {
+        if (lane == jj) v /= blk[jj][jj];
+        const double xj = __shfl_sync(0xffffffffu, v, jj);
+        if (lane > jj) v -= blk[lane][jj] * xj;
+      }
+      if (lane < w) x[kb + lane] = v;
+    }
+    __syncthreads();
+    for (int i = kb + w + tid; i < n; i += bd) {
+      const double *row = L + (size_t)i * n + kb;
+      double s = 0.0;
+      for (int j = 0; j < w; ++j) s = fma(row[j], x[kb + j], s);
+      x[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int kb = ((n - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int w = min(32, n - kb);
+    for (int e = tid; e < 32 * 32; e += bd) {
+      const int r = e >> 5, c = e & 31;
+      blk[r][c] = (r < w && c <= r) ? L[(size_t)(kb + r) * n + kb + c] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double v = lane < w ? x[kb + lane] : 0.0;
+      for (int jj = w - 1; jj >= 0; --jj) {
+        if (lane == jj) v /= blk[jj][jj];
+        const double xj = __shfl_sync(0xffffffffu, v, jj);
+        if (lane < jj) v -= blk[jj][lane] * xj;  // (L^T)[lane][jj] = L[jj][lane]
+      }
+      if (lane < w) x[kb + lane] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < kb; i += bd) {
+      double s = 0.0;
+      for (int j = 0; j < w; ++j) s = fma(L[(size_t)(kb + j) * n + i], x[kb + j], s);
+      x[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += bd) b[i] = x[i];
 }
 
 }  // namespace
@@ -285,5 +327,7 @@ void launch_cholesky(int n, double *A, int *flags, cudaStream_t st) {
   }
 }
 void launch_chol_solve(int n, const double *L, double *b, cudaStream_t st) {
-  k_chol_solve<<<1, 1024, 0, st>>>(n, L, b); ipm_count_launch();
+  const size_t bytes = (size_t)n * sizeof(double);
+  if (bytes > 0) cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_chol_solve<<<1, 256, bytes, st>>>(n, L, b); ipm_count_launch();
 }

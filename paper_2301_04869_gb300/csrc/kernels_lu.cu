@@ -171,37 +171,93 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
     }
     __syncthreads();
     const int *ts = S.tail_slot;
-    // forward, dense unit-lower part, column by column
-    for (int k = 0; k < nd - 1; ++k) {
-      const int m = (nd - k - 1) * 32;
-      for (int e = tid; e < m; e += bd) {
-        const int i = k + 1 + (e >> 5), q = e & 31;
-        const T l = (T)A[ts[i * nd + k]];
-        if (tail_smem) sh[i * 32 + q] -= l * sh[k * 32 + q];
-        else if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] -= l * Zs[(size_t)(t0 + k) * nu + c0 + q];
+    if (tail_smem) {
+      // Blocked by 32 in shared memory: one warp solves each 32 x 32
+      // diagonal block (lane = RHS column), then every warp applies the
+      // block's columns to the remaining rows (warp = row, lane = column).
+      // Column c of the block is contiguous in LU storage: (a, c) sits at
+      // tail_slot[c] + a.  Backward values are scaled as they are found.
+      __shared__ double blkd[32][33];
+      for (int kb = 0; kb < nd; kb += 32) {
+        const int w = min(32, nd - kb);
+        for (int e = tid; e < 32 * 32; e += bd) {
+          const int rr = e >> 5, c2 = e & 31;
+          blkd[rr][c2] = (rr < w && c2 < rr) ? A[ts[kb + c2] + kb + rr] : 0.0;  // L(kb+rr, kb+c2)
+        }
+        __syncthreads();
+        if (warp == 0) {
+          for (int jj = 0; jj < w; ++jj) {
+            const T xj = sh[(kb + jj) * 32 + lane];
+            for (int i2 = jj + 1; i2 < w; ++i2) sh[(kb + i2) * 32 + lane] -= (T)blkd[i2][jj] * xj;
+          }
+        }
+        __syncthreads();
+        for (int i = kb + w + warp; i < nd; i += nw) {
+          T acc = sh[i * 32 + lane];
+          for (int j = 0; j < w; ++j) acc -= (T)A[ts[kb + j] + i] * sh[(kb + j) * 32 + lane];
+          sh[i * 32 + lane] = acc;
+        }
+        __syncthreads();
       }
-      __syncthreads();
-    }
-    // backward, dense upper part (unscaled accumulators; x_k = acc_k / u_kk)
-    for (int k = nd - 1; k > 0; --k) {
-      const T rk = (T)r[t0 + k];
-      const int m = k * 32;
-      for (int e = tid; e < m; e += bd) {
+      for (int kb = ((nd - 1) / 32) * 32; kb >= 0; kb -= 32) {
+        const int w = min(32, nd - kb);
+        for (int e = tid; e < 32 * 32; e += bd) {
+          const int rr = e >> 5, c2 = e & 31;
+          blkd[rr][c2] = (rr < w && c2 < w && c2 > rr) ? A[ts[kb + c2] + kb + rr] : 0.0;  // U(kb+rr, kb+c2)
+        }
+        __syncthreads();
+        if (warp == 0) {
+          for (int jj = w - 1; jj >= 0; --jj) {
+            const T xj = sh[(kb + jj) * 32 + lane] * (T)r[t0 + kb + jj];
+            sh[(kb + jj) * 32 + lane] = xj;
+            for (int i2 = 0; i2 < jj; ++i2) sh[(kb + i2) * 32 + lane] -= (T)blkd[i2][jj] * xj;
+          }
+        }
+        __syncthreads();
+        for (int i = warp; i < kb; i += nw) {
+          T acc = sh[i * 32 + lane];
+          for (int j = 0; j < w; ++j) acc -= (T)A[ts[kb + j] + i] * sh[(kb + j) * 32 + lane];
+          sh[i * 32 + lane] = acc;
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < nd * 32; e += bd) {
         const int i = e >> 5, q = e & 31;
-        const T u = (T)A[ts[i * nd + k]];
-        if (tail_smem) sh[i * 32 + q] -= u * (sh[k * 32 + q] * rk);
-        else if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] -= u * (Zs[(size_t)(t0 + k) * nu + c0 + q] * rk);
+        if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] = sh[i * 32 + q];
+      }
+      __syncthreads();
+    } else {
+      // in place in Z (trailing block too large for shared memory):
+      // forward, dense unit-lower part, column by column
+      for (int k = 0; k < nd - 1; ++k) {
+        const int m = (nd - k - 1) * 32;
+        for (int e = tid; e < m; e += bd) {
+          const int i = k + 1 + (e >> 5), q = e & 31;
+          const T l = (T)A[ts[i * nd + k]];
+          if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] -= l * Zs[(size_t)(t0 + k) * nu + c0 + q];
+        }
+        __syncthreads();
+      }
+      // backward, dense upper part (unscaled accumulators; x_k = acc_k / u_kk)
+      for (int k = nd - 1; k > 0; --k) {
+        const T rk = (T)r[t0 + k];
+        const int m = k * 32;
+        for (int e = tid; e < m; e += bd) {
+          const int i = e >> 5, q = e & 31;
+          const T u = (T)A[ts[i * nd + k]];
+          if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] -= u * (Zs[(size_t)(t0 + k) * nu + c0 + q] * rk);
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < nd * 32; e += bd) {
+        const int i = e >> 5, q = e & 31;
+        if (c0 + q < nu) {
+          T *dst = &Zs[(size_t)(t0 + i) * nu + c0 + q];
+          *dst = *dst * (T)r[t0 + i];
+        }
       }
       __syncthreads();
     }
-    for (int e = tid; e < nd * 32; e += bd) {
-      const int i = e >> 5, q = e & 31;
-      if (c0 + q < nu) {
-        T *dst = &Zs[(size_t)(t0 + i) * nu + c0 + q];
-        *dst = (tail_smem ? sh[i * 32 + q] : *dst) * (T)r[t0 + i];
-      }
-    }
-    __syncthreads();
   }
   // backward, sparse rows
   for (int l = 0; l < S.nlev_bs; ++l) {
@@ -291,20 +347,73 @@ __global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *
       if (lane == 0) tv[i] = vs[row] - part;
     }
     __syncthreads();
-    // forward over the dense block: L (unit) or U^T (diagonal u_kk)
-    for (int k = 0; k < nd; ++k) {
-      const double xk = trans ? tv[k] * r[t0 + k] : tv[k];
-      for (int i = k + 1 + tid; i < nd; i += bd) tv[i] -= A[trans ? ts[k * nd + i] : ts[i * nd + k]] * xk;
+    // Dense trailing block, blocked by 32 (one warp per 32 x 32 diagonal
+    // block, shuffles; all threads for the off-diagonal updates).  Column c
+    // of the block is contiguous in LU storage: entry (a, c) sits at
+    // cb(c) + a with cb(c) = tail_slot[c] (rows sorted in each column).
+    // Forward: T = L (unit) or U^T (diagonal u_kk); backward: T = U or L^T.
+    //   L(a, c) = U(a, c) = A[cb(c) + a].
+    __shared__ double blk[32][33];
+    for (int kb = 0; kb < nd; kb += 32) {
+      const int w = min(32, nd - kb);
+      for (int e = tid; e < 32 * 32; e += bd) {
+        const int rr = e >> 5, cc = e & 31;
+        double bv = 0.0;
+        if (rr < w && cc < rr) bv = trans ? A[ts[kb + rr] + kb + cc] : A[ts[kb + cc] + kb + rr];
+        blk[rr][cc] = bv;
+      }
       __syncthreads();
-      if (tid == 0 && trans) tv[k] = xk;
+      if (warp == 0) {
+        double xv = lane < w ? tv[kb + lane] : 0.0;
+        for (int jj = 0; jj < w; ++jj) {
+          if (lane == jj && trans) xv *= r[t0 + kb + jj];
+          const double xj = __shfl_sync(0xffffffffu, xv, jj);
+          if (lane > jj) xv -= blk[lane][jj] * xj;
+        }
+        if (lane < w) tv[kb + lane] = xv;
+      }
+      __syncthreads();
+      for (int i = kb + w + tid; i < nd; i += bd) {
+        double s2 = 0.0;
+        if (trans) {
+          const double *col = A + ts[i] + kb;  // U(kb + j, i), j = 0..w-1
+          for (int j = 0; j < w; ++j) s2 = fma(col[j], tv[kb + j], s2);
+        } else {
+          for (int j = 0; j < w; ++j) s2 = fma(A[ts[kb + j] + i], tv[kb + j], s2);
+        }
+        tv[i] -= s2;
+      }
       __syncthreads();
     }
-    // backward over the dense block: U (diagonal) or L^T (unit)
-    for (int k = nd - 1; k >= 0; --k) {
-      const double xk = trans ? tv[k] : tv[k] * r[t0 + k];
-      for (int i = tid; i < k; i += bd) tv[i] -= A[trans ? ts[k * nd + i] : ts[i * nd + k]] * xk;
+    for (int kb = ((nd - 1) / 32) * 32; kb >= 0; kb -= 32) {
+      const int w = min(32, nd - kb);
+      for (int e = tid; e < 32 * 32; e += bd) {
+        const int rr = e >> 5, cc = e & 31;
+        double bv = 0.0;
+        if (rr < w && cc < w && cc > rr) bv = trans ? A[ts[kb + rr] + kb + cc] : A[ts[kb + cc] + kb + rr];
+        blk[rr][cc] = bv;
+      }
       __syncthreads();
-      if (tid == 0 && !trans) tv[k] = xk;
+      if (warp == 0) {
+        double xv = lane < w ? tv[kb + lane] : 0.0;
+        for (int jj = w - 1; jj >= 0; --jj) {
+          if (lane == jj && !trans) xv *= r[t0 + kb + jj];
+          const double xj = __shfl_sync(0xffffffffu, xv, jj);
+          if (lane < jj) xv -= blk[lane][jj] * xj;
+        }
+        if (lane < w) tv[kb + lane] = xv;
+      }
+      __syncthreads();
+      for (int i = tid; i < kb; i += bd) {
+        double s2 = 0.0;
+        if (trans) {
+          const double *col = A + ts[i] + kb;  // L(kb + j, i), j = 0..w-1
+          for (int j = 0; j < w; ++j) s2 = fma(col[j], tv[kb + j], s2);
+        } else {
+          for (int j = 0; j < w; ++j) s2 = fma(A[ts[kb + j] + i], tv[kb + j], s2);
+        }
+        tv[i] -= s2;
+      }
       __syncthreads();
     }
     for (int i = tid; i < nd; i += bd) vs[t0 + i] = tv[i];
@@ -340,7 +449,8 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
   dim3 grid((S.nu + 31) / 32, S.N);
   const int sm = zsolve_smem_ok(S, sizeof(double));
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(double) : 0;
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(k_zsolve64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // dynamic plus static shared memory may pass the 48 KB default
+  if (bytes > 0) cudaFuncSetAttribute(k_zsolve64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
 }
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
@@ -348,12 +458,12 @@ void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const 
   dim3 grid((S.nu + 31) / 32, S.N);
   const int sm = zsolve_smem_ok(S, sizeof(float));
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(float) : 0;
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(k_zsolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 0) cudaFuncSetAttribute(k_zsolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_zsolve32<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
 }
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st) {
   const size_t bytes = (size_t)S.nd * sizeof(double);
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(k_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 0) cudaFuncSetAttribute(k_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans); ipm_count_launch();
 }
