@@ -102,7 +102,9 @@ typedef struct {
                             (solve threads, scenario groups of the reduced-Hessian
                             contraction) and keep the fastest; results are cached per
                             (n_x, n_u, N, precision) for the process */
-  int reserved[4];
+  int poison;            /* 1: fill every device buffer with NaN when it is allocated (a check
+                            that nothing is read before it is written; results must not change) */
+  int reserved[3];
   double sigma;          /* centring factor of the adaptive rule (0.1) */
 } ipm_options;
 
@@ -204,6 +206,10 @@ ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
  * split (the tensor-core operands of Z and Y: BF16 slices or planes). */
 enum { IPM_N_PHASES = 10 };
 ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
+
+/* Kernels this library has launched in the process so far (all contexts;
+ * a replayed CUDA graph counts its kernel nodes). */
+long long ipm_kernel_launches(void);
 
 /* Replace the scenario loads of a context (same network and N) and reset the
  * cold-start state.  pd, qd: host [n_scen][n_bus].  Reuses every symbolic

@@ -68,6 +68,7 @@ ipm_status dalloc(ipm_ctx *c, T **p, size_t count) {
   }
   c->allocs.push_back(q);
   *p = (T *)q;
+  if (c->opt.poison) cudaMemset(q, 0xFF, count * sizeof(T));  // all-ones bytes: NaN in FP64 and FP32
   return IPM_OK;
 }
 
@@ -1121,6 +1122,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
       c->opt.max_iter < 0 || c->opt.max_refine < 0 ||
       (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
       (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
+      (c->opt.poison != 0 && c->opt.poison != 1) ||
       (c->opt.barrier_rule == IPM_BARRIER_ADAPTIVE && !(c->opt.sigma > 0 && c->opt.sigma < 1))) {
     delete c;
     return IPM_ERR_ARG;
@@ -1464,6 +1466,8 @@ ipm_status ipm_warm_start(ipm_ctx *c, const float *pred, void *stream) {
   if (!c || !pred) return IPM_ERR_ARG;
   return do_warm_start(c, pred, STR(stream));
 }
+
+long long ipm_kernel_launches(void) { return g_ipm_launches.load(); }
 
 ipm_status ipm_set_profiling(ipm_ctx *c, int on) {
   if (!c) return IPM_ERR_ARG;

@@ -12,6 +12,21 @@ inline void ipm_count_launch() {
   ++t_ipm_launches;
 }
 
+// Raise a kernel's dynamic shared-memory cap to everything the device allows
+// next to its static shared memory.  Done once per kernel: setting it per
+// launch to that launch's size would race between host threads that launch
+// the same kernel for different instances.
+template <class K>
+inline bool raise_smem_cap(K kernel) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes) == cudaSuccess;
+}
+
 // kernels_eval.cu
 void launch_functions(const DevSym &S, const double *x, const double *u, double *P, double *Q, double *g,
                       double *h, double *fs, cudaStream_t st);

@@ -328,6 +328,7 @@ void launch_cholesky(int n, double *A, int *flags, cudaStream_t st) {
 }
 void launch_chol_solve(int n, const double *L, double *b, cudaStream_t st) {
   const size_t bytes = (size_t)n * sizeof(double);
-  if (bytes > 0) cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static const bool cap = raise_smem_cap(k_chol_solve);
+  (void)cap;
   k_chol_solve<<<1, 256, bytes, st>>>(n, L, b); ipm_count_launch();
 }

@@ -438,7 +438,8 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
   // trailing sub-block held in shared memory: up to 160 x 160 doubles (200 KB)
   const int ns = S.nd < 160 ? S.nd : 160;
   const size_t smem = (size_t)ns * ns * sizeof(double);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const bool cap = raise_smem_cap(k_lu_factor);
+  (void)cap;
   k_lu_factor<<<S.N, 512, smem, st>>>(S, nL, J, LU, rd, flags, 1e-14, ns); ipm_count_launch();
 }
 static int zsolve_smem_ok(const DevSym &S, size_t elem) {
@@ -450,7 +451,8 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
   const int sm = zsolve_smem_ok(S, sizeof(double));
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(double) : 0;
   // dynamic plus static shared memory may pass the 48 KB default
-  if (bytes > 0) cudaFuncSetAttribute(k_zsolve64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static const bool cap = raise_smem_cap(k_zsolve64);
+  (void)cap;
   k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
 }
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
@@ -458,12 +460,14 @@ void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const 
   dim3 grid((S.nu + 31) / 32, S.N);
   const int sm = zsolve_smem_ok(S, sizeof(float));
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(float) : 0;
-  if (bytes > 0) cudaFuncSetAttribute(k_zsolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static const bool cap = raise_smem_cap(k_zsolve32);
+  (void)cap;
   k_zsolve32<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
 }
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st) {
   const size_t bytes = (size_t)S.nd * sizeof(double);
-  if (bytes > 0) cudaFuncSetAttribute(k_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static const bool cap = raise_smem_cap(k_solve1);
+  (void)cap;
   k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans); ipm_count_launch();
 }

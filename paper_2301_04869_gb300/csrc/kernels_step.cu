@@ -329,7 +329,8 @@ __global__ void k_zt_part(DevSym S, const double *__restrict__ Z, const double *
   part[t] = acc;
 }
 
-// out[j] = beta*out[j] + sum_s (alpha part[s][j] (+ (K_ux b_s)[j] when b != null))
+// out[j] = beta*out[j] + sum_s (alpha part[s][j] (+ (K_ux b_s)[j] when b != null));
+// beta = 0 does not read out (it may hold anything, NaN included)
 __global__ void k_zt_sum(DevSym S, const double *part, const double *K, const double *b, double alpha,
                          double beta, double *out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -343,7 +344,7 @@ __global__ void k_zt_sum(DevSym S, const double *part, const double *K, const do
         if (col < S.nx) acc += K[(size_t)S.ku_src[e] * S.N + sc] * b[(size_t)sc * S.nx + col];
       }
   }
-  out[j] = beta * out[j] + acc;
+  out[j] = beta == 0.0 ? acc : beta * out[j] + acc;
 }
 
 // v[s][p] = a * v[s][p] + (Z_s pu)[p]   (position rows)
@@ -356,7 +357,7 @@ __global__ void k_z_apply(DevSym S, const double *__restrict__ Z, const double *
   double part = 0.0;
   for (int j = lane; j < S.nu; j += 32) part += Zr[j] * pu[j];
   part = warp_sum(part);
-  if (lane == 0) v[row] = a * v[row] + part;
+  if (lane == 0) v[row] = (a == 0.0 ? 0.0 : a * v[row]) + part;
 }
 
 // out[j] = scale * sum_s (G_u^T a_s)[j]   (a in position order)

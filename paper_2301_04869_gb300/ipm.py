@@ -50,7 +50,8 @@ BARRIER_MONOTONE, BARRIER_ADAPTIVE = 0, 1
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("solve_threads", ctypes.c_int), ("barrier_rule", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3),
                 ("sigma", ctypes.c_double)]
 
 
@@ -105,6 +106,7 @@ def load():
         "ipm_warm_dim": (c_int, [vp, _I]),
         "ipm_warm_target": (c_int, [vp, vp, vp]),
         "ipm_warm_start": (c_int, [vp, vp, vp]),
+        "ipm_kernel_launches": (c_ll, []),
         "ipm_batch_default_options": (c_int, [ctypes.POINTER(BatchOptions)]),
         "ipm_solve_batch": (c_int, [ctypes.POINTER(vp), c_int, ctypes.POINTER(vp), ctypes.POINTER(BatchOptions),
                                     _I, _D, _I, _D]),
@@ -118,6 +120,11 @@ def load():
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def kernel_launches():
+    """Kernels libipm.so has launched in this process (all contexts)."""
+    return int(load().ipm_kernel_launches())
 
 
 def _ptr(a, ct):
@@ -154,7 +161,7 @@ def _cnet(net):
 
 
 def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, barrier_rule=None, sigma=None,
-                 graphs=False, autotune=False, solve_threads=0):
+                 graphs=False, autotune=False, solve_threads=0, poison=False):
     lib = load()
     opt = Options()
     lib.ipm_default_options(ctypes.byref(opt))
@@ -169,6 +176,7 @@ def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, bar
     opt.graphs = int(bool(graphs))
     opt.autotune = int(bool(autotune))
     opt.solve_threads = int(solve_threads)
+    opt.poison = int(bool(poison))
     return opt
 
 
@@ -176,13 +184,13 @@ class Solver:
     """One context: a network with N load scenarios on the current GPU."""
 
     def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
-                 barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0):
+                 barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0, poison=False):
         lib = load()
         self._lib = lib
         self._keep, cnet = _cnet(net)
         opt = make_options(precision=precision, tol=tol, max_iter=max_iter, max_refine=max_refine,
                            barrier_rule=barrier_rule, sigma=sigma, graphs=graphs, autotune=autotune,
-                           solve_threads=solve_threads)
+                           solve_threads=solve_threads, poison=poison)
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]

@@ -33,7 +33,9 @@ def gpu():
 # (n_bus, n_gen, N, sigma, seed): uneven sizes and scenario counts, one ragged
 # single-scenario case (each converges under the oracle in 18-26 iterations)
 BATCH = [(30, 6, 1, 0.0, 0), (60, 9, 5, 0.05, 0), (100, 15, 8, 0.05, 3), (150, 22, 12, 0.05, 5),
-         (200, 30, 3, 0.05, 7), (120, 18, 17, 0.05, 9)]
+         (200, 30, 3, 0.05, 7), (120, 18, 17, 0.05, 9), (1000, 150, 2, 0.05, 0)]
+# (the 1000-bus instance needs more than the default 48 KB of shared memory
+# per block in its solves, while the small ones do not)
 
 
 def instances():
@@ -126,7 +128,7 @@ def test_batch_small_instances_match_oracle(gpu):
 
 def test_batch_ungrouped_and_graphs(gpu):
     """Without the grouped contraction, and with graphs, the same results."""
-    insts = instances()[2:5]
+    insts = instances()[2:5] + instances()[6:]
     alone = [solve_alone(gpu, *t) for t in insts]
     for kw in (dict(group_contraction=False), dict(group_contraction=True)):
         sols = [gpu.Solver(*t, graphs=True) for t in insts]
