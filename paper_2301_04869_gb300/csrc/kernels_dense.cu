@@ -10,6 +10,8 @@
 // Only upper tiles (i <= j) are computed; the symmetric result is mirrored.
 #include <atomic>
 
+#include <cooperative_groups.h>
+
 #include "dev.cuh"
 #include "kernels.h"
 
@@ -213,6 +215,98 @@ __global__ void k_syrk_trail(int n, int k0, double *A) {
   }
 }
 
+// The same blocked factorization as one cooperative launch (grid-wide
+// barriers between the steps instead of three launches per block column):
+// per block column the panel rows are solved across the grid, then the
+// lower tiles of the trailing matrix are updated round-robin; the CTA that
+// updates the next diagonal tile factors it right away (one barrier saved).
+__device__ void potrf_tile(int n, int k0, double *A, int *flags, double (*a)[CB + 1]) {
+  const int nb = min(CB, n - k0), tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      const double d = a[k][k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        flags[FLAG_NOT_PD] = 1;
+        a[k][k] = 1.0;
+      } else {
+        a[k][k] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) a[i][k] /= a[k][k];
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+      const int i = e / nb, j = e % nb;
+      if (i > k && j > k && j <= i) a[i][j] -= a[i][k] * a[j][k];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? a[i][j] : 0.0;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_chol_coop(int n, double *A, int *flags) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  __shared__ double a[CB][CB + 1], b2[CB][CB + 1];
+  const int G = gridDim.x, bk = blockIdx.x, tid = threadIdx.x;
+  if (bk == 0) potrf_tile(n, 0, A, flags, a);
+  grid.sync();
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    const int nb = min(CB, n - k0), r0 = k0 + nb, rest = n - r0;
+    if (rest <= 0) break;
+    // panel: L_ik = A_ik L_kk^{-T}, one thread per row
+    if (r0 + bk * (int)blockDim.x < n) {
+      for (int e = tid; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
+      __syncthreads();
+      for (int i = r0 + bk * blockDim.x + tid; i < n; i += G * blockDim.x) {
+        double x[CB];
+        for (int j = 0; j < nb; ++j) {
+          double v = A[(size_t)i * n + k0 + j];
+          for (int t = 0; t < j; ++t) v -= x[t] * a[j][t];
+          x[j] = v / a[j][j];
+        }
+        for (int j = 0; j < nb; ++j) A[(size_t)i * n + k0 + j] = x[j];
+      }
+    }
+    grid.sync();
+    // trailing update of the lower tiles; tile (0, 0) is the next diagonal block
+    const int nt = (rest + CB - 1) / CB, ntl = nt * (nt + 1) / 2;
+    for (int t = bk; t < ntl; t += G) {
+      int bi = 0, rem = t;
+      while (rem > bi) {
+        rem -= bi + 1;
+        ++bi;
+      }
+      const int bj = rem;  // t = bi (bi + 1) / 2 + bj, bj <= bi
+      const int i0 = r0 + bi * CB, j0 = r0 + bj * CB;
+      __syncthreads();
+      for (int e = tid; e < CB * nb; e += blockDim.x) {
+        const int rr = e / nb, tt = e % nb;
+        a[rr][tt] = (i0 + rr < n) ? A[(size_t)(i0 + rr) * n + k0 + tt] : 0.0;
+        b2[rr][tt] = (j0 + rr < n) ? A[(size_t)(j0 + rr) * n + k0 + tt] : 0.0;
+      }
+      __syncthreads();
+      for (int e = tid; e < CB * CB; e += blockDim.x) {
+        const int ii = e / CB, jj = e % CB, i = i0 + ii, j = j0 + jj;
+        if (i >= n || j >= n || j > i) continue;
+        double v = 0.0;
+        for (int tt = 0; tt < nb; ++tt) v += a[ii][tt] * b2[jj][tt];
+        A[(size_t)i * n + j] -= v;
+      }
+      if (t == 0) {
+        __syncthreads();
+        potrf_tile(n, r0, A, flags, a);
+      }
+    }
+    grid.sync();
+  }
+}
+
 // solve L L^T x = b in place (one CTA; x in shared memory).  Blocked by 32:
 // one warp solves each 32 x 32 diagonal block with shuffles, then all
 // threads apply the block's columns to the remaining rows (forward: rows of
@@ -315,6 +409,28 @@ void launch_maxdiag(int n, const double *A, double *out, cudaStream_t st) {
   k_maxdiag<<<1, 256, 0, st>>>(n, A, out); ipm_count_launch();
 }
 void launch_cholesky(int n, double *A, int *flags, cudaStream_t st) {
+  // one cooperative launch when the device allows it (all CTAs resident)
+  static const int coop_ctas = [] {
+    int dev = 0, ok = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ok, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!ok || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_coop, 256, 0) != cudaSuccess || per < 1)
+      return 0;
+    return sms;  // one CTA per SM
+  }();
+  if (coop_ctas > 0) {
+    const int nt = (n + CB - 1) / CB;
+    int G = nt * (nt + 1) / 2;  // lower tiles of the first trailing update
+    G = G < coop_ctas ? G : coop_ctas;
+    if (G < 1) G = 1;
+    void *args[] = {(void *)&n, (void *)&A, (void *)&flags};
+    if (cudaLaunchCooperativeKernel((const void *)k_chol_coop, dim3(G), dim3(256), args, 0, st) == cudaSuccess) {
+      ipm_count_launch();
+      return;
+    }
+    cudaGetLastError();
+  }
   for (int k0 = 0; k0 < n; k0 += CB) {
     k_potrf_diag<<<1, 256, 0, st>>>(n, k0, A, flags); ipm_count_launch();
     const int nb = n - k0 < CB ? n - k0 : CB;

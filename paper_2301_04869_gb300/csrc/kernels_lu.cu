@@ -98,19 +98,62 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
   if (ns == 0) return;
   for (int e = tid; e < ns * ns; e += bd) T[e] = A[ts[(k0 + e / ns) * nd + k0 + e % ns]];
   __syncthreads();
-  for (int k = 0; k < ns; ++k) {
-    const double d = T[k * ns + k];
-    if (tid == 0) {
-      if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
-      r[t0 + k0 + k] = 1.0 / d;
+  // Blocked right-looking LU of the ns x ns block in shared memory (static
+  // diagonal pivots): per panel of PB columns, (a) the panel column by
+  // column, (b) U12 = L11^{-1} A12 (thread per column), (c) the trailing
+  // update A22 -= L21 U12 with 4 x 4 register tiles (one shared-memory read
+  // per 4 multiply-adds instead of three per multiply-add).
+  constexpr int PB = 16;
+  for (int kb = 0; kb < ns; kb += PB) {
+    const int pb = min(PB, ns - kb), ke = kb + pb;
+    for (int k = kb; k < ke; ++k) {
+      const double d = T[k * ns + k];
+      if (tid == 0) {
+        if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
+        r[t0 + k0 + k] = 1.0 / d;
+      }
+      const double rk = 1.0 / d;
+      for (int i = k + 1 + tid; i < ns; i += bd) T[i * ns + k] *= rk;
+      __syncthreads();
+      const int cols = ke - k - 1;
+      if (cols > 0)
+        for (int e = tid; e < (ns - k - 1) * PB; e += bd) {
+          const int i = k + 1 + e / PB, j = k + 1 + e % PB;
+          if (j < ke) T[i * ns + j] -= T[i * ns + k] * T[k * ns + j];
+        }
+      __syncthreads();
     }
-    const double rk = 1.0 / d;
-    const int m = ns - k - 1;
-    for (int e = tid; e < m; e += bd) T[(k + 1 + e) * ns + k] *= rk;
+    if (ke >= ns) break;
+    for (int j = ke + tid; j < ns; j += bd)
+      for (int k = kb; k < ke; ++k) {
+        const double x = T[k * ns + j];
+        for (int i = k + 1; i < ke; ++i) T[i * ns + j] -= T[i * ns + k] * x;
+      }
     __syncthreads();
-    for (int e = tid; e < m * m; e += bd) {
-      const int a = k + 1 + e / m, b = k + 1 + e % m;
-      T[a * ns + b] -= T[a * ns + k] * T[k * ns + b];
+    const int m = ns - ke, nt4 = (m + 3) / 4;
+    for (int e = tid; e < nt4 * nt4; e += bd) {
+      const int i0 = ke + (e / nt4) * 4, j0 = ke + (e % nt4) * 4;
+      double c[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) c[a][b] = 0.0;
+      for (int k = kb; k < ke; ++k) {
+        double lv[4], uv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) lv[a] = i0 + a < ns ? T[(i0 + a) * ns + k] : 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) uv[b] = j0 + b < ns ? T[k * ns + j0 + b] : 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) c[a][b] = fma(lv[a], uv[b], c[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (i0 + a < ns && j0 + b < ns) T[(i0 + a) * ns + j0 + b] -= c[a][b];
     }
     __syncthreads();
   }
@@ -435,8 +478,19 @@ __global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *
 
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
                       cudaStream_t st) {
-  // trailing sub-block held in shared memory: up to 160 x 160 doubles (200 KB)
-  const int ns = S.nd < 160 ? S.nd : 160;
+  // trailing sub-block held in shared memory: as large as fits next to the
+  // kernel's static shared memory (170 x 170 doubles on GB300)
+  static const int ns_max = [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_lu_factor);
+    int n = 1;
+    while ((size_t)(n + 1) * (n + 1) * sizeof(double) + fa.sharedSizeBytes <= (size_t)optin) ++n;
+    return n;
+  }();
+  const int ns = S.nd < ns_max ? S.nd : ns_max;
   const size_t smem = (size_t)ns * ns * sizeof(double);
   static const bool cap = raise_smem_cap(k_lu_factor);
   (void)cap;

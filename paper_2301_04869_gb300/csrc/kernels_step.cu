@@ -315,35 +315,43 @@ __global__ void k_rhs_reduced(DevSym S, const double *J, const double *K, const 
   rhs[j] = acc;
 }
 
-// part[s][j] = (Z_s^T w_s)[j]: thread per (scenario, column), rows swept in
-// order, consecutive threads read consecutive columns (coalesced).
-__global__ void k_zt_part(DevSym S, const double *__restrict__ Z, const double *__restrict__ w,
-                          double *part) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)S.N * S.nu) return;
-  const int sc = (int)(t / S.nu), j = (int)(t - (long long)sc * S.nu);
+// part[s][j] = alpha (Z_s^T w_s)[j] (+ (K_ux,s b_s)[j] when b != null).
+// CTA per (scenario, 32 columns): lane = column (coalesced row segments of
+// Z), the 8 warps take every 8th row, a fixed-order shared-memory sum joins
+// them.
+__global__ void __launch_bounds__(256) k_zt_part(DevSym S, const double *__restrict__ Z,
+                                                 const double *__restrict__ w, const double *__restrict__ K,
+                                                 const double *__restrict__ b, double alpha, double *part) {
+  __shared__ double red[8][33];
+  const int sc = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
   const double *Zs = Z + (size_t)sc * S.nx * S.nu;
   const double *ws = w + (size_t)sc * S.nx;
   double acc = 0.0;
-  for (int p = 0; p < S.nx; ++p) acc += Zs[(size_t)p * S.nu + j] * ws[p];
-  part[t] = acc;
-}
-
-// out[j] = beta*out[j] + sum_s (alpha part[s][j] (+ (K_ux b_s)[j] when b != null));
-// beta = 0 does not read out (it may hold anything, NaN included)
-__global__ void k_zt_sum(DevSym S, const double *part, const double *K, const double *b, double alpha,
-                         double beta, double *out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= S.nu) return;
-  double acc = 0.0;
-  for (int sc = 0; sc < S.N; ++sc) {
-    acc += alpha * part[(size_t)sc * S.nu + j];
+  if (j < S.nu)
+    for (int p = warp; p < S.nx; p += 8) acc += Zs[(size_t)p * S.nu + j] * ws[p];
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && j < S.nu) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    t *= alpha;
     if (b)
       for (int e = S.ku_ptr[j]; e < S.ku_ptr[j + 1]; ++e) {
         const int col = S.ku_col[e];
-        if (col < S.nx) acc += K[(size_t)S.ku_src[e] * S.N + sc] * b[(size_t)sc * S.nx + col];
+        if (col < S.nx) t += K[(size_t)S.ku_src[e] * S.N + sc] * b[(size_t)sc * S.nx + col];
       }
+    part[(size_t)sc * S.nu + j] = t;
   }
+}
+
+// out[j] = beta*out[j] + sum_s part[s][j]  (scenarios in index order);
+// beta = 0 does not read out (it may hold anything, NaN included)
+__global__ void k_zt_sum(DevSym S, const double *part, double beta, double *out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= S.nu) return;
+  double acc = 0.0;
+  for (int sc = 0; sc < S.N; ++sc) acc += part[(size_t)sc * S.nu + j];
   out[j] = beta == 0.0 ? acc : beta * out[j] + acc;
 }
 
@@ -560,8 +568,8 @@ void launch_rhs_reduced(const DevSym &S, const double *J, const double *K, const
 }
 void launch_zt_apply(const DevSym &S, const double *Z, const double *w, const double *K, const double *b,
                      double alpha, double beta, double *out, double *part, cudaStream_t st) {
-  k_zt_part<<<nblk((long long)S.N * S.nu, 128), 128, 0, st>>>(S, Z, w, part); ipm_count_launch();
-  k_zt_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, part, K, b, alpha, beta, out); ipm_count_launch();
+  k_zt_part<<<dim3((S.nu + 31) / 32, S.N), 256, 0, st>>>(S, Z, w, K, b, alpha, part); ipm_count_launch();
+  k_zt_sum<<<nblk(S.nu, 64), 64, 0, st>>>(S, part, beta, out); ipm_count_launch();
 }
 void launch_z_apply(const DevSym &S, const double *Z, const double *pu, double a, double *v, cudaStream_t st) {
   k_z_apply<<<nblk((long long)S.N * S.nx * 32, 256), 256, 0, st>>>(S, Z, pu, a, v); ipm_count_launch();
