@@ -42,9 +42,9 @@ METRIC = "scenario condensations/s & s per IPM iter (mixed vs FP64 path, 1e-8 KK
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per launch from one ncu capture of the kernel as it stands (profiles/); None once the
 # kernel changes until it is captured again.
-TRAFFIC = {"k_gemm_tn64": 591.243264e6 + 26.54592e6,     # profiles/k_gemm_tn64_opf1000_n64.md
-           "k_zsolve64": 1.730639e9 + 822.209024e6,      # profiles/k_zsolve64_opf1000_n64.md
-           "k_emu_schur": 1.13788e9 + 3.627776e6}        # profiles/k_emu_schur_opf1000_n64.md
+TRAFFIC = {"k_gemm_tn64": 591.243264e6 + 26.54592e6,   # DRAM read + write, one launch, 1000 buses x 64
+           "k_zsolve64": 1.730639e9 + 822.209024e6,
+           "k_emu_schur": 1.13788e9 + 3.627776e6}
 UNIT = "scenario condensations/s"
 
 
