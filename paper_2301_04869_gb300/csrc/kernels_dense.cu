@@ -263,12 +263,14 @@ __global__ void __launch_bounds__(256) k_chol_coop(int n, double *A, int *flags)
     if (r0 + bk * (int)blockDim.x < n) {
       for (int e = tid; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
       __syncthreads();
+      if (tid < nb) b2[0][tid] = 1.0 / a[tid][tid];  // reciprocal pivots
+      __syncthreads();
       for (int i = r0 + bk * blockDim.x + tid; i < n; i += G * blockDim.x) {
         double x[CB];
         for (int j = 0; j < nb; ++j) {
           double v = A[(size_t)i * n + k0 + j];
           for (int t = 0; t < j; ++t) v -= x[t] * a[j][t];
-          x[j] = v / a[j][j];
+          x[j] = v * b2[0][j];
         }
         for (int j = 0; j < nb; ++j) A[(size_t)i * n + k0 + j] = x[j];
       }

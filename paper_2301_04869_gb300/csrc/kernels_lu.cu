@@ -219,19 +219,15 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
       // diagonal block (lane = RHS column), then every warp applies the
       // block's columns to the remaining rows (warp = row, lane = column).
       // Column c of the block is contiguous in LU storage: (a, c) sits at
-      // tail_slot[c] + a.  Backward values are scaled as they are found.
-      __shared__ double blkd[32][33];
+      // tail_slot[c] + a (read straight from the LU values, the same address
+      // for all lanes).  Backward values are scaled as they are found.
       for (int kb = 0; kb < nd; kb += 32) {
         const int w = min(32, nd - kb);
-        for (int e = tid; e < 32 * 32; e += bd) {
-          const int rr = e >> 5, c2 = e & 31;
-          blkd[rr][c2] = (rr < w && c2 < rr) ? A[ts[kb + c2] + kb + rr] : 0.0;  // L(kb+rr, kb+c2)
-        }
-        __syncthreads();
         if (warp == 0) {
           for (int jj = 0; jj < w; ++jj) {
             const T xj = sh[(kb + jj) * 32 + lane];
-            for (int i2 = jj + 1; i2 < w; ++i2) sh[(kb + i2) * 32 + lane] -= (T)blkd[i2][jj] * xj;
+            const double *col = A + ts[kb + jj] + kb;  // L(kb + i2, kb + jj) = col[i2]
+            for (int i2 = jj + 1; i2 < w; ++i2) sh[(kb + i2) * 32 + lane] -= (T)col[i2] * xj;
           }
         }
         __syncthreads();
@@ -244,16 +240,12 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
       }
       for (int kb = ((nd - 1) / 32) * 32; kb >= 0; kb -= 32) {
         const int w = min(32, nd - kb);
-        for (int e = tid; e < 32 * 32; e += bd) {
-          const int rr = e >> 5, c2 = e & 31;
-          blkd[rr][c2] = (rr < w && c2 < w && c2 > rr) ? A[ts[kb + c2] + kb + rr] : 0.0;  // U(kb+rr, kb+c2)
-        }
-        __syncthreads();
         if (warp == 0) {
           for (int jj = w - 1; jj >= 0; --jj) {
             const T xj = sh[(kb + jj) * 32 + lane] * (T)r[t0 + kb + jj];
             sh[(kb + jj) * 32 + lane] = xj;
-            for (int i2 = 0; i2 < jj; ++i2) sh[(kb + i2) * 32 + lane] -= (T)blkd[i2][jj] * xj;
+            const double *col = A + ts[kb + jj] + kb;  // U(kb + i2, kb + jj) = col[i2]
+            for (int i2 = 0; i2 < jj; ++i2) sh[(kb + i2) * 32 + lane] -= (T)col[i2] * xj;
           }
         }
         __syncthreads();
@@ -335,7 +327,9 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
   }
 }
 
-__global__ void __launch_bounds__(256) k_zsolve64(DevSym S, const double *__restrict__ LU,
+// 5 CTAs per SM (shared memory and registers sized for it): the 640 CTAs of
+// 64 scenarios x 10 panels then run in one wave on 152 SMs instead of 1.05
+__global__ void __launch_bounds__(256, 5) k_zsolve64(DevSym S, const double *__restrict__ LU,
                                                   const double *__restrict__ rd,
                                                   const double *__restrict__ J,
                                                   const double *__restrict__ K, double *Z, double *Y,
@@ -344,7 +338,7 @@ __global__ void __launch_bounds__(256) k_zsolve64(DevSym S, const double *__rest
   zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd);
 }
 
-__global__ void __launch_bounds__(256) k_zsolve32(DevSym S, const double *__restrict__ LU,
+__global__ void __launch_bounds__(256, 5) k_zsolve32(DevSym S, const double *__restrict__ LU,
                                                   const double *__restrict__ rd,
                                                   const double *__restrict__ J,
                                                   const double *__restrict__ K, float *Z, float *Y,
