@@ -612,7 +612,8 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
     launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
     ph_begin(c, PH_ZSOLVE, st);
-    if (fp64) launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads);
+    // FP64: b = G_x^{-1} g of eq. (11) rides along as an extra right-hand side
+    if (fp64) launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads, D.g, c->bpos);
     else launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
     ph_end(c, PH_ZSOLVE, st);
     ph_begin(c, PH_SPLIT, st);
@@ -637,8 +638,12 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
       ph_begin(c, PH_RRHS, st);
       // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
       //   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
-      launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
-      launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+      // (b came with Z from the multi-RHS solve when the trailing block fits
+      // in shared memory)
+      if (!zsolve64_folds_b(S)) {
+        launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
+        launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+      }
       launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
       launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
       launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);

@@ -41,8 +41,12 @@ void launch_ugrad(const DevSym &S, DevWork &D, double *gLu, cudaStream_t st);
 // kernels_lu.cu
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
                       cudaStream_t st);
+// g, b (optional, [N][n_x]): also b = G_x^{-1} g in position order (g in
+// state order), in an extra right-hand-side lane, when zsolve64_folds_b
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
-                     double *Z, double *Y, double *Yu, cudaStream_t st, int threads = 256);
+                     double *Z, double *Y, double *Yu, cudaStream_t st, int threads = 256,
+                     const double *g = nullptr, double *b = nullptr);
+bool zsolve64_folds_b(const DevSym &S);
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
                      float *Z, float *Y, double *Yu, cudaStream_t st, int threads = 256);
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,

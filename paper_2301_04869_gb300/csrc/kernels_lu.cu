@@ -170,7 +170,7 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
 template <typename T>
 __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, const double *__restrict__ rd,
                             const double *__restrict__ J, const double *__restrict__ K, T *Z, T *Y, double *Yu,
-                            bool tail_smem, T *sh) {
+                            bool tail_smem, T *sh, const double *__restrict__ gvec, T *bvec) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, bd = blockDim.x;
   const int sc = blockIdx.y, c0 = blockIdx.x * 32, c = c0 + lane, nu = S.nu, nx = S.nx, N = S.N;
   const int t0 = S.t0, nd = S.nd;
@@ -181,19 +181,31 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
   T *Zs = Z + (size_t)sc * nx * nu;
   T *Ys = Y + (size_t)sc * nx * nu;
   double *Yus = Yu + (size_t)sc * nu * nu;
+  // Optional extra column n_u (when bvec is given): b = G_x^{-1} g of the
+  // reduced right-hand side rides along in an otherwise idle lane, stored in
+  // bvec [N][n_x] (position order) instead of Z.  zb/zst read a lane's own
+  // column, zw writes it.
+  const bool xb = bvec != nullptr && c == nu;
+  T *bs = bvec ? bvec + (size_t)sc * nx : nullptr;
+  const T *zb = xb ? bs : Zs + cc;
+  T *zw = xb ? bs : Zs + c;
+  const size_t zst = xb ? 1 : (size_t)nu;
+  const bool wr = valid || xb;
   // forward, sparse rows
   for (int l = 0; l < S.nlev_fs; ++l) {
     for (int e = S.fs_lev_ptr[l] + warp; e < S.fs_lev_ptr[l + 1]; e += nw) {
       const int row = S.fs_rows[e];
       T acc = 0;
-      for (int g = S.gu_ptr[row]; g < S.gu_ptr[row + 1]; ++g)
-        if (S.gu_col[g] == cc) {
-          const int src = S.gu_src[g];
-          acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
-        }
+      if (xb) acc = (T)gvec[(size_t)sc * nx + S.iperm[row]];
+      else
+        for (int g = S.gu_ptr[row]; g < S.gu_ptr[row + 1]; ++g)
+          if (S.gu_col[g] == cc) {
+            const int src = S.gu_src[g];
+            acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
+          }
       for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1]; ++f)
-        acc -= (T)A[S.fr_lslot[f]] * Zs[(size_t)S.fr_col[f] * nu + cc];
-      if (valid) Zs[(size_t)row * nu + c] = acc;
+        acc -= (T)A[S.fr_lslot[f]] * zb[(size_t)S.fr_col[f] * zst];
+      if (wr) zw[(size_t)row * zst] = acc;
     }
     __syncthreads();
   }
@@ -202,13 +214,15 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
     for (int i = warp; i < nd; i += nw) {
       const int row = t0 + i;
       T acc = 0;
-      for (int g = S.gu_ptr[row]; g < S.gu_ptr[row + 1]; ++g)
-        if (S.gu_col[g] == cc) {
-          const int src = S.gu_src[g];
-          acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
-        }
+      if (xb) acc = (T)gvec[(size_t)sc * nx + S.iperm[row]];
+      else
+        for (int g = S.gu_ptr[row]; g < S.gu_ptr[row + 1]; ++g)
+          if (S.gu_col[g] == cc) {
+            const int src = S.gu_src[g];
+            acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
+          }
       for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1] && S.fr_col[f] < t0; ++f)
-        acc -= (T)A[S.fr_lslot[f]] * Zs[(size_t)S.fr_col[f] * nu + cc];
+        acc -= (T)A[S.fr_lslot[f]] * zb[(size_t)S.fr_col[f] * zst];
       if (tail_smem) sh[i * 32 + lane] = acc;
       else if (valid) Zs[(size_t)row * nu + c] = acc;
     }
@@ -259,6 +273,7 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
       for (int e = tid; e < nd * 32; e += bd) {
         const int i = e >> 5, q = e & 31;
         if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] = sh[i * 32 + q];
+        else if (bvec && c0 + q == nu) bs[t0 + i] = sh[i * 32 + q];
       }
       __syncthreads();
     } else {
@@ -298,10 +313,10 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
   for (int l = 0; l < S.nlev_bs; ++l) {
     for (int e = S.bs_lev_ptr[l] + warp; e < S.bs_lev_ptr[l + 1]; e += nw) {
       const int row = S.bs_rows[e];
-      T acc = Zs[(size_t)row * nu + cc];
+      T acc = zb[(size_t)row * zst];
       for (int f = S.br_ptr[row]; f < S.br_ptr[row + 1]; ++f)
-        acc -= (T)A[S.br_uslot[f]] * Zs[(size_t)S.br_col[f] * nu + cc];
-      if (valid) Zs[(size_t)row * nu + c] = acc * (T)r[row];
+        acc -= (T)A[S.br_uslot[f]] * zb[(size_t)S.br_col[f] * zst];
+      if (wr) zw[(size_t)row * zst] = acc * (T)r[row];
     }
     __syncthreads();
   }
@@ -333,9 +348,10 @@ __global__ void __launch_bounds__(256, 5) k_zsolve64(DevSym S, const double *__r
                                                   const double *__restrict__ rd,
                                                   const double *__restrict__ J,
                                                   const double *__restrict__ K, double *Z, double *Y,
-                                                  double *Yu, int tail_smem) {
+                                                  double *Yu, int tail_smem, const double *__restrict__ gvec,
+                                                  double *bvec) {
   extern __shared__ double shd[];
-  zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd);
+  zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd, gvec, bvec);
 }
 
 __global__ void __launch_bounds__(256, 5) k_zsolve32(DevSym S, const double *__restrict__ LU,
@@ -344,7 +360,7 @@ __global__ void __launch_bounds__(256, 5) k_zsolve32(DevSym S, const double *__r
                                                   const double *__restrict__ K, float *Z, float *Y,
                                                   double *Yu, int tail_smem) {
   extern __shared__ float shf[];
-  zsolve_body<float>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shf);
+  zsolve_body<float>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shf, nullptr, (float *)nullptr);
 }
 
 // In-place solve of G_x v = b (trans = 0) or G_x^T v = b (trans = 1) for every
@@ -493,15 +509,19 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
 static int zsolve_smem_ok(const DevSym &S, size_t elem) {
   return (S.nd > 0 && (size_t)S.nd * 32 * elem <= 100 * 1024) ? 1 : 0;
 }
+bool zsolve64_folds_b(const DevSym &S) { return S.nd == 0 || zsolve_smem_ok(S, sizeof(double)); }
+
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J,
-                     const double *K, double *Z, double *Y, double *Yu, cudaStream_t st, int threads) {
-  dim3 grid((S.nu + 31) / 32, S.N);
+                     const double *K, double *Z, double *Y, double *Yu, cudaStream_t st, int threads,
+                     const double *g, double *b) {
   const int sm = zsolve_smem_ok(S, sizeof(double));
+  if (!zsolve64_folds_b(S)) b = nullptr;
+  dim3 grid((S.nu + (b ? 1 : 0) + 31) / 32, S.N);
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(double) : 0;
   // dynamic plus static shared memory may pass the 48 KB default
   static const bool cap = raise_smem_cap(k_zsolve64);
   (void)cap;
-  k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
+  k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm, g, b); ipm_count_launch();
 }
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
                      const double *K, float *Z, float *Y, double *Yu, cudaStream_t st, int threads) {
