@@ -21,6 +21,9 @@ struct DevSym {
   const int *fs_lev_ptr, *fs_rows, *bs_lev_ptr, *bs_rows;
   const int *gu_ptr, *gu_col, *gu_src, *gut_ptr, *gut_col, *gut_src;
   const int *kx_ptr, *kx_col, *kx_src, *ku_ptr, *ku_col, *ku_src;
+  int zp_npan;  // forward schedules per 32-column panel of Z (symbolic.cpp)
+  const int *zp_lev_off, *zp_lev_ptr, *zp_rows, *zp_eptr, *zp_col, *zp_slot, *zp_zptr, *zp_zrows, *zp_tptr, *zp_tcol,
+      *zp_tslot;
   const double *xl, *xu, *ul, *uu, *sl, *su, *c2, *c1;
   const double *pd, *qd;  // [N][n]
 };

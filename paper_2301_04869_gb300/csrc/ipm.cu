@@ -127,6 +127,11 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   TRY(upload(c, &d.br_col, S.br_col)); TRY(upload(c, &d.br_uslot, S.br_uslot)); TRY(upload(c, &d.br_lslot, S.br_lslot));
   TRY(upload(c, &d.gu_ptr, S.gu_ptr)); TRY(upload(c, &d.gu_col, S.gu_col)); TRY(upload(c, &d.gu_src, S.gu_src));
   TRY(upload(c, &d.gut_ptr, S.gut_ptr)); TRY(upload(c, &d.gut_col, S.gut_col)); TRY(upload(c, &d.gut_src, S.gut_src));
+  d.zp_npan = S.zp_npan;
+  TRY(upload(c, &d.zp_lev_off, S.zp_lev_off)); TRY(upload(c, &d.zp_lev_ptr, S.zp_lev_ptr));
+  TRY(upload(c, &d.zp_rows, S.zp_rows)); TRY(upload(c, &d.zp_eptr, S.zp_eptr)); TRY(upload(c, &d.zp_col, S.zp_col));
+  TRY(upload(c, &d.zp_slot, S.zp_slot)); TRY(upload(c, &d.zp_zptr, S.zp_zptr)); TRY(upload(c, &d.zp_zrows, S.zp_zrows));
+  TRY(upload(c, &d.zp_tptr, S.zp_tptr)); TRY(upload(c, &d.zp_tcol, S.zp_tcol)); TRY(upload(c, &d.zp_tslot, S.zp_tslot));
   TRY(upload(c, &d.kx_ptr, S.kx_ptr)); TRY(upload(c, &d.kx_col, S.kx_col)); TRY(upload(c, &d.kx_src, S.kx_src));
   TRY(upload(c, &d.ku_ptr, S.ku_ptr)); TRY(upload(c, &d.ku_col, S.ku_col)); TRY(upload(c, &d.ku_src, S.ku_src));
   TRY(upload(c, &d.xl, S.xl)); TRY(upload(c, &d.xu, S.xu)); TRY(upload(c, &d.ul, S.ul)); TRY(upload(c, &d.uu, S.uu));

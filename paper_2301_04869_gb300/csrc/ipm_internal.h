@@ -54,6 +54,14 @@ struct Sym {
   // sparse operators by position (x rows) or u rows
   std::vector<int> gu_ptr, gu_col, gu_src;
   std::vector<int> gut_ptr, gut_col, gut_src;
+  // forward schedules per 32-column panel of Z (see symbolic.cpp):
+  // levels [zp_lev_off[p], zp_lev_off[p+1]) of panel p, rows of level l in
+  // zp_rows[zp_lev_ptr[l], zp_lev_ptr[l+1]), products of scheduled row e in
+  // [zp_eptr[e], zp_eptr[e+1]); zero rows zp_zrows[zp_zptr[p], zp_zptr[p+1]);
+  // products of trailing-block row a in [zp_tptr[p*nd + a], zp_tptr[p*nd + a + 1])
+  int zp_npan = 0;
+  std::vector<int> zp_lev_off, zp_lev_ptr, zp_rows, zp_eptr, zp_col, zp_slot, zp_zptr, zp_zrows, zp_tptr, zp_tcol,
+      zp_tslot;
   std::vector<int> kx_ptr, kx_col, kx_src;
   std::vector<int> ku_ptr, ku_col, ku_src;
   // bounds (+-inf allowed)

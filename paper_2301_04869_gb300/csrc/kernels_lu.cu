@@ -191,10 +191,14 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
   T *zw = xb ? bs : Zs + c;
   const size_t zst = xb ? 1 : (size_t)nu;
   const bool wr = valid || xb;
-  // forward, sparse rows
-  for (int l = 0; l < S.nlev_fs; ++l) {
-    for (int e = S.fs_lev_ptr[l] + warp; e < S.fs_lev_ptr[l + 1]; e += nw) {
-      const int row = S.fs_rows[e];
+  // forward, sparse rows: this panel's schedule (rows its columns of G_u
+  // reach, products against such rows only); the other rows are zero
+  const int pan = blockIdx.x;
+  for (int e = S.zp_zptr[pan] + warp; e < S.zp_zptr[pan + 1]; e += nw)
+    if (wr) zw[(size_t)S.zp_zrows[e] * zst] = (T)0;
+  for (int l = S.zp_lev_off[pan]; l < S.zp_lev_off[pan + 1]; ++l) {
+    for (int e = S.zp_lev_ptr[l] + warp; e < S.zp_lev_ptr[l + 1]; e += nw) {
+      const int row = S.zp_rows[e];
       T acc = 0;
       if (xb) acc = (T)gvec[(size_t)sc * nx + S.iperm[row]];
       else
@@ -203,8 +207,8 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
             const int src = S.gu_src[g];
             acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
           }
-      for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1]; ++f)
-        acc -= (T)A[S.fr_lslot[f]] * zb[(size_t)S.fr_col[f] * zst];
+      for (int f = S.zp_eptr[e]; f < S.zp_eptr[e + 1]; ++f)
+        acc -= (T)A[S.zp_slot[f]] * zb[(size_t)S.zp_col[f] * zst];
       if (wr) zw[(size_t)row * zst] = acc;
     }
     __syncthreads();
@@ -221,8 +225,8 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
             const int src = S.gu_src[g];
             acc -= src >= 0 ? (T)J[(size_t)src * N + sc] : (T)-1.0;
           }
-      for (int f = S.fr_ptr[row]; f < S.fr_ptr[row + 1] && S.fr_col[f] < t0; ++f)
-        acc -= (T)A[S.fr_lslot[f]] * zb[(size_t)S.fr_col[f] * zst];
+      for (int f = S.zp_tptr[pan * nd + i]; f < S.zp_tptr[pan * nd + i + 1]; ++f)
+        acc -= (T)A[S.zp_tslot[f]] * zb[(size_t)S.zp_tcol[f] * zst];
       if (tail_smem) sh[i * 32 + lane] = acc;
       else if (valid) Zs[(size_t)row * nu + c] = acc;
     }

@@ -449,6 +449,64 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
       S.gut_ptr[j + 1] = (int)S.gut_col.size();
     }
   }
+  // ---- forward schedules per 32-column panel of the multi-RHS solve ----
+  // A column of G_u reaches few rows of the forward sweep L^{-1} G_u: row i
+  // is structurally nonzero for a panel iff G_u has an entry of a panel
+  // column in row i, or L(i, k) != 0 for a nonzero row k < i.  The panel
+  // holding column n_u (where b = G_x^{-1} g rides along) keeps every row.
+  // Per panel: the nonzero sparse rows by level of the reduced sweep with
+  // their products against nonzero rows only, the zero rows, and for each
+  // trailing-block row its products against nonzero sparse rows.
+  {
+    const int np = (nu + 1 + 31) / 32, t0 = S.t0, nd = S.nd;
+    S.zp_npan = np;
+    S.zp_lev_off.assign(1, 0);
+    S.zp_lev_ptr.assign(1, 0);
+    S.zp_eptr.assign(1, 0);
+    S.zp_zptr.assign(1, 0);
+    S.zp_tptr.assign(1, 0);
+    std::vector<char> nz(nx);
+    std::vector<int> zl(nx);
+    for (int p = 0; p < np; ++p) {
+      const int c0 = 32 * p, c1 = 32 * p + 32;
+      const bool all = c0 <= nu && nu < c1;
+      int nl = 0;
+      for (int i = 0; i < t0; ++i) {
+        bool z = all;
+        for (int g = S.gu_ptr[i]; !z && g < S.gu_ptr[i + 1]; ++g) z = S.gu_col[g] >= c0 && S.gu_col[g] < c1;
+        int lv = 0;
+        for (int f = S.fr_ptr[i]; f < S.fr_ptr[i + 1]; ++f) {
+          const int k = S.fr_col[f];
+          if (nz[k]) { z = true; lv = std::max(lv, zl[k] + 1); }
+        }
+        nz[i] = z;
+        zl[i] = lv;
+        if (z) nl = std::max(nl, lv + 1);
+      }
+      std::vector<std::vector<int>> byl(nl);
+      for (int i = 0; i < t0; ++i) {
+        if (nz[i]) byl[zl[i]].push_back(i);
+        else S.zp_zrows.push_back(i);
+      }
+      S.zp_zptr.push_back((int)S.zp_zrows.size());
+      for (int l = 0; l < nl; ++l) {
+        for (int i : byl[l]) {
+          S.zp_rows.push_back(i);
+          for (int f = S.fr_ptr[i]; f < S.fr_ptr[i + 1]; ++f)
+            if (nz[S.fr_col[f]]) { S.zp_col.push_back(S.fr_col[f]); S.zp_slot.push_back(S.fr_lslot[f]); }
+          S.zp_eptr.push_back((int)S.zp_col.size());
+        }
+        S.zp_lev_ptr.push_back((int)S.zp_rows.size());
+      }
+      S.zp_lev_off.push_back(S.zp_lev_off.back() + nl);
+      for (int a = 0; a < nd; ++a) {
+        const int i = t0 + a;
+        for (int f = S.fr_ptr[i]; f < S.fr_ptr[i + 1] && S.fr_col[f] < t0; ++f)
+          if (nz[S.fr_col[f]]) { S.zp_tcol.push_back(S.fr_col[f]); S.zp_tslot.push_back(S.fr_lslot[f]); }
+        S.zp_tptr.push_back((int)S.zp_tcol.size());
+      }
+    }
+  }
   // ---- K_x (rows: positions) and K_u (rows: u) ----
   auto var_col = [&](int b, int kind) -> int {  // column id: position or nx + u
     if (kind == 0) return S.xth[b] >= 0 ? S.perm[S.xth[b]] : -1;
