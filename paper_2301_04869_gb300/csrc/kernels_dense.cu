@@ -148,30 +148,77 @@ __global__ void k_maxdiag(int n, const double *A, double *out) {
 constexpr int CB = 32;  // Cholesky block
 
 // factor the CB x CB diagonal block at (k0, k0) in place (lower), unblocked
-__global__ void k_potrf_diag(int n, int k0, double *A, int *flags) {
-  __shared__ double a[CB][CB + 1];
+// 1/sqrt(d) for d > 0: the single-precision hardware estimate (relative
+// error below 2^-22) refined by two Newton-Raphson steps for the reciprocal
+// square root, y <- y + y (1/2 - (d/2) y^2), each of which about squares
+// the relative error (2^-43, then below FP64 rounding).  Three dependent
+// FP64 operations per step instead of a square root and a division (~1,200
+// cycles of dependent latency on GB300).  Outside [1e-30, 1e30] (no FP32
+// estimate) the plain form is used.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)d));
+  double y = (double)yf;
+  const double h = 0.5 * d;
+  double r = fma(-h * y, y, 0.5);
+  y = fma(y, r, y);
+  r = fma(-h * y, y, 0.5);
+  return fma(y, r, y);
+}
+
+// Right-looking Cholesky of the nb x nb block a (lower part, in shared
+// memory) by the calling CTA: thread 0 takes each pivot's reciprocal square
+// root, then warps 0-3 scale the column and update the trailing columns
+// (warp w: columns j = w mod 4; lane = row; column entries by shuffles).  A
+// non-positive or non-finite pivot raises FLAG_NOT_PD and is replaced by 1.
+__device__ void potrf_block(int nb, int *flags, double (*a)[CB + 1], double *rs_sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      double d = a[k][k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        flags[FLAG_NOT_PD] = 1;
+        d = 1.0;
+      }
+      const double rs = rsqrt_newton(d);
+      *rs_sh = rs;
+      a[k][k] = d * rs;
+    }
+    __syncthreads();
+    double lik = 0.0;
+    if (warp < 4) {
+      lik = (lane > k && lane < nb) ? a[lane][k] * *rs_sh : 0.0;
+      for (int j = k + 1 + ((warp - (k + 1)) & 3); j < nb; j += 4) {
+        const double ljk = __shfl_sync(0xffffffffu, lik, j);
+        if (lane >= j && lane < nb) a[lane][j] -= lik * ljk;
+      }
+    }
+    __syncthreads();
+    // column k is read by no later step: written after the barrier
+    if (warp == 0 && lane > k && lane < nb) a[lane][k] = lik;
+  }
+  __syncthreads();
+}
+
+// Load, factor and store the diagonal block at (k0, k0) (upper part of the
+// block set to zero).
+__device__ void potrf_tile(int n, int k0, double *A, int *flags, double (*a)[CB + 1], double *rs_sh) {
   const int nb = min(CB, n - k0), tid = threadIdx.x;
   for (int e = tid; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
   __syncthreads();
-  for (int k = 0; k < nb; ++k) {
-    if (tid == 0) {
-      const double d = a[k][k];
-      if (!(d > 0.0) || !isfinite(d)) { flags[FLAG_NOT_PD] = 1; a[k][k] = 1.0; }
-      else a[k][k] = sqrt(d);
-    }
-    __syncthreads();
-    for (int i = k + 1 + tid; i < nb; i += blockDim.x) a[i][k] /= a[k][k];
-    __syncthreads();
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-      const int i = e / nb, j = e % nb;
-      if (i > k && j > k && j <= i) a[i][j] -= a[i][k] * a[j][k];
-    }
-    __syncthreads();
-  }
+  potrf_block(nb, flags, a, rs_sh);
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e % nb;
     A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? a[i][j] : 0.0;
   }
+  __syncthreads();
+}
+
+__global__ void k_potrf_diag(int n, int k0, double *A, int *flags) {
+  __shared__ double a[CB][CB + 1];
+  __shared__ double rs_sh;
+  potrf_tile(n, k0, A, flags, a, &rs_sh);
 }
 
 // rows below the diagonal block: L_ik = A_ik L_kk^{-T}
@@ -216,93 +263,98 @@ __global__ void k_syrk_trail(int n, int k0, double *A) {
 }
 
 // The same blocked factorization as one cooperative launch (grid-wide
-// barriers between the steps instead of three launches per block column):
-// per block column the panel rows are solved across the grid, then the
-// lower tiles of the trailing matrix are updated round-robin; the CTA that
-// updates the next diagonal tile factors it right away (one barrier saved).
-__device__ void potrf_tile(int n, int k0, double *A, int *flags, double (*a)[CB + 1]) {
-  const int nb = min(CB, n - k0), tid = threadIdx.x;
-  for (int e = tid; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
+// barriers between the steps instead of three launches per block column).
+// Per block column k0 (32 wide): (a) every CTA with panel rows loads L_kk and
+// solves its rows x L_kk^T = a (a warp per row, lane = column, shuffles; the
+// multipliers L_jt / L_tt are formed once per CTA so each step is one
+// shuffle and one multiply-add); (b) the lower 16 x 16 tiles of the trailing
+// matrix are updated, CTA 0 taking the three that make up the next
+// diagonal block and factoring it right away, the others round-robin over
+// the remaining CTAs.
+constexpr int CT = 16;  // trailing-update tile
+
+__device__ void syrk_tile16(int n, int k0, int nb, int i0, int j0, double *A, double (*Li)[CB + 1],
+                            double (*Lj)[CB + 1]) {
+  const int tid = threadIdx.x;
   __syncthreads();
-  for (int k = 0; k < nb; ++k) {
-    if (tid == 0) {
-      const double d = a[k][k];
-      if (!(d > 0.0) || !isfinite(d)) {
-        flags[FLAG_NOT_PD] = 1;
-        a[k][k] = 1.0;
-      } else {
-        a[k][k] = sqrt(d);
-      }
-    }
-    __syncthreads();
-    for (int i = k + 1 + tid; i < nb; i += blockDim.x) a[i][k] /= a[k][k];
-    __syncthreads();
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-      const int i = e / nb, j = e % nb;
-      if (i > k && j > k && j <= i) a[i][j] -= a[i][k] * a[j][k];
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, j = e % nb;
-    A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? a[i][j] : 0.0;
+  for (int e = tid; e < CT * nb; e += blockDim.x) {
+    const int rr = e / nb, t = e % nb;
+    Li[rr][t] = (i0 + rr < n) ? A[(size_t)(i0 + rr) * n + k0 + t] : 0.0;
+    Lj[rr][t] = (j0 + rr < n) ? A[(size_t)(j0 + rr) * n + k0 + t] : 0.0;
   }
   __syncthreads();
+  if (tid < CT * CT) {
+    const int ii = tid / CT, jj = tid % CT, i = i0 + ii, j = j0 + jj;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int t = 0;
+    for (; t + 4 <= nb; t += 4) {
+      s0 = fma(Li[ii][t], Lj[jj][t], s0);
+      s1 = fma(Li[ii][t + 1], Lj[jj][t + 1], s1);
+      s2 = fma(Li[ii][t + 2], Lj[jj][t + 2], s2);
+      s3 = fma(Li[ii][t + 3], Lj[jj][t + 3], s3);
+    }
+    for (; t < nb; ++t) s0 = fma(Li[ii][t], Lj[jj][t], s0);
+    if (i < n && j < n && j <= i) A[(size_t)i * n + j] -= (s0 + s1) + (s2 + s3);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_chol_coop(int n, double *A, int *flags) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double a[CB][CB + 1], b2[CB][CB + 1];
-  const int G = gridDim.x, bk = blockIdx.x, tid = threadIdx.x;
-  if (bk == 0) potrf_tile(n, 0, A, flags, a);
+  __shared__ double rinv[CB], rs_sh;
+  const int G = gridDim.x, bk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (bk == 0) potrf_tile(n, 0, A, flags, a, &rs_sh);
   grid.sync();
   for (int k0 = 0; k0 < n; k0 += CB) {
     const int nb = min(CB, n - k0), r0 = k0 + nb, rest = n - r0;
     if (rest <= 0) break;
-    // panel: L_ik = A_ik L_kk^{-T}, one thread per row
-    if (r0 + bk * (int)blockDim.x < n) {
-      for (int e = tid; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * n + k0 + e % nb];
+    // (a) panel rows
+    if (r0 + bk * 8 < n) {
+      for (int e = tid; e < CB * CB; e += blockDim.x) {
+        const int rr = e / CB, cc = e % CB;
+        a[rr][cc] = (rr < nb && cc <= rr) ? A[(size_t)(k0 + rr) * n + k0 + cc] : 0.0;
+      }
       __syncthreads();
-      if (tid < nb) b2[0][tid] = 1.0 / a[tid][tid];  // reciprocal pivots
+      if (tid < CB) rinv[tid] = tid < nb ? 1.0 / a[tid][tid] : 0.0;
       __syncthreads();
-      for (int i = r0 + bk * blockDim.x + tid; i < n; i += G * blockDim.x) {
-        double x[CB];
-        for (int j = 0; j < nb; ++j) {
-          double v = A[(size_t)i * n + k0 + j];
-          for (int t = 0; t < j; ++t) v -= x[t] * a[j][t];
-          x[j] = v * b2[0][j];
+      for (int e = tid; e < CB * CB; e += blockDim.x) {
+        const int rr = e / CB, cc = e % CB;
+        b2[rr][cc] = cc < rr ? a[rr][cc] * rinv[cc] : 0.0;  // L_jt / L_tt (j = rr, t = cc)
+      }
+      __syncthreads();
+      for (int i = r0 + bk * 8 + warp; i < n; i += G * 8) {
+        double v = lane < nb ? A[(size_t)i * n + k0 + lane] : 0.0;
+        for (int t = 0; t < nb; ++t) {
+          const double vt = __shfl_sync(0xffffffffu, v, t);
+          if (lane > t) v = fma(-b2[lane][t], vt, v);
         }
-        for (int j = 0; j < nb; ++j) A[(size_t)i * n + k0 + j] = x[j];
+        if (lane < nb) A[(size_t)i * n + k0 + lane] = v * rinv[lane];
       }
     }
     grid.sync();
-    // trailing update of the lower tiles; tile (0, 0) is the next diagonal block
-    const int nt = (rest + CB - 1) / CB, ntl = nt * (nt + 1) / 2;
-    for (int t = bk; t < ntl; t += G) {
-      int bi = 0, rem = t;
-      while (rem > bi) {
-        rem -= bi + 1;
-        ++bi;
+    // (b) trailing update; tiles with bi, bj < 2 form the next diagonal block
+    const int nt = (rest + CT - 1) / CT;
+    const int nd = nt >= 2 ? 3 : 1;
+    const int ntl = nt * (nt + 1) / 2 - nd;
+    if (bk == 0) {
+      for (int q = 0; q < nd; ++q) {
+        const int bi = q == 0 ? 0 : 1, bj = q == 2 ? 1 : 0;
+        syrk_tile16(n, k0, nb, r0 + bi * CT, r0 + bj * CT, A, a, b2);
       }
-      const int bj = rem;  // t = bi (bi + 1) / 2 + bj, bj <= bi
-      const int i0 = r0 + bi * CB, j0 = r0 + bj * CB;
+      if (G == 1)
+        for (int t = 0; t < ntl; ++t) {
+          int bi = 2, rem = t;
+          while (rem > bi) { rem -= bi + 1; ++bi; }
+          syrk_tile16(n, k0, nb, r0 + bi * CT, r0 + rem * CT, A, a, b2);
+        }
       __syncthreads();
-      for (int e = tid; e < CB * nb; e += blockDim.x) {
-        const int rr = e / nb, tt = e % nb;
-        a[rr][tt] = (i0 + rr < n) ? A[(size_t)(i0 + rr) * n + k0 + tt] : 0.0;
-        b2[rr][tt] = (j0 + rr < n) ? A[(size_t)(j0 + rr) * n + k0 + tt] : 0.0;
-      }
-      __syncthreads();
-      for (int e = tid; e < CB * CB; e += blockDim.x) {
-        const int ii = e / CB, jj = e % CB, i = i0 + ii, j = j0 + jj;
-        if (i >= n || j >= n || j > i) continue;
-        double v = 0.0;
-        for (int tt = 0; tt < nb; ++tt) v += a[ii][tt] * b2[jj][tt];
-        A[(size_t)i * n + j] -= v;
-      }
-      if (t == 0) {
-        __syncthreads();
-        potrf_tile(n, r0, A, flags, a);
+      potrf_tile(n, r0, A, flags, a, &rs_sh);
+    } else {
+      for (int t = bk - 1; t < ntl; t += G - 1) {
+        // t-th lower tile in rows bi >= 2: row bi holds bi + 1 tiles
+        int bi = 2, rem = t;
+        while (rem > bi) { rem -= bi + 1; ++bi; }
+        syrk_tile16(n, k0, nb, r0 + bi * CT, r0 + rem * CT, A, a, b2);
       }
     }
     grid.sync();
@@ -313,7 +365,13 @@ __global__ void __launch_bounds__(256) k_chol_coop(int n, double *A, int *flags)
 // one warp solves each 32 x 32 diagonal block with shuffles, then all
 // threads apply the block's columns to the remaining rows (forward: rows of
 // L, contiguous per thread; backward: rows of L read across threads).
-__global__ void __launch_bounds__(256) k_chol_solve(int n, const double *__restrict__ L, double *b) {
+// L L^T x = b for one right-hand side, one CTA (x in shared memory).
+// Blocked by 32: one warp solves each 32 x 32 diagonal
+// block (lane = row, shuffles), multiplying by reciprocal pivots that all
+// lanes form at once (a dependent FP64 division costs ~9 multiply-adds of
+// latency); then a thread per remaining row applies the block's 32 columns
+// with four partial sums (the dependent FP64 chain is 8 long instead of 32).
+__global__ void __launch_bounds__(512) k_chol_solve(int n, const double *__restrict__ L, double *b) {
   extern __shared__ double x[];
   __shared__ double blk[32][33];
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -327,9 +385,10 @@ __global__ void __launch_bounds__(256) k_chol_solve(int n, const double *__restr
     }
     __syncthreads();
     if (warp == 0) {
+      const double ri = lane < w ? 1.0 / blk[lane][lane] : 0.0;
       double v = lane < w ? x[kb + lane] : 0.0;
       for (int jj = 0; jj < w; ++jj) {
-        if (lane == jj) v /= blk[jj][jj];
+        if (lane == jj) v *= ri;
         const double xj = __shfl_sync(0xffffffffu, v, jj);
         if (lane > jj) v -= blk[lane][jj] * xj;
       }
@@ -338,9 +397,16 @@ __global__ void __launch_bounds__(256) k_chol_solve(int n, const double *__restr
     __syncthreads();
     for (int i = kb + w + tid; i < n; i += bd) {
       const double *row = L + (size_t)i * n + kb;
-      double s = 0.0;
-      for (int j = 0; j < w; ++j) s = fma(row[j], x[kb + j], s);
-      x[i] -= s;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 4 <= w; j += 4) {
+        s0 = fma(row[j], x[kb + j], s0);
+        s1 = fma(row[j + 1], x[kb + j + 1], s1);
+        s2 = fma(row[j + 2], x[kb + j + 2], s2);
+        s3 = fma(row[j + 3], x[kb + j + 3], s3);
+      }
+      for (; j < w; ++j) s0 = fma(row[j], x[kb + j], s0);
+      x[i] -= (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
   }
@@ -352,9 +418,10 @@ __global__ void __launch_bounds__(256) k_chol_solve(int n, const double *__restr
     }
     __syncthreads();
     if (warp == 0) {
+      const double ri = lane < w ? 1.0 / blk[lane][lane] : 0.0;
       double v = lane < w ? x[kb + lane] : 0.0;
       for (int jj = w - 1; jj >= 0; --jj) {
-        if (lane == jj) v /= blk[jj][jj];
+        if (lane == jj) v *= ri;
         const double xj = __shfl_sync(0xffffffffu, v, jj);
         if (lane < jj) v -= blk[jj][lane] * xj;  // (L^T)[lane][jj] = L[jj][lane]
       }
@@ -362,9 +429,16 @@ __global__ void __launch_bounds__(256) k_chol_solve(int n, const double *__restr
     }
     __syncthreads();
     for (int i = tid; i < kb; i += bd) {
-      double s = 0.0;
-      for (int j = 0; j < w; ++j) s = fma(L[(size_t)(kb + j) * n + i], x[kb + j], s);
-      x[i] -= s;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 4 <= w; j += 4) {
+        s0 = fma(L[(size_t)(kb + j) * n + i], x[kb + j], s0);
+        s1 = fma(L[(size_t)(kb + j + 1) * n + i], x[kb + j + 1], s1);
+        s2 = fma(L[(size_t)(kb + j + 2) * n + i], x[kb + j + 2], s2);
+        s3 = fma(L[(size_t)(kb + j + 3) * n + i], x[kb + j + 3], s3);
+      }
+      for (; j < w; ++j) s0 = fma(L[(size_t)(kb + j) * n + i], x[kb + j], s0);
+      x[i] -= (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
   }
@@ -422,8 +496,8 @@ void launch_cholesky(int n, double *A, int *flags, cudaStream_t st) {
     return sms;  // one CTA per SM
   }();
   if (coop_ctas > 0) {
-    const int nt = (n + CB - 1) / CB;
-    int G = nt * (nt + 1) / 2;  // lower tiles of the first trailing update
+    const int nt = (n + CT - 1) / CT;
+    int G = 1 + nt * (nt + 1) / 2;  // CTA 0 plus one per lower tile of the first trailing update
     G = G < coop_ctas ? G : coop_ctas;
     if (G < 1) G = 1;
     void *args[] = {(void *)&n, (void *)&A, (void *)&flags};
@@ -448,5 +522,5 @@ void launch_chol_solve(int n, const double *L, double *b, cudaStream_t st) {
   const size_t bytes = (size_t)n * sizeof(double);
   static const bool cap = raise_smem_cap(k_chol_solve);
   (void)cap;
-  k_chol_solve<<<1, 256, bytes, st>>>(n, L, b); ipm_count_launch();
+  k_chol_solve<<<1, 512, bytes, st>>>(n, L, b); ipm_count_launch();
 }

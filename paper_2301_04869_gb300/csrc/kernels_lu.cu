@@ -371,74 +371,131 @@ __global__ void __launch_bounds__(256, 5) k_zsolve32(DevSym S, const double *__r
 // scenario; v is [N][nx] in LU position order.  One CTA per scenario: sparse
 // rows by levels (one warp per row, lanes over the row's entries), the dense
 // trailing block column by column in shared memory.
-__global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
-                         double *v, int trans) {
-  extern __shared__ double tv[];
+// Sum over a group of GS consecutive lanes (GS a power of two <= 32).
+template <int GS>
+__device__ __forceinline__ double group_sum(double p) {
+#pragma unroll
+  for (int o = GS / 2; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+  return p;
+}
+
+// One level of sparse rows, GS lanes per row: x[row] = (x[row] - sum_f
+// A[slot[f]] x[col[f]]) * (scale ? r[row] : 1) over f in [ptr[row],
+// ptr[row+1]) with col[f] < cend.  Rows of a level are independent; the
+// loop bounds are uniform over the CTA (shuffles).
+template <int GS>
+__device__ __forceinline__ void solve_level(const int *__restrict__ rows, int e0, int e1,
+                                            const int *__restrict__ ptr, const int *__restrict__ col,
+                                            const int *__restrict__ slot, int cend, const double *__restrict__ A,
+                                            const double *__restrict__ r, bool scale, double *x) {
+  const int grp = threadIdx.x / GS, sub = threadIdx.x % GS, ngrp = blockDim.x / GS;
+  for (int eb = e0; eb < e1; eb += ngrp) {
+    const int e = eb + grp;
+    double part = 0.0;
+    int row = -1;
+    if (e < e1) {
+      row = rows[e];
+      for (int f = ptr[row] + sub; f < ptr[row + 1]; f += GS) {
+        const int c = col[f];
+        if (c < cend) part = fma(A[slot[f]], x[c], part);
+      }
+    }
+    part = group_sum<GS>(part);
+    if (sub == 0 && row >= 0) x[row] = scale ? (x[row] - part) * r[row] : x[row] - part;
+  }
+}
+
+__global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
+                                                double *v, int trans, int in_smem) {
+  extern __shared__ double xsm[];
+  __shared__ double blk[32][33];
   const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
-  const int t0 = S.t0, nd = S.nd;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nx = S.nx, t0 = S.t0, nd = S.nd;
   const double *A = LU + (size_t)sc * S.nnzLU;
-  const double *r = rd + (size_t)sc * S.nx;
-  double *vs = v + (size_t)sc * S.nx;
+  const double *r = rd + (size_t)sc * nx;
+  double *vs = v + (size_t)sc * nx;
+  // the solution vector of this scenario lives in shared memory when it fits
+  double *x = in_smem ? xsm : vs;
+  if (in_smem) {
+    for (int i = tid; i < nx; i += bd) x[i] = vs[i];
+    __syncthreads();
+  }
   const int *fsl = trans ? S.fr_uslot : S.fr_lslot;
   const int *bsl = trans ? S.br_lslot : S.br_uslot;
+  // forward sparse rows (few entries each): four lanes per row
   for (int l = 0; l < S.nlev_fs; ++l) {
-    for (int e = S.fs_lev_ptr[l] + warp; e < S.fs_lev_ptr[l + 1]; e += nw) {
-      const int row = S.fs_rows[e];
-      double part = 0.0;
-      for (int f = S.fr_ptr[row] + lane; f < S.fr_ptr[row + 1]; f += 32) part += A[fsl[f]] * vs[S.fr_col[f]];
-      part = warp_sum(part);
-      if (lane == 0) vs[row] = trans ? (vs[row] - part) * r[row] : vs[row] - part;
-    }
+    solve_level<4>(S.fs_rows, S.fs_lev_ptr[l], S.fs_lev_ptr[l + 1], S.fr_ptr, S.fr_col, fsl, nx, A, r, trans != 0, x);
     __syncthreads();
   }
   if (nd > 0) {
     const int *ts = S.tail_slot;
-    // sparse part of the trailing rows
-    for (int i = warp; i < nd; i += nw) {
-      const int row = t0 + i;
-      double part = 0.0;
-      for (int f = S.fr_ptr[row] + lane; f < S.fr_ptr[row + 1]; f += 32)
-        if (S.fr_col[f] < t0) part += A[fsl[f]] * vs[S.fr_col[f]];
-      part = warp_sum(part);
-      if (lane == 0) tv[i] = vs[row] - part;
+    double *tv = x + t0;
+    // sparse part of the trailing rows (their columns < t0), eight lanes per row
+    {
+      const int grp = tid / 8, sub = tid % 8, ngrp = bd / 8;
+      for (int ib = 0; ib < nd; ib += ngrp) {
+        const int i = ib + grp;
+        double part = 0.0;
+        if (i < nd) {
+          const int row = t0 + i;
+          for (int f = S.fr_ptr[row] + sub; f < S.fr_ptr[row + 1]; f += 8) {
+            const int c = S.fr_col[f];
+            if (c < t0) part = fma(A[fsl[f]], x[c], part);
+          }
+        }
+        part = group_sum<8>(part);
+        if (sub == 0 && i < nd) tv[i] -= part;
+      }
     }
     __syncthreads();
-    // Dense trailing block, blocked by 32 (one warp per 32 x 32 diagonal
-    // block, shuffles; all threads for the off-diagonal updates).  Column c
-    // of the block is contiguous in LU storage: entry (a, c) sits at
-    // cb(c) + a with cb(c) = tail_slot[c] (rows sorted in each column).
-    // Forward: T = L (unit) or U^T (diagonal u_kk); backward: T = U or L^T.
-    //   L(a, c) = U(a, c) = A[cb(c) + a].
-    __shared__ double blk[32][33];
+    // Dense trailing block, blocked by 32: one warp per 32 x 32 diagonal
+    // block (lane = row, shuffles), all threads for the off-diagonal updates
+    // (four partial sums).  Column c of the block is contiguous in LU
+    // storage: entry (a, c) sits at tail_slot[c] + a.  Forward: T = L (unit)
+    // or U^T (diagonal u_kk); backward: T = U or L^T.  Where T has the
+    // diagonal u_kk the block multipliers are pre-scaled by 1/u_kk, so each
+    // step of the diagonal solve is one shuffle and one multiply-add.
     for (int kb = 0; kb < nd; kb += 32) {
       const int w = min(32, nd - kb);
       for (int e = tid; e < 32 * 32; e += bd) {
         const int rr = e >> 5, cc = e & 31;
         double bv = 0.0;
-        if (rr < w && cc < rr) bv = trans ? A[ts[kb + rr] + kb + cc] : A[ts[kb + cc] + kb + rr];
+        if (rr < w && cc < rr) bv = trans ? A[ts[kb + rr] + kb + cc] * r[t0 + kb + cc] : A[ts[kb + cc] + kb + rr];
         blk[rr][cc] = bv;
       }
       __syncthreads();
       if (warp == 0) {
         double xv = lane < w ? tv[kb + lane] : 0.0;
         for (int jj = 0; jj < w; ++jj) {
-          if (lane == jj && trans) xv *= r[t0 + kb + jj];
           const double xj = __shfl_sync(0xffffffffu, xv, jj);
-          if (lane > jj) xv -= blk[lane][jj] * xj;
+          if (lane > jj) xv = fma(-blk[lane][jj], xj, xv);
         }
-        if (lane < w) tv[kb + lane] = xv;
+        if (lane < w) tv[kb + lane] = trans ? xv * r[t0 + kb + lane] : xv;
       }
       __syncthreads();
       for (int i = kb + w + tid; i < nd; i += bd) {
-        double s2 = 0.0;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = 0;
         if (trans) {
           const double *col = A + ts[i] + kb;  // U(kb + j, i), j = 0..w-1
-          for (int j = 0; j < w; ++j) s2 = fma(col[j], tv[kb + j], s2);
+          for (; j + 4 <= w; j += 4) {
+            s0 = fma(col[j], tv[kb + j], s0);
+            s1 = fma(col[j + 1], tv[kb + j + 1], s1);
+            s2 = fma(col[j + 2], tv[kb + j + 2], s2);
+            s3 = fma(col[j + 3], tv[kb + j + 3], s3);
+          }
+          for (; j < w; ++j) s0 = fma(col[j], tv[kb + j], s0);
         } else {
-          for (int j = 0; j < w; ++j) s2 = fma(A[ts[kb + j] + i], tv[kb + j], s2);
+          for (; j + 4 <= w; j += 4) {
+            s0 = fma(A[ts[kb + j] + i], tv[kb + j], s0);
+            s1 = fma(A[ts[kb + j + 1] + i], tv[kb + j + 1], s1);
+            s2 = fma(A[ts[kb + j + 2] + i], tv[kb + j + 2], s2);
+            s3 = fma(A[ts[kb + j + 3] + i], tv[kb + j + 3], s3);
+          }
+          for (; j < w; ++j) s0 = fma(A[ts[kb + j] + i], tv[kb + j], s0);
         }
-        tv[i] -= s2;
+        tv[i] -= (s0 + s1) + (s2 + s3);
       }
       __syncthreads();
     }
@@ -447,45 +504,52 @@ __global__ void k_solve1(DevSym S, const double *__restrict__ LU, const double *
       for (int e = tid; e < 32 * 32; e += bd) {
         const int rr = e >> 5, cc = e & 31;
         double bv = 0.0;
-        if (rr < w && cc < w && cc > rr) bv = trans ? A[ts[kb + rr] + kb + cc] : A[ts[kb + cc] + kb + rr];
+        if (rr < w && cc < w && cc > rr) bv = trans ? A[ts[kb + rr] + kb + cc] : A[ts[kb + cc] + kb + rr] * r[t0 + kb + cc];
         blk[rr][cc] = bv;
       }
       __syncthreads();
       if (warp == 0) {
         double xv = lane < w ? tv[kb + lane] : 0.0;
         for (int jj = w - 1; jj >= 0; --jj) {
-          if (lane == jj && !trans) xv *= r[t0 + kb + jj];
           const double xj = __shfl_sync(0xffffffffu, xv, jj);
-          if (lane < jj) xv -= blk[lane][jj] * xj;
+          if (lane < jj) xv = fma(-blk[lane][jj], xj, xv);
         }
-        if (lane < w) tv[kb + lane] = xv;
+        if (lane < w) tv[kb + lane] = trans ? xv : xv * r[t0 + kb + lane];
       }
       __syncthreads();
       for (int i = tid; i < kb; i += bd) {
-        double s2 = 0.0;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = 0;
         if (trans) {
           const double *col = A + ts[i] + kb;  // L(kb + j, i), j = 0..w-1
-          for (int j = 0; j < w; ++j) s2 = fma(col[j], tv[kb + j], s2);
+          for (; j + 4 <= w; j += 4) {
+            s0 = fma(col[j], tv[kb + j], s0);
+            s1 = fma(col[j + 1], tv[kb + j + 1], s1);
+            s2 = fma(col[j + 2], tv[kb + j + 2], s2);
+            s3 = fma(col[j + 3], tv[kb + j + 3], s3);
+          }
+          for (; j < w; ++j) s0 = fma(col[j], tv[kb + j], s0);
         } else {
-          for (int j = 0; j < w; ++j) s2 = fma(A[ts[kb + j] + i], tv[kb + j], s2);
+          for (; j + 4 <= w; j += 4) {
+            s0 = fma(A[ts[kb + j] + i], tv[kb + j], s0);
+            s1 = fma(A[ts[kb + j + 1] + i], tv[kb + j + 1], s1);
+            s2 = fma(A[ts[kb + j + 2] + i], tv[kb + j + 2], s2);
+            s3 = fma(A[ts[kb + j + 3] + i], tv[kb + j + 3], s3);
+          }
+          for (; j < w; ++j) s0 = fma(A[ts[kb + j] + i], tv[kb + j], s0);
         }
-        tv[i] -= s2;
+        tv[i] -= (s0 + s1) + (s2 + s3);
       }
       __syncthreads();
     }
-    for (int i = tid; i < nd; i += bd) vs[t0 + i] = tv[i];
-    __syncthreads();
   }
+  // backward sparse rows: eight lanes per row
   for (int l = 0; l < S.nlev_bs; ++l) {
-    for (int e = S.bs_lev_ptr[l] + warp; e < S.bs_lev_ptr[l + 1]; e += nw) {
-      const int row = S.bs_rows[e];
-      double part = 0.0;
-      for (int f = S.br_ptr[row] + lane; f < S.br_ptr[row + 1]; f += 32) part += A[bsl[f]] * vs[S.br_col[f]];
-      part = warp_sum(part);
-      if (lane == 0) vs[row] = trans ? vs[row] - part : (vs[row] - part) * r[row];
-    }
+    solve_level<8>(S.bs_rows, S.bs_lev_ptr[l], S.bs_lev_ptr[l + 1], S.br_ptr, S.br_col, bsl, nx, A, r, trans == 0, x);
     __syncthreads();
   }
+  if (in_smem)
+    for (int i = tid; i < nx; i += bd) vs[i] = x[i];
 }
 
 }  // namespace
@@ -538,8 +602,17 @@ void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const 
 }
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st) {
-  const size_t bytes = (size_t)S.nd * sizeof(double);
-  static const bool cap = raise_smem_cap(k_solve1);
-  (void)cap;
-  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans); ipm_count_launch();
+  // the scenario's vector in shared memory when it fits next to the
+  // kernel's static shared memory
+  static const size_t cap = [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_solve1);
+    return raise_smem_cap(k_solve1) ? (size_t)optin - fa.sharedSizeBytes : (size_t)0;
+  }();
+  const int sm = (size_t)S.nx * sizeof(double) <= cap ? 1 : 0;
+  const size_t bytes = sm ? (size_t)S.nx * sizeof(double) : 0;
+  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm); ipm_count_launch();
 }
