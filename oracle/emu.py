@@ -15,10 +15,10 @@ Entries below 2^-1022 (subnormal) count as zero throughout.
    entry below 2^-1022 counts as zero).
 2. Per group of 512 rows and per column j: e_j = ilogb(max |x_kj|) + 2 (0 for
    an all-zero column), so |x 2^-e| < 1/2; X = round-half-away(|x| 2^(56-e))
-   with the sign of x (|X| <= 2^55); then S = 8 digits, rounded half up:
-   R = X; q_t = floor((R + 2^(s-1)) / 2^s), R <- R - q_t 2^s with
-   s = 56 - 7t (q_8 = R), integers |q_t| <= 64 with
-   X = sum_t q_t 2^(56-7t).
+   with the sign of x (|X| <= 2^55); then S = 8 digits, the unique
+   representation X = sum_t q_t 2^(49-7t) (t = 0..7) with q_t in [-64, 63]
+   for t >= 1: with O = 64 sum_{t>=1} 2^(49-7t), q_0 = floor((X + O) / 2^49)
+   (|q_0| <= 64) and q_t = (bits 49-7t .. 55-7t of X + O) - 64.
 3. Levels: acc_L = sum_{t+u=L} Q_t^T Q'_u (0-based t, u; L = 0..S-1),
    integer matrices (at most 8 * 2^12 * 512 = 2^24 in magnitude).
 4. Group value in units of 2^(e_i + e'_j - 49): the exact integers
@@ -91,13 +91,11 @@ def split(X, shift=None):
     s_ = -sh[dn]
     Xi[dn] = (m[dn] + (np.int64(1) << (s_ - 1))) >> s_
     Xi = np.where(neg, -Xi, Xi)
-    qs = []
-    R = Xi
-    for t in range(NS):
-        s = 49 - 7 * t
-        q = (R + (np.int64(1) << (s - 1))) >> s if s > 0 else R.copy()
-        R = R - (q << s)
-        qs.append(q)
+    offset = sum(64 << (49 - 7 * t) for t in range(1, NS))
+    Y = Xi + np.int64(offset)
+    qs = [Y >> 49]
+    for t in range(1, NS):
+        qs.append(((Y >> (49 - 7 * t)) & 127) - 64)
     return np.stack(qs), e
 
 

@@ -4,6 +4,11 @@
 #include <math.h>
 #include <stdint.h>
 
+#ifndef IPM_LU_THREADS_DEFINED
+#define IPM_LU_THREADS_DEFINED
+constexpr int LU_THREADS = 512;  // threads of the LU factorization CTA (per-thread op lists)
+#endif
+
 struct DevSym {
   int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b, nlev_f, t0, nd, nlev_fs, nlev_bs;
   const int *xth, *xv, *uv, *gen_of_bus, *xbus, *xkind;
@@ -16,6 +21,7 @@ struct DevSym {
   const int *lu_diag, *lu_init, *tail_slot;
   const int *f_lev_ptr, *f_piv_ptr, *f_piv, *f_tgt, *f_op_ptr, *f_op_l, *f_op_u, *f_op_k;
   const int *lsc_slot, *lsc_k;
+  const int *tw_len, *tw_l, *tw_u, *tw_e;  // trailing-block products per LU thread
   const int *fw_lev_ptr, *fw_rows, *fr_ptr, *fr_col, *fr_lslot, *fr_uslot;
   const int *bw_lev_ptr, *bw_rows, *br_ptr, *br_col, *br_uslot, *br_lslot;
   const int *fs_lev_ptr, *fs_rows, *bs_lev_ptr, *bs_rows;

@@ -121,6 +121,8 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   TRY(upload(c, &d.f_tgt, S.f_tgt)); TRY(upload(c, &d.f_op_ptr, S.f_op_ptr)); TRY(upload(c, &d.f_op_l, S.f_op_l));
   TRY(upload(c, &d.f_op_u, S.f_op_u)); TRY(upload(c, &d.f_op_k, S.f_op_k));
   TRY(upload(c, &d.lsc_slot, S.lsc_slot)); TRY(upload(c, &d.lsc_k, S.lsc_k));
+  TRY(upload(c, &d.tw_len, S.tw_len)); TRY(upload(c, &d.tw_l, S.tw_l)); TRY(upload(c, &d.tw_u, S.tw_u));
+  TRY(upload(c, &d.tw_e, S.tw_e));
   TRY(upload(c, &d.fw_lev_ptr, S.fw_lev_ptr)); TRY(upload(c, &d.fw_rows, S.fw_rows)); TRY(upload(c, &d.fr_ptr, S.fr_ptr));
   TRY(upload(c, &d.fr_col, S.fr_col)); TRY(upload(c, &d.fr_lslot, S.fr_lslot)); TRY(upload(c, &d.fr_uslot, S.fr_uslot));
   TRY(upload(c, &d.bw_lev_ptr, S.bw_lev_ptr)); TRY(upload(c, &d.bw_rows, S.bw_rows)); TRY(upload(c, &d.br_ptr, S.br_ptr));

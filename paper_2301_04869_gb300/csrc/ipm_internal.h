@@ -5,6 +5,11 @@
 
 #include "../../include/ipm.h"
 
+#ifndef IPM_LU_THREADS_DEFINED
+#define IPM_LU_THREADS_DEFINED
+constexpr int LU_THREADS = 512;  // threads of the LU factorization CTA (per-thread op lists)
+#endif
+
 struct HostNet {
   int n = 0, L = 0, ng = 0;
   std::vector<int> fr, to, gen;
@@ -49,6 +54,10 @@ struct Sym {
   std::vector<int> fs_lev_ptr, fs_rows, bs_lev_ptr, bs_rows;
   std::vector<int> f_lev_ptr, f_piv_ptr, f_piv, f_tgt, f_op_ptr, f_op_l, f_op_u, f_op_k;
   std::vector<int> lsc_slot, lsc_k;
+  // products of the sparse pivots into the dense trailing block, per thread
+  // of the factorization CTA (symbolic.cpp)
+  std::vector<int> tw_len, tw_l, tw_u, tw_e;
+  long long n_tail_ops = 0;
   std::vector<int> fw_lev_ptr, fw_rows, fr_ptr, fr_col, fr_lslot, fr_uslot;
   std::vector<int> bw_lev_ptr, bw_rows, br_ptr, br_col, br_uslot, br_lslot;
   // sparse operators by position (x rows) or u rows

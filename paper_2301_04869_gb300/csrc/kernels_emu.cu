@@ -86,73 +86,129 @@ __device__ __forceinline__ long long fixed56(int E, long long m, bool neg, int e
 // FP64 [krows][nu] -> NS BF16 slice planes [NS][nu][kpad] (K-major) and the
 // exponents [kpad / GROUP][nu].  Row k is first scaled by 2^(rsign rs[k])
 // (row balancing; rs may be null).  Column exponent of a row group:
-// e = ilogb(max |x|) + 2.  Digits of X in base 2^7, rounded half up:
-//   R = X; q_t = floor((R + 2^(s-1)) / 2^s), R -= q_t 2^s, s = 56 - 7t
-// (t = 1..8; q_8 = R), so |q_t| <= 64 and x 2^-e = sum_t q_t 2^-7t up to
-// the rounding of X (2^-57).  CTA: one row group x 32 columns.
-__global__ void __launch_bounds__(256) k_emu_split(long long krows, int nu, long long kpad,
-                                                   const double *__restrict__ src, const int *__restrict__ rs,
-                                                   int rsign, __nv_bfloat16 *planes, int *exps) {
-  __shared__ int es[32];
-  __shared__ __nv_bfloat16 sl[NS][32][34];
-  const long long g = blockIdx.x;
-  const int j0 = blockIdx.y * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const long long r0 = g * GROUP;
-  const int j = j0 + tx;
-  // largest balanced magnitude: compare (biased exponent, mantissa) as one
-  // unsigned key; balanced exponents outside 1..2047 count as zero / clamp
+// e = ilogb(max |x|) + 2.  Digits of X in base 2^7 with
+//   X = sum_t q_t 2^(49 - 7t)  (t = 0..7),  q_t in [-64, 63] for t >= 1,
+// the unique such representation: with O = 64 sum_{t>=1} 2^(49 - 7t),
+// q_0 = (X + O) >> 49 (|q_0| <= 64) and q_t = bits [s, s+7) of X + O minus
+// 64 (s = 49 - 7t), so x 2^-e = sum_t q_t 2^-7(t+1) up to the rounding of X
+// (2^-57).  A digit becomes BF16 bits through the FP32 pattern of
+// 1.5 2^23 + q (exact for |q| < 2^22; the low 16 bits are zero).
+//
+// CTA: one row group (512 rows) x 16 columns.  The group is copied into
+// shared memory once with asynchronous 8-byte copies (all 64 KB in flight,
+// no second read of global memory); the column maxima and the digits are
+// taken from there.  Digits of 128 rows at a time go through a staging
+// buffer and leave as 256-byte runs of each plane and column (streaming
+// stores).  Column blocks are the fast grid index, so the CTAs that share
+// the cache lines of the same rows run together.
+constexpr long long DIGIT_OFFSET = (64ll << 42) + (64ll << 35) + (64ll << 28) + (64ll << 21) + (64ll << 14) +
+                                   (64ll << 7) + 64ll;
+constexpr int SPLIT_COLS = 16;
+constexpr int SPLIT_CHUNK = 128;
+constexpr int SPLIT_ROW = SPLIT_CHUNK + 8;  // bf16 per (plane, column) row of the staging buffer (272 bytes)
+constexpr size_t SPLIT_SMEM = (size_t)GROUP * SPLIT_COLS * sizeof(double) + (size_t)NS * SPLIT_COLS * SPLIT_ROW * 2;
+
+__device__ __forceinline__ uint32_t digit_bf16(int q) {
+  return __float_as_uint(__int_as_float(0x4B400000 + q) - 12582912.0f) >> 16;
+}
+
+__global__ void __launch_bounds__(256, 2) k_emu_split(long long krows, int nu, long long kpad,
+                                                      const double *__restrict__ src, const int *__restrict__ rs,
+                                                      int rsign, __nv_bfloat16 *planes, int *exps) {
+  extern __shared__ __align__(16) uint8_t split_smem[];
+  double *tile = reinterpret_cast<double *>(split_smem);  // [GROUP][SPLIT_COLS]
+  uint16_t *buf = reinterpret_cast<uint16_t *>(split_smem + (size_t)GROUP * SPLIT_COLS * sizeof(double));
+  __shared__ int es[SPLIT_COLS];
+  __shared__ int shf[GROUP];
+  __shared__ unsigned long long kred[16][SPLIT_COLS];
+  const int j0 = blockIdx.x * SPLIT_COLS;
+  const long long g = blockIdx.y, rg = g * GROUP;
+  const int tid = threadIdx.x, c = tid & 15, o = tid >> 4;  // column, row slot 0..15
+  const int j = j0 + c;
+  const bool jv = j < nu;
+  // (1) the group into shared memory; row shifts alongside
+  for (int r = o; r < GROUP; r += 16) {
+    const long long k = rg + r;
+    double *d = tile + r * SPLIT_COLS + c;
+    if (k < krows && jv) {
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(d)),
+                   "l"(src + k * nu + j));
+    } else {
+      *d = 0.0;
+    }
+  }
+  for (int r = tid; r < GROUP; r += 256) {
+    const long long k = rg + r;
+    shf[r] = (rs && k < krows) ? rsign * rs[k] : 0;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  // (2) largest balanced magnitude per column: compare (biased exponent,
+  // mantissa) as one unsigned key; balanced exponents outside 1..2047 count
+  // as zero / clamp
   unsigned long long key = 0;
-  for (int r = ty; r < GROUP; r += 8) {
-    const long long k = r0 + r;
-    if (k < krows && j < nu) {
+  for (int r = o; r < GROUP; r += 16) {
+    int E;
+    long long m;
+    bool neg;
+    dsplit_bits(tile[r * SPLIT_COLS + c], E, m, neg);
+    if (m) {
+      E += shf[r];
+      if (E > 0) key = max(key, ((unsigned long long)min(E, 2047) << 53) | (unsigned long long)m);
+    }
+  }
+  kred[o][c] = key;
+  __syncthreads();
+  if (tid < SPLIT_COLS) {
+    unsigned long long kk = kred[0][tid];
+    for (int q = 1; q < 16; ++q) kk = max(kk, kred[q][tid]);
+    const int e = kk > 0 ? (int)(kk >> 53) - 1023 + 2 : 0;
+    es[tid] = e;
+    if (j0 + tid < nu) exps[g * nu + j0 + tid] = e;
+  }
+  __syncthreads();
+  const int e = es[c];
+  const size_t plane = (size_t)nu * kpad;
+  const int ncol = min(SPLIT_COLS, nu - j0);
+  for (int cb = 0; cb < GROUP; cb += SPLIT_CHUNK) {
+    // (3) digits of rows cb + 8 o .. + 7 of column c
+    uint32_t w[NS][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int rr = cb + o * 8 + r;
       int E;
       long long m;
       bool neg;
-      dsplit_bits(src[k * nu + j], E, m, neg);
-      if (m) {
-        E += rs ? rsign * rs[k] : 0;
-        if (E > 0) key = max(key, ((unsigned long long)min(E, 2047) << 53) | (unsigned long long)m);
-      }
-    }
-  }
-  __shared__ unsigned long long kred[8][32];
-  kred[ty][tx] = key;
-  __syncthreads();
-  if (ty == 0) {
-    unsigned long long kk = kred[0][tx];
-    for (int q = 1; q < 8; ++q) kk = max(kk, kred[q][tx]);
-    const int e = kk > 0 ? (int)(kk >> 53) - 1023 + 2 : 0;
-    es[tx] = e;
-    if (j < nu) exps[g * nu + j] = e;
-  }
-  __syncthreads();
-  const size_t plane = (size_t)nu * kpad;
-  for (int c = 0; c < GROUP; c += 32) {
-    for (int r = ty; r < 32; r += 8) {
-      const long long k = r0 + c + r;
-      long long R = 0;
-      if (k < krows && j < nu) {
-        int E;
-        long long m;
-        bool neg;
-        dsplit_bits(src[k * nu + j], E, m, neg);
-        if (m) R = fixed56(E + (rs ? rsign * rs[k] : 0), m, neg, es[tx]);
-      }
+      dsplit_bits(tile[rr * SPLIT_COLS + c], E, m, neg);
+      const long long X = m ? fixed56(E + shf[rr], m, neg, e) : 0;
+      const unsigned long long Y = (unsigned long long)(X + DIGIT_OFFSET);
+      const uint32_t lo = (uint32_t)Y, hi = (uint32_t)(Y >> 32);
+      uint32_t d[NS];
+      d[0] = digit_bf16((int)hi >> 17);
+      d[1] = digit_bf16((int)((hi >> 10) & 127) - 64);
+      d[2] = digit_bf16((int)((hi >> 3) & 127) - 64);
+      d[3] = digit_bf16((int)(__funnelshift_r(lo, hi, 28) & 127) - 64);
+      d[4] = digit_bf16((int)((lo >> 21) & 127) - 64);
+      d[5] = digit_bf16((int)((lo >> 14) & 127) - 64);
+      d[6] = digit_bf16((int)((lo >> 7) & 127) - 64);
+      d[7] = digit_bf16((int)(lo & 127) - 64);
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
-        const int sh = 49 - 7 * t;
-        const long long q = sh > 0 ? (R + (1ll << (sh - 1))) >> sh : R;
-        R -= q << sh;
-        sl[t][tx][r] = __int2bfloat16_rn((int)q);
+        if (r & 1) w[t][r >> 1] |= d[t] << 16;
+        else w[t][r >> 1] = d[t];
       }
     }
-    __syncthreads();
-    for (int jj = ty; jj < 32; jj += 8) {
-      const int jc = j0 + jj;
-      if (jc < nu) {
 #pragma unroll
-        for (int t = 0; t < NS; ++t) planes[t * plane + (size_t)jc * kpad + r0 + c + tx] = sl[t][jj][tx];
+    for (int t = 0; t < NS; ++t)
+      *reinterpret_cast<uint4 *>(buf + (t * SPLIT_COLS + c) * SPLIT_ROW + o * 8) =
+          make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+    __syncthreads();
+    // (4) 16-byte pieces (plane, column, piece of 8 rows), pieces fastest
+    for (int p = tid; p < NS * SPLIT_COLS * (SPLIT_CHUNK / 8); p += 256) {
+      const int seg = p & 15, jj = (p >> 4) & 15, t = p >> 8;
+      if (jj < ncol) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(buf + (t * SPLIT_COLS + jj) * SPLIT_ROW + seg * 8);
+        __stcs(reinterpret_cast<uint4 *>(planes + t * plane + (size_t)(j0 + jj) * kpad + rg + cb + seg * 8), v);
       }
     }
     __syncthreads();
@@ -430,8 +486,11 @@ void launch_emu_rowscale(const EmuPlan &P, const double *Z, const double *Y, int
 }
 
 void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st) {
-  dim3 grid((unsigned)(P.kpad / emu::GROUP), (unsigned)((P.nu + 31) / 32));
-  emu::k_emu_split<<<grid, dim3(32, 8), 0, st>>>(P.krows, P.nu, P.kpad, src, rs, b_side ? -1 : 1,
+  static const bool cap = cudaFuncSetAttribute(emu::k_emu_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)emu::SPLIT_SMEM) == cudaSuccess;
+  (void)cap;
+  dim3 grid((unsigned)((P.nu + emu::SPLIT_COLS - 1) / emu::SPLIT_COLS), (unsigned)(P.kpad / emu::GROUP));
+  emu::k_emu_split<<<grid, 256, emu::SPLIT_SMEM, st>>>(P.krows, P.nu, P.kpad, src, rs, b_side ? -1 : 1,
                                                  (__nv_bfloat16 *)(b_side ? P.b_planes : P.a_planes),
                                                  b_side ? P.exp_b : P.exp_a);
   ipm_count_launch();

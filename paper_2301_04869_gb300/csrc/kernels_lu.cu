@@ -79,14 +79,66 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
   const int *ts = S.tail_slot;
   const int k0 = nd - ns;
   __syncthreads();
+  // Products of the sparse pivots into the trailing block (L already
+  // scaled): each entry owned by one thread, its products summed and
+  // subtracted once; lists interleaved over the threads (coalesced).
+  // The products read sparse L and U slots only, never a trailing-block
+  // slot, so batches of eight have all their loads issued before the
+  // multiply-adds and stores.
+  {
+    const int len = S.tw_len[tid];
+    const double *__restrict__ Ar = A;
+    double acc = 0.0;
+    for (int q0 = 0; q0 < len; q0 += 8) {
+      double lv[8], uv[8];
+      int ev[8];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        lv[b] = 0.0;
+        uv[b] = 0.0;
+        ev[b] = -1;
+        if (q0 + b < len) {
+          const size_t at = (size_t)(q0 + b) * LU_THREADS + tid;
+          lv[b] = Ar[S.tw_l[at]];
+          uv[b] = Ar[S.tw_u[at]];
+          ev[b] = S.tw_e[at];
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if (q0 + b < len) {
+          acc = fma(lv[b], uv[b], acc);
+          if (ev[b] >= 0) {
+            A[ev[b]] -= acc;
+            acc = 0.0;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // columns [0, k0 - 1) through the slot map; the last of them is fused
+  // into the load of the shared-memory block
   for (int k = 0; k < k0; ++k) {
-    const double d = A[ts[k * nd + k]];
     if (tid == 0) {
+      const double d = A[ts[k * nd + k]];
       if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
       r[t0 + k] = 1.0 / d;
+      sh[0] = r[t0 + k];
     }
-    const double rk = 1.0 / d;
+    __syncthreads();
+    const double rk = sh[0];
     const int m = nd - k - 1;
+    if (k + 1 == k0) {
+      // T = A22 - (A21 / d) A12, and L21 = A21 / d written back
+      for (int e = tid; e < ns * ns; e += bd) {
+        const int a = k0 + e / ns, b = k0 + e % ns;
+        T[e] = A[ts[a * nd + b]] - (A[ts[a * nd + k]] * rk) * A[ts[k * nd + b]];
+      }
+      __syncthreads();
+      for (int e = tid; e < m; e += bd) A[ts[(k + 1 + e) * nd + k]] *= rk;
+      break;
+    }
     for (int e = tid; e < m; e += bd) A[ts[(k + 1 + e) * nd + k]] *= rk;
     __syncthreads();
     for (int e = tid; e < m * m; e += bd) {
@@ -96,7 +148,8 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
     __syncthreads();
   }
   if (ns == 0) return;
-  for (int e = tid; e < ns * ns; e += bd) T[e] = A[ts[(k0 + e / ns) * nd + k0 + e % ns]];
+  if (k0 == 0)
+    for (int e = tid; e < ns * ns; e += bd) T[e] = A[ts[(k0 + e / ns) * nd + k0 + e % ns]];
   __syncthreads();
   // Blocked right-looking LU of the ns x ns block in shared memory (static
   // diagonal pivots): per panel of PB columns, (a) the panel column by
@@ -107,20 +160,22 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
   for (int kb = 0; kb < ns; kb += PB) {
     const int pb = min(PB, ns - kb), ke = kb + pb;
     for (int k = kb; k < ke; ++k) {
-      const double d = T[k * ns + k];
+      // one thread forms the pivot's reciprocal (a dependent FP64 division
+      // is ~9 multiply-adds of FP64 work: not once per thread)
       if (tid == 0) {
+        const double d = T[k * ns + k];
         if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
         r[t0 + k0 + k] = 1.0 / d;
+        sh[0] = r[t0 + k0 + k];
       }
-      const double rk = 1.0 / d;
-      for (int i = k + 1 + tid; i < ns; i += bd) T[i * ns + k] *= rk;
       __syncthreads();
-      const int cols = ke - k - 1;
-      if (cols > 0)
-        for (int e = tid; e < (ns - k - 1) * PB; e += bd) {
-          const int i = k + 1 + e / PB, j = k + 1 + e % PB;
-          if (j < ke) T[i * ns + j] -= T[i * ns + k] * T[k * ns + j];
-        }
+      const double rk = sh[0];
+      // thread per row: scale L(i, k), update the rest of the panel row
+      for (int i = k + 1 + tid; i < ns; i += bd) {
+        const double l = T[i * ns + k] * rk;
+        T[i * ns + k] = l;
+        for (int j = k + 1; j < ke; ++j) T[i * ns + j] -= l * T[k * ns + j];
+      }
       __syncthreads();
     }
     if (ke >= ns) break;

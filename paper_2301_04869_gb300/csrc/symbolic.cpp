@@ -337,6 +337,10 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
     S.f_piv_ptr[l + 1] = (int)S.f_piv.size();
   }
   S.f_op_ptr.push_back(0);
+  // updates of the dense trailing block by the sparse pivots (L(i,k) U(k,j),
+  // i, j >= t0, k < t0) are kept out of the level lists: per trailing-block
+  // entry, all its products, applied after the sparse phase (see below)
+  std::map<int, std::vector<std::pair<int, int>>> tail_ops;  // slot -> (L slot, U slot)
   for (int l = 0; l < nlevf; ++l) {
     std::unordered_map<int, std::vector<int>> tg;  // target slot -> pivots
     std::vector<int> tslots;
@@ -354,6 +358,11 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
       int i = S.lu_row[t];
       // column of slot t
       int j = (int)(std::upper_bound(S.lu_colptr.begin(), S.lu_colptr.end(), t) - S.lu_colptr.begin()) - 1;
+      if (i >= t0 && j >= t0) {
+        auto &v = tail_ops[t];
+        for (int k : tg[t]) v.push_back({luslot(i, k), luslot(k, j)});
+        continue;
+      }
       S.f_tgt.push_back(t);
       for (int k : tg[t]) {
         S.f_op_l.push_back(luslot(i, k));
@@ -367,6 +376,47 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   S.n_ops = (long long)S.f_op_l.size();
   for (int k = 0; k < t0; ++k)
     for (int i : pat[k]) { S.lsc_slot.push_back(luslot(i, k)); S.lsc_k.push_back(k); }
+  // Trailing-block products, one list per thread of the factorization CTA
+  // (LU_THREADS): entries dealt to the least-loaded thread, longest first;
+  // op s of thread t at s * LU_THREADS + t (coalesced); tw_e names the entry
+  // slot after its last product, else -1.
+  {
+    std::vector<std::pair<int, int>> ents;  // (op count, slot)
+    for (auto &kv : tail_ops) ents.push_back({(int)kv.second.size(), kv.first});
+    std::sort(ents.begin(), ents.end(), [](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+      return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    std::vector<std::vector<int>> own(LU_THREADS);
+    std::vector<long long> load(LU_THREADS, 0);
+    for (auto &e : ents) {
+      int best = 0;
+      for (int q = 1; q < LU_THREADS; ++q)
+        if (load[q] < load[best]) best = q;
+      own[best].push_back(e.second);
+      load[best] += e.first;
+    }
+    int M = 0;
+    for (int q = 0; q < LU_THREADS; ++q) M = std::max(M, (int)load[q]);
+    S.tw_len.assign(LU_THREADS, 0);
+    S.tw_l.assign((size_t)M * LU_THREADS, 0);
+    S.tw_u.assign((size_t)M * LU_THREADS, 0);
+    S.tw_e.assign((size_t)M * LU_THREADS, -1);
+    for (int q = 0; q < LU_THREADS; ++q) {
+      int s_ = 0;
+      for (int slot : own[q]) {
+        const auto &v = tail_ops[slot];
+        for (size_t o = 0; o < v.size(); ++o, ++s_) {
+          const size_t at = (size_t)s_ * LU_THREADS + q;
+          S.tw_l[at] = v[o].first;
+          S.tw_u[at] = v[o].second;
+          if (o + 1 == v.size()) S.tw_e[at] = slot;
+        }
+      }
+      S.tw_len[q] = s_;
+    }
+    S.n_tail_ops = 0;
+    for (auto &kv : tail_ops) S.n_tail_ops += (long long)kv.second.size();
+  }
   // forward rows (L rows, k < i) with the matching U(k,i) slots
   {
     std::vector<std::vector<int>> frow(nx);

@@ -48,6 +48,7 @@ def test_slices_reconstruct_the_operand():
     X = rng.normal(size=(512, 4)) * 1e3
     Q, e = emu.split(X)
     assert np.abs(Q).max() <= 64
+    assert Q[1:].min() >= -64 and Q[1:].max() <= 63  # balanced digits after the first
     from fractions import Fraction
     for i in range(0, 512, 37):
         for j in range(4):
