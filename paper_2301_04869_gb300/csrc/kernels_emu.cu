@@ -94,25 +94,26 @@ __device__ __forceinline__ long long fixed56(int E, long long m, bool neg, int e
 // (2^-57).  A digit becomes BF16 bits through the FP32 pattern of
 // 1.5 2^23 + q (exact for |q| < 2^22; the low 16 bits are zero).
 //
-// CTA: one row group (512 rows) x 16 columns.  The group is copied into
-// shared memory once with asynchronous 8-byte copies (all 64 KB in flight,
+// CTA: one row group (512 rows) x 8 columns.  The group is copied into
+// shared memory once with asynchronous 8-byte copies (all 32 KB in flight,
 // no second read of global memory); the column maxima and the digits are
-// taken from there.  Digits of 128 rows at a time go through a staging
-// buffer and leave as 256-byte runs of each plane and column (streaming
+// taken from there.  Digits of 256 rows at a time go through a staging
+// buffer and leave as 512-byte runs of each plane and column (streaming
 // stores).  Column blocks are the fast grid index, so the CTAs that share
 // the cache lines of the same rows run together.
 constexpr long long DIGIT_OFFSET = (64ll << 42) + (64ll << 35) + (64ll << 28) + (64ll << 21) + (64ll << 14) +
                                    (64ll << 7) + 64ll;
-constexpr int SPLIT_COLS = 16;
-constexpr int SPLIT_CHUNK = 128;
-constexpr int SPLIT_ROW = SPLIT_CHUNK + 8;  // bf16 per (plane, column) row of the staging buffer (272 bytes)
+constexpr int SPLIT_COLS = 8;                  // columns per CTA
+constexpr int SPLIT_SLOTS = 256 / SPLIT_COLS;  // row slots (threads per column)
+constexpr int SPLIT_CHUNK = SPLIT_SLOTS * 8;   // rows split per pass (8 per thread)
+constexpr int SPLIT_ROW = SPLIT_CHUNK + 8;     // bf16 per (plane, column) row of the staging buffer
 constexpr size_t SPLIT_SMEM = (size_t)GROUP * SPLIT_COLS * sizeof(double) + (size_t)NS * SPLIT_COLS * SPLIT_ROW * 2;
 
 __device__ __forceinline__ uint32_t digit_bf16(int q) {
   return __float_as_uint(__int_as_float(0x4B400000 + q) - 12582912.0f) >> 16;
 }
 
-__global__ void __launch_bounds__(256, 2) k_emu_split(long long krows, int nu, long long kpad,
+__global__ void __launch_bounds__(256, 3) k_emu_split(long long krows, int nu, long long kpad,
                                                       const double *__restrict__ src, const int *__restrict__ rs,
                                                       int rsign, __nv_bfloat16 *planes, int *exps) {
   extern __shared__ __align__(16) uint8_t split_smem[];
@@ -120,14 +121,14 @@ __global__ void __launch_bounds__(256, 2) k_emu_split(long long krows, int nu, l
   uint16_t *buf = reinterpret_cast<uint16_t *>(split_smem + (size_t)GROUP * SPLIT_COLS * sizeof(double));
   __shared__ int es[SPLIT_COLS];
   __shared__ int shf[GROUP];
-  __shared__ unsigned long long kred[16][SPLIT_COLS];
+  __shared__ unsigned long long kred[SPLIT_SLOTS][SPLIT_COLS];
   const int j0 = blockIdx.x * SPLIT_COLS;
   const long long g = blockIdx.y, rg = g * GROUP;
-  const int tid = threadIdx.x, c = tid & 15, o = tid >> 4;  // column, row slot 0..15
+  const int tid = threadIdx.x, c = tid % SPLIT_COLS, o = tid / SPLIT_COLS;  // column, row slot
   const int j = j0 + c;
   const bool jv = j < nu;
   // (1) the group into shared memory; row shifts alongside
-  for (int r = o; r < GROUP; r += 16) {
+  for (int r = o; r < GROUP; r += SPLIT_SLOTS) {
     const long long k = rg + r;
     double *d = tile + r * SPLIT_COLS + c;
     if (k < krows && jv) {
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(256, 2) k_emu_split(long long krows, int nu, l
   // mantissa) as one unsigned key; balanced exponents outside 1..2047 count
   // as zero / clamp
   unsigned long long key = 0;
-  for (int r = o; r < GROUP; r += 16) {
+  for (int r = o; r < GROUP; r += SPLIT_SLOTS) {
     int E;
     long long m;
     bool neg;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(256, 2) k_emu_split(long long krows, int nu, l
   __syncthreads();
   if (tid < SPLIT_COLS) {
     unsigned long long kk = kred[0][tid];
-    for (int q = 1; q < 16; ++q) kk = max(kk, kred[q][tid]);
+    for (int q = 1; q < SPLIT_SLOTS; ++q) kk = max(kk, kred[q][tid]);
     const int e = kk > 0 ? (int)(kk >> 53) - 1023 + 2 : 0;
     es[tid] = e;
     if (j0 + tid < nu) exps[g * nu + j0 + tid] = e;
@@ -205,7 +206,8 @@ __global__ void __launch_bounds__(256, 2) k_emu_split(long long krows, int nu, l
     __syncthreads();
     // (4) 16-byte pieces (plane, column, piece of 8 rows), pieces fastest
     for (int p = tid; p < NS * SPLIT_COLS * (SPLIT_CHUNK / 8); p += 256) {
-      const int seg = p & 15, jj = (p >> 4) & 15, t = p >> 8;
+      const int seg = p % (SPLIT_CHUNK / 8), jj = (p / (SPLIT_CHUNK / 8)) % SPLIT_COLS,
+                t = p / (SPLIT_CHUNK / 8 * SPLIT_COLS);
       if (jj < ncol) {
         const uint4 v = *reinterpret_cast<const uint4 *>(buf + (t * SPLIT_COLS + jj) * SPLIT_ROW + seg * 8);
         __stcs(reinterpret_cast<uint4 *>(planes + t * plane + (size_t)(j0 + jj) * kpad + rg + cb + seg * 8), v);
