@@ -140,7 +140,7 @@ void tc_plan(int nu, long long krows, TcPlan &P);
 // multiple of 8), box 64 (k) x 128 (rows), 128-byte swizzle
 bool tc_make_kmajor_map(void *map, const void *base, int rows, long long k);
 // the same with a box of box_rows rows (64 or 128)
-bool tc_make_kmajor_map_box(void *map, const void *base, int rows, long long k, int box_rows);
+bool tc_make_kmajor_map_box(void *map, const void *base, int rows, long long k, int box_rows, int box_k);
 
 // kernels_emu.cu (FP64-grade K_hat from exact BF16 slices on the tensor cores)
 struct EmuPlan {

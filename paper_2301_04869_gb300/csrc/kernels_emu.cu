@@ -20,8 +20,10 @@
 // integers (levels 0-5 and levels 6-7), converts their sum to FP64 (two
 // roundings) and accumulates it, scaled by 2^(e_A + e_B - 49), in FP64.
 //
-// Tiles are 128 (rows of K_hat) x 64 (columns), upper part only; one stage
-// of operands (8 x 16 KB + 8 x 8 KB); TMEM holds the eight 64-column level
+// Tiles are 128 (rows of K_hat) x 64 (columns), upper part only; two
+// stages of operands, 32 rows of the contraction each (8 x 8 KB + 8 x 4 KB,
+// 64-byte rows with the 64-byte swizzle), so the TMA loads of one stage run
+// under the MMAs of the other; TMEM holds the eight 64-column level
 // accumulators (all 512 columns).  Warp 0 issues the TMA loads, warp 1 the MMAs, warps 2-9
 // drain the levels (lane quarter x column half); every wait is bounded as in
 // the BF16x3 kernel (kernels_tc.cu).  A non-finite sum raises FLAG_NONFINITE and
@@ -44,13 +46,16 @@ namespace emu {
 using namespace tcx;
 
 constexpr int NS = 8;                      // slices per operand
-constexpr int BM = 128, BN = 64, BK = 64;  // tile
+constexpr int BM = 128, BN = 64, BK = 32;  // tile; K per stage (64-byte rows, 64-byte swizzle)
 constexpr int GROUP = 512;                 // rows per exact level sum
 constexpr int KB_PER_GROUP = GROUP / BK;
-constexpr int A_PLANE = BM * BK * 2;  // 16 KB
-constexpr int B_PLANE = BN * BK * 2;  // 8 KB
-constexpr int STAGE_BYTES = NS * (A_PLANE + B_PLANE);
-constexpr int SMEM_BYTES = STAGE_BYTES + 1024 + 256;
+constexpr int A_PLANE = BM * BK * 2;  // 8 KB
+constexpr int B_PLANE = BN * BK * 2;  // 4 KB
+constexpr int STAGE_BYTES = NS * (A_PLANE + B_PLANE);  // 96 KB
+constexpr int NSTAGE = 2;                               // TMA of one stage under the MMAs of the other
+// stages, alignment slack, barriers, and 8 KB of slack after the last
+// plane (no descriptor can address past the allocation)
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256 + 8192;
 
 struct Maps {
   CUtensorMap a[NS], b[NS];
@@ -251,9 +256,9 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
                                                       double *partial, int *flags) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGE_BYTES);
-  uint64_t *empty = full + 1;
-  uint64_t *acc_full = empty + 1;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE_BYTES);  // [NSTAGE]
+  uint64_t *empty = full + NSTAGE;                                               // [NSTAGE]
+  uint64_t *acc_full = empty + NSTAGE;
   uint64_t *acc_empty = acc_full + 1;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -265,8 +270,10 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
   const int nkb = kb1 - kb0;               // a multiple of KB_PER_GROUP
   const int ngr = nkb / KB_PER_GROUP;
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
-    mbar_init(empty, 1);
+    for (int q = 0; q < NSTAGE; ++q) {
+      mbar_init(full + q, 1);
+      mbar_init(empty + q, 1);
+    }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 8);
     *abort_flag = 0;
@@ -284,34 +291,42 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
 
   if (warp == 0 && lane == 0) {
     for (int i = 0; i < nkb; ++i) {
-      if (i >= 1 && !mbar_wait(empty, (i - 1) & 1)) {
+      const int s = i % NSTAGE;
+      // stage s is free once the MMAs of load i - NSTAGE have completed
+      if (i >= NSTAGE && !mbar_wait(empty + s, ((i - NSTAGE) / NSTAGE) & 1)) {
         flags[FLAG_TIMEOUT] = 1;
         *abort_flag = 1;
         break;
       }
       if (*abort_flag) break;
-      mbar_expect_tx(full, STAGE_BYTES);
+      uint8_t *st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(full + s, STAGE_BYTES);
       const int kx = (kb0 + i) * BK;
-      for (int p = 0; p < NS; ++p) tma_load_2d(smem + p * A_PLANE, &maps.a[p], full, kx, ti * BM);
-      for (int p = 0; p < NS; ++p) tma_load_2d(smem + NS * A_PLANE + p * B_PLANE, &maps.b[p], full, kx, tj * BN);
+      for (int p = 0; p < NS; ++p) tma_load_2d(st + p * A_PLANE, &maps.a[p], full + s, kx, ti * BM);
+      for (int p = 0; p < NS; ++p) tma_load_2d(st + NS * A_PLANE + p * B_PLANE, &maps.b[p], full + s, kx, tj * BN);
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    const uint32_t abase = smem_u32(smem), bbase = abase + NS * A_PLANE;
     for (int i = 0; i < nkb; ++i) {
+      const int s = i % NSTAGE;
       const int d = i / KB_PER_GROUP, kbi = i % KB_PER_GROUP;
       if (kbi == 0 && d >= 1 && !mbar_wait(acc_empty, (d - 1) & 1)) {
         flags[FLAG_TIMEOUT] = 1;
         *abort_flag = 1;
         break;
       }
-      if (!mbar_wait(full, i & 1)) {
+      if (!mbar_wait(full + s, (i / NSTAGE) & 1)) {
         flags[FLAG_TIMEOUT] = 1;
         *abort_flag = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // descriptors of the stage's first A and B planes; the others differ
+      // only in the start-address field (16-byte units, no carry: the
+      // stage lies below 256 KB of shared memory)
+      const uint32_t abase = smem_u32(smem + s * STAGE_BYTES), bbase = abase + NS * A_PLANE;
+      const uint64_t da0 = sdesc_sw64(abase), db0 = sdesc_sw64(bbase);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
@@ -320,12 +335,12 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
           for (int t = 0; t <= L; ++t) {
             const int u = L - t;
             const uint32_t acc = (kbi > 0 || kk > 0 || t > 0) ? 1u : 0u;
-            mma_bf16(tmem + (uint32_t)(L * BN), sdesc(abase + t * A_PLANE + kk * 32),
-                     sdesc(bbase + u * B_PLANE + kk * 32), idesc, acc);
+            mma_bf16(tmem + (uint32_t)(L * BN), da0 + (uint64_t)((t * A_PLANE + kk * 32) >> 4),
+                     db0 + (uint64_t)((u * B_PLANE + kk * 32) >> 4), idesc, acc);
           }
         }
       }
-      mma_commit(empty);
+      mma_commit(empty + s);
       if (kbi == KB_PER_GROUP - 1) mma_commit(acc_full);
     }
   } else if (warp >= 2) {
@@ -367,7 +382,9 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            const long long a = (long long)__float2ll_rn(__uint_as_float(v[e]));  // exact: an integer
+            // exact: an integer of at most 2^24 in magnitude (a 32-bit
+            // conversion; the 64-bit one runs on the FP64 units)
+            const long long a = (long long)__float2int_rn(__uint_as_float(v[e]));
             if (L == 0) V[e] = a;
             else if (L <= 5) V[e] = (V[e] << 7) + a;
             else if (L == 6) W[e] = a << 7;
@@ -397,7 +414,9 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
     }
     if (bad) flags[FLAG_NONFINITE] = 1;
   }
-  if (warp == 0 && lane == 0 && *abort_flag && issued > 0) (void)mbar_wait(full, (issued - 1) & 1);
+  // after an abort, let the loads in flight land before the CTA exits
+  if (warp == 0 && lane == 0 && *abort_flag)
+    for (int i = max(0, issued - NSTAGE); i < issued; ++i) (void)mbar_wait(full + i % NSTAGE, (i / NSTAGE) & 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -462,8 +481,10 @@ bool emu_plan(EmuPlan &P, int nu, long long krows, const void *a_planes, const v
   emu::Maps m;
   const size_t plane = (size_t)nu * P.kpad * 2;
   for (int p = 0; p < emu::NS; ++p) {
-    if (!tc_make_kmajor_map_box(&m.a[p], (const char *)a_planes + p * plane, nu, P.kpad, emu::BM)) return false;
-    if (!tc_make_kmajor_map_box(&m.b[p], (const char *)b_planes + p * plane, nu, P.kpad, emu::BN)) return false;
+    if (!tc_make_kmajor_map_box(&m.a[p], (const char *)a_planes + p * plane, nu, P.kpad, emu::BM, emu::BK))
+      return false;
+    if (!tc_make_kmajor_map_box(&m.b[p], (const char *)b_planes + p * plane, nu, P.kpad, emu::BN, emu::BK))
+      return false;
   }
   static_assert(sizeof(emu::Maps) <= sizeof(P.maps), "map storage");
   memcpy(P.maps, &m, sizeof(m));

@@ -279,15 +279,18 @@ static EncodeTiledFn get_encode() {
 }
 
 // tensor map of one BF16 plane [rows][kpad], box 64 (K) x box_rows, 128-byte swizzle
-static bool make_map(CUtensorMap *m, const void *base, int rows, long long kpad, int box_rows = tc::BM) {
+static bool make_map(CUtensorMap *m, const void *base, int rows, long long kpad, int box_rows = tc::BM,
+                     int box_k = tc::BK) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-  cuuint32_t box[2] = {tc::BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
+  // 128-byte rows (64 BF16) take the 128-byte swizzle, 64-byte rows the 64-byte one
+  const CUtensorMapSwizzle sw = box_k * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -295,8 +298,9 @@ bool tc_make_kmajor_map(void *map, const void *base, int rows, long long k) {
   return make_map(reinterpret_cast<CUtensorMap *>(map), base, rows, k);
 }
 
-bool tc_make_kmajor_map_box(void *map, const void *base, int rows, long long k, int box_rows) {
-  return make_map(reinterpret_cast<CUtensorMap *>(map), base, rows, k, box_rows);
+bool tc_make_kmajor_map_box(void *map, const void *base, int rows, long long k, int box_rows, int box_k) {
+  if (box_k != 32 && box_k != 64) return false;
+  return make_map(reinterpret_cast<CUtensorMap *>(map), base, rows, k, box_rows, box_k);
 }
 
 void tc_plan(int nu, long long krows, TcPlan &P) {

@@ -60,6 +60,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
+// the same for 64-byte rows (K = 32 BF16 per row) with 64-byte swizzle:
+// 8-row groups 512 bytes apart, layout type 4
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                      // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;             // SBO
+  d |= (uint64_t)1 << 46;                      // version
+  d |= (uint64_t)4 << 61;                      // SWIZZLE_64B
+  return d;
+}
+
 // instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4)            // D = F32
