@@ -39,13 +39,13 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
 // updates), then the dense trailing block [t0, nx) is factorized right-looking
 // in shared memory when it fits (dynamic shared memory of nd*nd doubles),
 // else in place through the slot map.
-__global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, double *LU, double *rd,
-                            int *flags, double piv_tol, int ns) {
-  __shared__ double sh[32];
-  extern __shared__ double T[];
-  const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
-  double *A = LU + (size_t)sc * S.nnzLU;
-  double *r = rd + (size_t)sc * S.nx;
+// Sparse part of the factorization of one scenario by one CTA: values of
+// G_x into the LU pattern, the level-scheduled sparse pivots (gather form),
+// the scaling of L, and the products of the sparse pivots into the dense
+// trailing block.  Returns max |G_x| (the reference of the pivot test).
+__device__ double lu_sparse_part(const DevSym &S, int nL, const double *__restrict__ J, double *A, double *r,
+                                 int *flags, double piv_tol, int sc, double *sh) {
+  const int tid = threadIdx.x, bd = blockDim.x;
   double amax = 0.0;
   for (int p = tid; p < S.nnzLU; p += bd) {
     const int src = S.lu_init[p];
@@ -72,13 +72,8 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
     __syncthreads();
   }
   for (int e = tid; e < nL; e += bd) A[S.lsc_slot[e]] *= r[S.lsc_k[e]];
-  // dense trailing block: columns [0, k0) in place through the slot map,
-  // then the remaining (nd-k0)^2 block in shared memory (k0 = nd - ns)
-  const int nd = S.nd, t0 = S.t0;
-  if (nd == 0) return;
-  const int *ts = S.tail_slot;
-  const int k0 = nd - ns;
   __syncthreads();
+  if (S.nd == 0) return amax;
   // Products of the sparse pivots into the trailing block (L already
   // scaled): each entry owned by one thread, its products summed and
   // subtracted once; lists interleaved over the threads (coalesced).
@@ -117,6 +112,23 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
     }
   }
   __syncthreads();
+  return amax;
+}
+
+__global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, double *LU, double *rd,
+                            int *flags, double piv_tol, int ns) {
+  __shared__ double sh[32];
+  extern __shared__ double T[];
+  const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  double *A = LU + (size_t)sc * S.nnzLU;
+  double *r = rd + (size_t)sc * S.nx;
+  const double amax = lu_sparse_part(S, nL, J, A, r, flags, piv_tol, sc, sh);
+  const int nd = S.nd, t0 = S.t0;
+  if (nd == 0) return;
+  const int *ts = S.tail_slot;
+  // dense trailing block: columns [0, k0) in place through the slot map,
+  // then the remaining (nd-k0)^2 block in shared memory (k0 = nd - ns)
+  const int k0 = nd - ns;
   // columns [0, k0 - 1) through the slot map; the last of them is fused
   // into the load of the shared-memory block
   for (int k = 0; k < k0; ++k) {
@@ -607,6 +619,146 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
     for (int i = tid; i < nx; i += bd) vs[i] = x[i];
 }
 
+
+// Cluster helpers: rank in the cluster, a barrier over both CTAs with
+// release/acquire ordering (shared and global memory), and a load from the
+// peer CTA's shared memory.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ double ld_peer(const double *local, unsigned peer) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local));
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(peer));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// The same factorization by a cluster of two CTAs per scenario (two SMs'
+// FP64 units for the dense trailing block): CTA 0 does the sparse part; the
+// nd x nd trailing block is then split by column panels of 16, panel q
+// held by CTA q mod 2 in its shared memory.  Per panel: its owner factors
+// it (pivots, L column scaling, the rest of the panel), both CTAs meet at a
+// cluster barrier, the other CTA copies the panel from the owner's shared
+// memory, and each CTA solves U12 = L11^{-1} A12 and updates A22 -= L21 U12
+// on its own columns (4 x 4 register tiles).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
+    k_lu_factor_pair(DevSym S, int nL, const double *__restrict__ J, double *LU, double *rd, int *flags,
+                     double piv_tol) {
+  constexpr int PB = 16;
+  __shared__ double sh[32];
+  extern __shared__ double Tl[];
+  const unsigned rank = cluster_rank();
+  const int sc = blockIdx.x >> 1, tid = threadIdx.x, bd = blockDim.x;
+  double *A = LU + (size_t)sc * S.nnzLU;
+  double *r = rd + (size_t)sc * S.nx;
+  const int nd = S.nd, t0 = S.t0, ns = nd;
+  if (rank == 0) {
+    const double am = lu_sparse_part(S, nL, J, A, r, flags, piv_tol, sc, sh);
+    if (tid == 0) sh[16] = am;
+  }
+  if (nd == 0) return;  // the same on both CTAs
+  cluster_sync_all();   // sparse part, trailing-block products and max |G_x| visible
+  const double amax = rank == 0 ? sh[16] : ld_peer(&sh[16], 0);
+  const int np = (ns + PB - 1) / PB, LDL = ((np + 1) / 2) * PB;
+  double *Pb = Tl + (size_t)ns * LDL;  // the other CTA's panel [ns][PB]
+  const int *ts = S.tail_slot;
+  // own local column lc <-> block column (2 (lc / PB) + rank) PB + lc % PB
+  for (int e = tid; e < ns * LDL; e += bd) {
+    const int i = e / LDL, lc = e % LDL;
+    const int c = (2 * (lc / PB) + (int)rank) * PB + lc % PB;
+    Tl[e] = c < ns ? A[ts[i * nd + c]] : 0.0;
+  }
+  __syncthreads();
+  for (int p = 0; p < np; ++p) {
+    const int kb = p * PB, ke = min(kb + PB, ns), pb = ke - kb;
+    const bool own = (p & 1) == (int)rank;
+    const int lc0 = (p >> 1) * PB;  // the panel's first local column in its owner
+    if (own) {
+      for (int k = kb; k < ke; ++k) {
+        const int lk = lc0 + (k - kb);
+        if (tid == 0) {
+          const double d = Tl[k * LDL + lk];
+          if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
+          r[t0 + k] = 1.0 / d;
+          sh[17] = r[t0 + k];
+        }
+        __syncthreads();
+        const double rk = sh[17];
+        for (int i = k + 1 + tid; i < ns; i += bd) {
+          const double l = Tl[i * LDL + lk] * rk;
+          Tl[i * LDL + lk] = l;
+          for (int j = k + 1; j < ke; ++j) Tl[i * LDL + lc0 + (j - kb)] -= l * Tl[k * LDL + lc0 + (j - kb)];
+        }
+        __syncthreads();
+      }
+    }
+    cluster_sync_all();  // panel p factored
+    if (p == np - 1) break;
+    const double *Lp;
+    int ldp, cp0;
+    if (own) {
+      Lp = Tl;
+      ldp = LDL;
+      cp0 = lc0;
+    } else {
+      for (int e = tid; e < (ns - kb) * pb; e += bd) {
+        const int i = kb + e / pb, j = e % pb;
+        Pb[i * PB + j] = ld_peer(&Tl[i * LDL + lc0 + j], rank ^ 1u);
+      }
+      __syncthreads();
+      Lp = Pb;
+      ldp = PB;
+      cp0 = 0;
+    }
+    // own columns right of the panel: local panels from lps on
+    const int lcs = ((p + 2 - (int)rank) / 2) * PB;
+    for (int lj = lcs + tid; lj < LDL; lj += bd)
+      for (int k = kb; k < ke; ++k) {
+        const double x = Tl[k * LDL + lj];
+        for (int i = k + 1; i < ke; ++i) Tl[i * LDL + lj] -= Lp[i * ldp + cp0 + (k - kb)] * x;
+      }
+    __syncthreads();
+    const int m = ns - ke, nc = LDL - lcs, nt4r = (m + 3) / 4, nt4c = (nc + 3) / 4;
+    for (int e = tid; e < nt4r * nt4c; e += bd) {
+      const int i0 = ke + (e / nt4c) * 4, j0 = lcs + (e % nt4c) * 4;
+      double c[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) c[a][b] = 0.0;
+      for (int k = kb; k < ke; ++k) {
+        double lv[4], uv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) lv[a] = i0 + a < ns ? Lp[(i0 + a) * ldp + cp0 + (k - kb)] : 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) uv[b] = j0 + b < LDL ? Tl[k * LDL + j0 + b] : 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) c[a][b] = fma(lv[a], uv[b], c[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (i0 + a < ns && j0 + b < LDL) Tl[(i0 + a) * LDL + j0 + b] -= c[a][b];
+    }
+    __syncthreads();
+  }
+  cluster_sync_all();  // no CTA leaves while the other may still read its panels
+  for (int e = tid; e < ns * LDL; e += bd) {
+    const int i = e / LDL, lc = e % LDL;
+    const int c = (2 * (lc / PB) + (int)rank) * PB + lc % PB;
+    if (c < ns) A[ts[i * nd + c]] = Tl[e];
+  }
+}
 }  // namespace
 
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
@@ -623,6 +775,23 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
     while ((size_t)(n + 1) * (n + 1) * sizeof(double) + fa.sharedSizeBytes <= (size_t)optin) ++n;
     return n;
   }();
+  // a cluster of two CTAs per scenario when the trailing block fits their
+  // shared memory (own columns plus one panel of the other CTA)
+  static const size_t pair_cap = [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_lu_factor_pair) != cudaSuccess) return (size_t)0;
+    return raise_smem_cap(k_lu_factor_pair) ? (size_t)optin - fa.sharedSizeBytes : (size_t)0;
+  }();
+  const int np = (S.nd + 15) / 16, ldl = ((np + 1) / 2) * 16;
+  const size_t pair_smem = (size_t)S.nd * (ldl + 16) * sizeof(double);
+  if (S.nd > 0 && pair_smem <= pair_cap) {
+    k_lu_factor_pair<<<2 * S.N, 512, pair_smem, st>>>(S, nL, J, LU, rd, flags, 1e-14);
+    ipm_count_launch();
+    return;
+  }
   const int ns = S.nd < ns_max ? S.nd : ns_max;
   const size_t smem = (size_t)ns * ns * sizeof(double);
   static const bool cap = raise_smem_cap(k_lu_factor);
