@@ -4,9 +4,9 @@
 #include <math.h>
 #include <stdint.h>
 
-#ifndef IPM_LU_THREADS_DEFINED
-#define IPM_LU_THREADS_DEFINED
-constexpr int LU_THREADS = 512;  // threads of the LU factorization CTA (per-thread op lists)
+#ifndef IPM_LU_LISTS_DEFINED
+#define IPM_LU_LISTS_DEFINED
+constexpr int LU_LISTS = 1024;  // lists of trailing-block products of the LU factorization
 #endif
 
 struct DevSym {

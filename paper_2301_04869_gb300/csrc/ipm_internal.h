@@ -5,9 +5,9 @@
 
 #include "../../include/ipm.h"
 
-#ifndef IPM_LU_THREADS_DEFINED
-#define IPM_LU_THREADS_DEFINED
-constexpr int LU_THREADS = 512;  // threads of the LU factorization CTA (per-thread op lists)
+#ifndef IPM_LU_LISTS_DEFINED
+#define IPM_LU_LISTS_DEFINED
+constexpr int LU_LISTS = 1024;  // lists of trailing-block products of the LU factorization
 #endif
 
 struct HostNet {
@@ -54,8 +54,8 @@ struct Sym {
   std::vector<int> fs_lev_ptr, fs_rows, bs_lev_ptr, bs_rows;
   std::vector<int> f_lev_ptr, f_piv_ptr, f_piv, f_tgt, f_op_ptr, f_op_l, f_op_u, f_op_k;
   std::vector<int> lsc_slot, lsc_k;
-  // products of the sparse pivots into the dense trailing block, per thread
-  // of the factorization CTA (symbolic.cpp)
+  // products of the sparse pivots into the dense trailing block, in
+  // LU_LISTS lists (symbolic.cpp)
   std::vector<int> tw_len, tw_l, tw_u, tw_e;
   long long n_tail_ops = 0;
   std::vector<int> fw_lev_ptr, fw_rows, fr_ptr, fr_col, fr_lslot, fr_uslot;

@@ -39,50 +39,84 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
 // updates), then the dense trailing block [t0, nx) is factorized right-looking
 // in shared memory when it fits (dynamic shared memory of nd*nd doubles),
 // else in place through the slot map.
-// Sparse part of the factorization of one scenario by one CTA: values of
-// G_x into the LU pattern, the level-scheduled sparse pivots (gather form),
-// the scaling of L, and the products of the sparse pivots into the dense
-// trailing block.  Returns max |G_x| (the reference of the pivot test).
+// Cluster helpers: rank in the cluster, a barrier over both CTAs with
+// release/acquire ordering (shared and global memory), and a load from the
+// peer CTA's shared memory.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ double ld_peer(const double *local, unsigned peer) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local));
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(peer));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// Sparse part of the factorization of one scenario: values of G_x into the
+// LU pattern, the level-scheduled sparse pivots (gather form), the scaling
+// of L, and the products of the sparse pivots into the dense trailing
+// block.  One CTA, or (PAIR) the two CTAs of a cluster sharing every step
+// by index parity with cluster barriers between the steps.  Returns
+// max |G_x| (the reference of the pivot test).
+template <bool PAIR>
 __device__ double lu_sparse_part(const DevSym &S, int nL, const double *__restrict__ J, double *A, double *r,
-                                 int *flags, double piv_tol, int sc, double *sh) {
+                                 int *flags, double piv_tol, int sc, double *sh, unsigned rank) {
   const int tid = threadIdx.x, bd = blockDim.x;
+  const int t0i = PAIR ? tid + (int)rank * bd : tid, step = PAIR ? 2 * bd : bd;
+  auto sync = [] {
+    if (PAIR) cluster_sync_all();
+    else __syncthreads();
+  };
   double amax = 0.0;
-  for (int p = tid; p < S.nnzLU; p += bd) {
+  for (int p = t0i; p < S.nnzLU; p += step) {
     const int src = S.lu_init[p];
     const double v = src >= 0 ? J[(size_t)src * S.N + sc] : 0.0;
     A[p] = v;
     amax = fmax(amax, fabs(v));
   }
   amax = block_max(amax, sh);
+  if (PAIR) {
+    if (tid == 0) sh[16] = amax;
+    cluster_sync_all();
+    amax = fmax(amax, ld_peer(&sh[16], rank ^ 1u));
+  }
   for (int l = 0; l < S.nlev_f; ++l) {
-    for (int e = S.f_piv_ptr[l] + tid; e < S.f_piv_ptr[l + 1]; e += bd) {
+    for (int e = S.f_piv_ptr[l] + t0i; e < S.f_piv_ptr[l + 1]; e += step) {
       const int k = S.f_piv[e];
       const double d = A[S.lu_diag[k]];
       if (!(fabs(d) > piv_tol * amax)) flags[FLAG_SINGULAR] = 1;
       r[k] = 1.0 / d;
     }
-    __syncthreads();
-    for (int t = S.f_lev_ptr[l] + tid; t < S.f_lev_ptr[l + 1]; t += bd) {
+    sync();
+    for (int t = S.f_lev_ptr[l] + t0i; t < S.f_lev_ptr[l + 1]; t += step) {
       const int slot = S.f_tgt[t];
       double acc = A[slot];
       for (int o = S.f_op_ptr[t]; o < S.f_op_ptr[t + 1]; ++o)
         acc -= A[S.f_op_l[o]] * (A[S.f_op_u[o]] * r[S.f_op_k[o]]);
       A[slot] = acc;
     }
-    __syncthreads();
+    sync();
   }
-  for (int e = tid; e < nL; e += bd) A[S.lsc_slot[e]] *= r[S.lsc_k[e]];
-  __syncthreads();
+  for (int e = t0i; e < nL; e += step) A[S.lsc_slot[e]] *= r[S.lsc_k[e]];
+  sync();
   if (S.nd == 0) return amax;
   // Products of the sparse pivots into the trailing block (L already
-  // scaled): each entry owned by one thread, its products summed and
-  // subtracted once; lists interleaved over the threads (coalesced).
-  // The products read sparse L and U slots only, never a trailing-block
-  // slot, so batches of eight have all their loads issued before the
-  // multiply-adds and stores.
-  {
-    const int len = S.tw_len[tid];
-    const double *__restrict__ Ar = A;
+  // scaled): each entry owned by one of LU_LISTS lists, its products summed
+  // and subtracted once; lists interleaved (coalesced), list q taken by
+  // thread q of the cluster (or q mod blockDim.x of one CTA).  The products
+  // read sparse L and U slots only, never a trailing-block slot, so batches
+  // of eight have all their loads issued before the multiply-adds and
+  // stores.
+  const double *__restrict__ Ar = A;
+  for (int q = t0i; q < LU_LISTS; q += step) {
+    const int len = S.tw_len[q];
     double acc = 0.0;
     for (int q0 = 0; q0 < len; q0 += 8) {
       double lv[8], uv[8];
@@ -93,7 +127,7 @@ __device__ double lu_sparse_part(const DevSym &S, int nL, const double *__restri
         uv[b] = 0.0;
         ev[b] = -1;
         if (q0 + b < len) {
-          const size_t at = (size_t)(q0 + b) * LU_THREADS + tid;
+          const size_t at = (size_t)(q0 + b) * LU_LISTS + q;
           lv[b] = Ar[S.tw_l[at]];
           uv[b] = Ar[S.tw_u[at]];
           ev[b] = S.tw_e[at];
@@ -111,7 +145,7 @@ __device__ double lu_sparse_part(const DevSym &S, int nL, const double *__restri
       }
     }
   }
-  __syncthreads();
+  sync();
   return amax;
 }
 
@@ -122,7 +156,7 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
   const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
   double *A = LU + (size_t)sc * S.nnzLU;
   double *r = rd + (size_t)sc * S.nx;
-  const double amax = lu_sparse_part(S, nL, J, A, r, flags, piv_tol, sc, sh);
+  const double amax = lu_sparse_part<false>(S, nL, J, A, r, flags, piv_tol, sc, sh, 0u);
   const int nd = S.nd, t0 = S.t0;
   if (nd == 0) return;
   const int *ts = S.tail_slot;
@@ -620,29 +654,9 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
 }
 
 
-// Cluster helpers: rank in the cluster, a barrier over both CTAs with
-// release/acquire ordering (shared and global memory), and a load from the
-// peer CTA's shared memory.
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ double ld_peer(const double *local, unsigned peer) {
-  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local));
-  uint32_t ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(peer));
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
-  return v;
-}
-
 // The same factorization by a cluster of two CTAs per scenario (two SMs'
-// FP64 units for the dense trailing block): CTA 0 does the sparse part; the
-// nd x nd trailing block is then split by column panels of 16, panel q
+// FP64 units): the sparse part shared by index parity; the nd x nd
+// trailing block is then split by column panels of 16, panel q
 // held by CTA q mod 2 in its shared memory.  Per panel: its owner factors
 // it (pivots, L column scaling, the rest of the panel), both CTAs meet at a
 // cluster barrier, the other CTA copies the panel from the owner's shared
@@ -659,13 +673,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
   double *A = LU + (size_t)sc * S.nnzLU;
   double *r = rd + (size_t)sc * S.nx;
   const int nd = S.nd, t0 = S.t0, ns = nd;
-  if (rank == 0) {
-    const double am = lu_sparse_part(S, nL, J, A, r, flags, piv_tol, sc, sh);
-    if (tid == 0) sh[16] = am;
-  }
+  const double amax = lu_sparse_part<true>(S, nL, J, A, r, flags, piv_tol, sc, sh, rank);
   if (nd == 0) return;  // the same on both CTAs
-  cluster_sync_all();   // sparse part, trailing-block products and max |G_x| visible
-  const double amax = rank == 0 ? sh[16] : ld_peer(&sh[16], 0);
   const int np = (ns + PB - 1) / PB, LDL = ((np + 1) / 2) * PB;
   double *Pb = Tl + (size_t)ns * LDL;  // the other CTA's panel [ns][PB]
   const int *ts = S.tail_slot;

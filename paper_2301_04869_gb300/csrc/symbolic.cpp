@@ -376,9 +376,9 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   S.n_ops = (long long)S.f_op_l.size();
   for (int k = 0; k < t0; ++k)
     for (int i : pat[k]) { S.lsc_slot.push_back(luslot(i, k)); S.lsc_k.push_back(k); }
-  // Trailing-block products, one list per thread of the factorization CTA
-  // (LU_THREADS): entries dealt to the least-loaded thread, longest first;
-  // op s of thread t at s * LU_THREADS + t (coalesced); tw_e names the entry
+  // Trailing-block products in LU_LISTS lists (one per thread of a
+  // two-CTA cluster): entries dealt to the least-loaded list, longest first;
+  // op s of list t at s * LU_LISTS + t (coalesced); tw_e names the entry
   // slot after its last product, else -1.
   {
     std::vector<std::pair<int, int>> ents;  // (op count, slot)
@@ -386,27 +386,27 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
     std::sort(ents.begin(), ents.end(), [](const std::pair<int, int> &a, const std::pair<int, int> &b) {
       return a.first != b.first ? a.first > b.first : a.second < b.second;
     });
-    std::vector<std::vector<int>> own(LU_THREADS);
-    std::vector<long long> load(LU_THREADS, 0);
+    std::vector<std::vector<int>> own(LU_LISTS);
+    std::vector<long long> load(LU_LISTS, 0);
     for (auto &e : ents) {
       int best = 0;
-      for (int q = 1; q < LU_THREADS; ++q)
+      for (int q = 1; q < LU_LISTS; ++q)
         if (load[q] < load[best]) best = q;
       own[best].push_back(e.second);
       load[best] += e.first;
     }
     int M = 0;
-    for (int q = 0; q < LU_THREADS; ++q) M = std::max(M, (int)load[q]);
-    S.tw_len.assign(LU_THREADS, 0);
-    S.tw_l.assign((size_t)M * LU_THREADS, 0);
-    S.tw_u.assign((size_t)M * LU_THREADS, 0);
-    S.tw_e.assign((size_t)M * LU_THREADS, -1);
-    for (int q = 0; q < LU_THREADS; ++q) {
+    for (int q = 0; q < LU_LISTS; ++q) M = std::max(M, (int)load[q]);
+    S.tw_len.assign(LU_LISTS, 0);
+    S.tw_l.assign((size_t)M * LU_LISTS, 0);
+    S.tw_u.assign((size_t)M * LU_LISTS, 0);
+    S.tw_e.assign((size_t)M * LU_LISTS, -1);
+    for (int q = 0; q < LU_LISTS; ++q) {
       int s_ = 0;
       for (int slot : own[q]) {
         const auto &v = tail_ops[slot];
         for (size_t o = 0; o < v.size(); ++o, ++s_) {
-          const size_t at = (size_t)s_ * LU_THREADS + q;
+          const size_t at = (size_t)s_ * LU_LISTS + q;
           S.tw_l[at] = v[o].first;
           S.tw_u[at] = v[o].second;
           if (o + 1 == v.size()) S.tw_e[at] = slot;
