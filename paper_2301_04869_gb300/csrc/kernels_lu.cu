@@ -273,7 +273,10 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
                             const double *__restrict__ J, const double *__restrict__ K, T *Z, T *Y, double *Yu,
                             bool tail_smem, T *sh, const double *__restrict__ gvec, T *bvec) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, bd = blockDim.x;
-  const int sc = blockIdx.y, c0 = blockIdx.x * 32, c = c0 + lane, nu = S.nu, nx = S.nx, N = S.N;
+  const int nu = S.nu, nx = S.nx, N = S.N;
+  // the CTA after the panels of Z (when bvec is given) solves b alone
+  const bool bpanel = bvec != nullptr && (int)blockIdx.x == (nu + 31) / 32;
+  const int sc = blockIdx.y, c0 = blockIdx.x * 32, c = bpanel ? nu + lane : c0 + lane;
   const int t0 = S.t0, nd = S.nd;
   const bool valid = c < nu;
   const int cc = valid ? c : nu - 1;
@@ -283,10 +286,12 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
   T *Ys = Y + (size_t)sc * nx * nu;
   double *Yus = Yu + (size_t)sc * nu * nu;
   // Optional extra column n_u (when bvec is given): b = G_x^{-1} g of the
-  // reduced right-hand side rides along in an otherwise idle lane, stored in
-  // bvec [N][n_x] (position order) instead of Z.  zb/zst read a lane's own
-  // column, zw writes it.
-  const bool xb = bvec != nullptr && c == nu;
+  // reduced right-hand side, solved by lane 0 of an extra CTA per scenario
+  // (its forward sweep is dense, unlike those of the columns of G_u, so it
+  // gets a CTA of its own instead of slowing one panel of Z), stored in
+  // bvec [N][n_x] (position order).  zb/zst read a lane's own column, zw
+  // writes it.
+  const bool xb = bpanel && lane == 0;
   T *bs = bvec ? bvec + (size_t)sc * nx : nullptr;
   const T *zb = xb ? bs : Zs + cc;
   T *zw = xb ? bs : Zs + c;
@@ -377,8 +382,11 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
       }
       for (int e = tid; e < nd * 32; e += bd) {
         const int i = e >> 5, q = e & 31;
-        if (c0 + q < nu) Zs[(size_t)(t0 + i) * nu + c0 + q] = sh[i * 32 + q];
-        else if (bvec && c0 + q == nu) bs[t0 + i] = sh[i * 32 + q];
+        if (bpanel) {
+          if (q == 0) bs[t0 + i] = sh[i * 32];
+        } else if (c0 + q < nu) {
+          Zs[(size_t)(t0 + i) * nu + c0 + q] = sh[i * 32 + q];
+        }
       }
       __syncthreads();
     } else {
@@ -425,6 +433,7 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
     }
     __syncthreads();
   }
+  if (bpanel) return;  // b needs no product with K
   for (int row = warp; row < nx; row += nw) {
     T acc = 0;
     for (int e = S.kx_ptr[row]; e < S.kx_ptr[row + 1]; ++e) {
@@ -817,7 +826,7 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
                      const double *g, double *b) {
   const int sm = zsolve_smem_ok(S, sizeof(double));
   if (!zsolve64_folds_b(S)) b = nullptr;
-  dim3 grid((S.nu + (b ? 1 : 0) + 31) / 32, S.N);
+  dim3 grid((S.nu + 31) / 32 + (b ? 1 : 0), S.N);
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(double) : 0;
   // dynamic plus static shared memory may pass the 48 KB default
   static const bool cap = raise_smem_cap(k_zsolve64);

@@ -502,13 +502,14 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   // ---- forward schedules per 32-column panel of the multi-RHS solve ----
   // A column of G_u reaches few rows of the forward sweep L^{-1} G_u: row i
   // is structurally nonzero for a panel iff G_u has an entry of a panel
-  // column in row i, or L(i, k) != 0 for a nonzero row k < i.  The panel
-  // holding column n_u (where b = G_x^{-1} g rides along) keeps every row.
+  // column in row i, or L(i, k) != 0 for a nonzero row k < i.  Panels
+  // 0 .. ceil(n_u/32) - 1 hold the columns of Z; the last one holds
+  // b = G_x^{-1} g alone and keeps every row.
   // Per panel: the nonzero sparse rows by level of the reduced sweep with
   // their products against nonzero rows only, the zero rows, and for each
   // trailing-block row its products against nonzero sparse rows.
   {
-    const int np = (nu + 1 + 31) / 32, t0 = S.t0, nd = S.nd;
+    const int np = (nu + 31) / 32 + 1, t0 = S.t0, nd = S.nd;
     S.zp_npan = np;
     S.zp_lev_off.assign(1, 0);
     S.zp_lev_ptr.assign(1, 0);
@@ -518,8 +519,8 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
     std::vector<char> nz(nx);
     std::vector<int> zl(nx);
     for (int p = 0; p < np; ++p) {
-      const int c0 = 32 * p, c1 = 32 * p + 32;
-      const bool all = c0 <= nu && nu < c1;
+      const int c0 = 32 * p, c1 = std::min(32 * p + 32, nu);
+      const bool all = p == np - 1;  // the panel of b
       int nl = 0;
       for (int i = 0; i < t0; ++i) {
         bool z = all;
