@@ -78,6 +78,11 @@ struct ipm_ctx {
   // phase timers
   bool prof = false;
   cudaEvent_t ev[2 * IPM_N_PHASES] = {};
+  // transposed solve for p_y on a side stream, joined before y is updated
+  // (it overlaps the line search, which does not need p_y)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool py_pending = false;
   bool ev_pending[IPM_N_PHASES] = {};
   double t_ms[IPM_N_PHASES] = {0};
   double t_cnt[IPM_N_PHASES] = {0};

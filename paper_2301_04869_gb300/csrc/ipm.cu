@@ -597,8 +597,16 @@ ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
   return IPM_OK;
 }
 
+// the stream st waits for a p_y solve left on the side stream
+void join_py(ipm_ctx *c, cudaStream_t st) {
+  if (!c->py_pending) return;
+  cudaStreamWaitEvent(st, c->ev_join, 0);
+  c->py_pending = false;
+}
+
 // Sigma, K, LU(G_x), Z, Y, K_hat (delta = 0), reduced right-hand side
 ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
+  join_py(c, st);
   if (!c->have_eval) return fail(c, IPM_ERR_STATE, "condense before eval");
   const DevSym &S = c->ds;
   DevWork &D = c->dw;
@@ -820,8 +828,11 @@ ipm_status pcg_reduced(ipm_ctx *c, double delta, cudaStream_t st) {
 }
 
 // Newton step: p_u from the Cholesky factor, then p_x, p_y (Prop. 2.3),
-// p_z, p_s (Prop. 2.1) and the bound-dual steps.
-ipm_status do_solve(ipm_ctx *c, cudaStream_t st) {
+// p_z, p_s (Prop. 2.1) and the bound-dual steps.  With defer_py the
+// transposed solve for p_y runs on the side stream (join_py before y is
+// used).
+ipm_status do_solve(ipm_ctx *c, cudaStream_t st, bool defer_py = false) {
+  join_py(c, st);
   if (!c->have_fact) return fail(c, IPM_ERR_STATE, "solve before a successful factorization");
   const DevSym &S = c->ds;
   DevWork &D = c->dw;
@@ -847,8 +858,22 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st) {
   launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);
   launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
   launch_lincomb(NX, c->apos, 1.0, c->apos, 1.0, c->kpx, delta, c->vpos, st);
-  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
-  launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, c->py, -1.0, st);
+  if (defer_py) {
+    if (!c->side) {
+      CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(c->ev_fork, st));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    launch_solve1(S, D.LU, D.rd, c->apos, 1, c->side);
+    launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, c->py, -1.0, c->side);
+    CK(cudaEventRecord(c->ev_join, c->side));
+    c->py_pending = true;
+  } else {
+    launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+    launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, c->py, -1.0, st);
+  }
   launch_pz_ps(S, D, c->px, c->pu, c->Hp, c->pz, c->ps, st);
   launch_bound_steps(NX, S.nx, D.x, c->px, S.xl, S.xu, D.zlx, D.zux, mu, c->dz[0], c->dz[1], st);
   launch_bound_steps(S.nu, S.nu, D.u, c->pu, S.ul, S.uu, D.zlu, D.zuu, mu, c->dz[2], c->dz[3], st);
@@ -939,8 +964,9 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
       if (delta > DELTA_MAX) return fail(c, IPM_ERR_NOT_PD, "inertia correction exceeded delta_max");
     }
   }
-  TRY(do_solve(c, st));
+  TRY(do_solve(c, st, true));
   if (c->mixed && !c->exact_iter && (c->neg_curv || !(c->refine_res <= 1e-10))) {
+    join_py(c, st);
     // CG met non-positive curvature or did not converge: redo in FP64
     c->exact_iter = true;
     ++c->n_fallback;
@@ -961,8 +987,14 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
         if (delta > DELTA_MAX) return fail(c, IPM_ERR_NOT_PD, "inertia correction exceeded delta_max");
       }
     }
-    TRY(do_solve(c, st));
+    TRY(do_solve(c, st, true));
   }
+  // every exit from here on waits for the p_y solve on the side stream
+  struct JoinPy {
+    ipm_ctx *c;
+    cudaStream_t st;
+    ~JoinPy() { join_py(c, st); }
+  } join_at_exit{c, st};
   ph_begin(c, PH_LS, st);
   const double tau = std::max(TAU_MIN, 1.0 - mu);
   launch_ftb(S, D, c->px, c->pu, c->ps, c->dz, tau, c->red_partial, c->red_out, st);
@@ -999,6 +1031,7 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
   CK(cudaMemcpyAsync(D.x, c->xt, NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(D.u, c->ut, S.nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(D.s, c->st, NM * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  join_py(c, st);
   launch_lincomb(NX, D.y, 1.0, D.y, alpha, c->py, 0.0, nullptr, st);
   launch_lincomb(NM, D.z, 1.0, D.z, alpha, c->pz, 0.0, nullptr, st);
   launch_dual_update(NX, S.nx, D.x, S.xl, S.xu, D.zlx, D.zux, c->dz[0], c->dz[1], az, mu, KAPPA_SIGMA, st);
@@ -1170,8 +1203,12 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
 
 ipm_status ipm_destroy(ipm_ctx *c) {
   if (!c) return IPM_ERR_ARG;
+  if (c->side) cudaStreamSynchronize(c->side);
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   for (void *p : c->allocs) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->h_flags) cudaFreeHost(c->h_flags);
