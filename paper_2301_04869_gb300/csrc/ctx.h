@@ -78,10 +78,12 @@ struct ipm_ctx {
   // phase timers
   bool prof = false;
   cudaEvent_t ev[2 * IPM_N_PHASES] = {};
-  // transposed solve for p_y on a side stream, joined before y is updated
-  // (it overlaps the line search, which does not need p_y)
-  cudaStream_t side = nullptr;
+  // side streams: the transposed solve for p_y (joined before y is
+  // updated; it overlaps the line search, which does not need p_y), and the
+  // reduced right-hand side beside the split (inside the captured graph)
+  cudaStream_t side = nullptr, side2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;  // reduced right-hand side beside the split
   bool py_pending = false;
   bool ev_pending[IPM_N_PHASES] = {};
   double t_ms[IPM_N_PHASES] = {0};

@@ -604,9 +604,43 @@ void join_py(ipm_ctx *c, cudaStream_t st) {
   c->py_pending = false;
 }
 
+// Reduced right-hand side, eq. (11), FP64 path: with b = G_x^{-1} r3 and
+// Z = -G_x^{-1} G_u,
+//   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
+// (b came with Z from the multi-RHS solve when the trailing block fits in
+// shared memory).  Needs only the solve's outputs, so it runs on the side
+// stream next to the split and the contraction.
+void reduced_rhs_fp64(ipm_ctx *c, cudaStream_t s2) {
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  ph_begin(c, PH_RRHS, s2);
+  if (!zsolve64_folds_b(S)) {
+    launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, s2);
+    launch_solve1(S, D.LU, D.rd, c->bpos, 0, s2);
+  }
+  launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, s2);
+  launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, s2);
+  launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, s2);
+  launch_lincomb(S.nu, c->rhs_u, -1.0, D.rh2, 0.0, nullptr, 0.0, nullptr, s2);
+  launch_zt_apply(S, c->Z, c->apos, D.K, c->bpos, -1.0, 1.0, c->rhs_u, c->cpos, s2);
+  ph_end(c, PH_RRHS, s2);
+}
+
 // Sigma, K, LU(G_x), Z, Y, K_hat (delta = 0), reduced right-hand side
+ipm_status ensure_side(ipm_ctx *c) {
+  if (c->side) return IPM_OK;
+  CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
+  return IPM_OK;
+}
+
 ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   join_py(c, st);
+  TRY(ensure_side(c));
   if (!c->have_eval) return fail(c, IPM_ERR_STATE, "condense before eval");
   const DevSym &S = c->ds;
   DevWork &D = c->dw;
@@ -631,6 +665,14 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     if (fp64) launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads, D.g, c->bpos);
     else launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
     ph_end(c, PH_ZSOLVE, st);
+    if (fp64) {
+      // the reduced right-hand side needs Z and b only: on the side stream,
+      // under the split and the contraction's set-up
+      cudaEventRecord(c->ev_fork2, st);
+      cudaStreamWaitEvent(c->side2, c->ev_fork2, 0);
+      reduced_rhs_fp64(c, c->side2);
+      cudaEventRecord(c->ev_join2, c->side2);
+    }
     ph_begin(c, PH_SPLIT, st);
     if (fp64 && c->emu) {
       // exact BF16 slices of the row-balanced Z and Y for the tensor cores
@@ -643,6 +685,7 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
       launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
     }
     ph_end(c, PH_SPLIT, st);
+    if (fp64) cudaStreamWaitEvent(st, c->ev_join2, 0);
   };
   auto post = [&] {
     if (fp64) {
@@ -650,20 +693,6 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
       else launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
                                 c->Khat, st);
       ph_end(c, PH_GEMM, st);
-      ph_begin(c, PH_RRHS, st);
-      // reduced RHS, eq. (11): with b = G_x^{-1} r3 and Z = -G_x^{-1} G_u,
-      //   rhs_u = -rhat2 - sum_i Z_i^T (rhat1_i - K_xx b_i) + K_ux b_i
-      // (b came with Z from the multi-RHS solve when the trailing block fits
-      // in shared memory)
-      if (!zsolve64_folds_b(S)) {
-        launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
-        launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
-      }
-      launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
-      launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
-      launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
-      launch_lincomb(S.nu, c->rhs_u, -1.0, D.rh2, 0.0, nullptr, 0.0, nullptr, st);
-      launch_zt_apply(S, c->Z, c->apos, D.K, c->bpos, -1.0, 1.0, c->rhs_u, c->cpos, st);
     } else {
       launch_tc_assemble(c->planZY, S.N, c->tcpart, c->Yu, c->diag1, c->Khat, st);
       ph_end(c, PH_GEMM, st);
@@ -676,8 +705,8 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
       launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
       launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
       launch_rhs_reduced(S, D.J, D.K, D.rh2, c->apos, c->bpos, c->rhs_u, st);
+      ph_end(c, PH_RRHS, st);
     }
-    ph_end(c, PH_RRHS, st);
   };
   if (c->opt.autotune && !c->tuned) {
     pre();  // direct launches: the tuned shapes must be fixed before a graph is captured
@@ -859,11 +888,7 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st, bool defer_py = false) {
   launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
   launch_lincomb(NX, c->apos, 1.0, c->apos, 1.0, c->kpx, delta, c->vpos, st);
   if (defer_py) {
-    if (!c->side) {
-      CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-      CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-      CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    }
+    TRY(ensure_side(c));
     CK(cudaEventRecord(c->ev_fork, st));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     launch_solve1(S, D.LU, D.rd, c->apos, 1, c->side);
@@ -1204,11 +1229,13 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
 ipm_status ipm_destroy(ipm_ctx *c) {
   if (!c) return IPM_ERR_ARG;
   if (c->side) cudaStreamSynchronize(c->side);
+  if (c->side2) cudaStreamSynchronize(c->side2);
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (cudaEvent_t e : {c->ev_fork, c->ev_join, c->ev_fork2, c->ev_join2})
+    if (e) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->side2) cudaStreamDestroy(c->side2);
   for (void *p : c->allocs) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->h_flags) cudaFreeHost(c->h_flags);
