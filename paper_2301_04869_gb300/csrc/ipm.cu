@@ -195,7 +195,7 @@ ipm_status alloc_work(ipm_ctx *c) {
       c->zplE = pz;
       c->yplE = py;
       TRY(dalloc(c, &c->expZ, ngr * nu));
-      TRY(dalloc(c, &c->emu_rs, krows));
+      TRY(dalloc(c, &c->emu_rs, 2 * krows));  // row exponent maxima of Z and Y
       TRY(dalloc(c, &c->expY, ngr * nu));
       const long long nt = ((nu + 127) / 128) * ((nu + 63) / 64);
       TRY(dalloc(c, &c->emu_tiles, nt));
@@ -662,7 +662,11 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
     ph_begin(c, PH_ZSOLVE, st);
     // FP64: b = G_x^{-1} g of eq. (11) rides along as an extra right-hand side
-    if (fp64) launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads, D.g, c->bpos);
+    if (fp64 && c->emu)
+      cudaMemsetAsync(c->emu_rs, 0, 2 * (size_t)S.N * S.nx * sizeof(int), st);  // row exponent maxima
+    if (fp64)
+      launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads, D.g, c->bpos,
+                      c->emu ? c->emu_rs : nullptr);
     else launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
     ph_end(c, PH_ZSOLVE, st);
     if (fp64) {
@@ -676,9 +680,9 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     ph_begin(c, PH_SPLIT, st);
     if (fp64 && c->emu) {
       // exact BF16 slices of the row-balanced Z and Y for the tensor cores
-      launch_emu_rowscale(c->emuZY, c->Z, c->Y, c->emu_rs, st);
-      launch_emu_split(c->emuZY, c->Z, false, c->emu_rs, st);
-      launch_emu_split(c->emuZY, c->Y, true, c->emu_rs, st);
+      // (row shifts from the row exponent maxima the solve left in emu_rs)
+      launch_emu_split(c->emuZY, c->Z, false, nullptr, st, c->emu_rs);
+      launch_emu_split(c->emuZY, c->Y, true, nullptr, st, c->emu_rs);
     } else if (!fp64) {
       // mixed: BF16x3 planes of the FP32 Z and Y
       launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);
@@ -1022,21 +1026,22 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
   } join_at_exit{c, st};
   ph_begin(c, PH_LS, st);
   const double tau = std::max(TAU_MIN, 1.0 - mu);
+  // fraction to the boundary, directional-derivative terms and the merit
+  // at the current point: three reductions, one read-back
   launch_ftb(S, D, c->px, c->pu, c->ps, c->dz, tau, c->red_partial, c->red_out, st);
-  TRY(read_red(c, 2, st));
+  launch_dir(S, D, c->px, c->pu, c->ps, c->kpx, c->kpu, c->Hp, mu, delta, c->red_partial, c->red_out + 2, st);
+  launch_merit(S, D.x, D.u, D.s, D.g, D.h, D.fs, c->red_partial, c->red_out + 5, st);
+  TRY(read_red(c, 8, st));
   const double amax = std::min(1.0, c->h_red[0]), az = std::min(1.0, c->h_red[1]);
-  launch_dir(S, D, c->px, c->pu, c->ps, c->kpx, c->kpu, c->Hp, mu, delta, c->red_partial, c->red_out, st);
-  TRY(read_red(c, 3, st));
-  const double gphi = c->h_red[0], q = c->h_red[1], c1 = c->h_red[2];
+  const double gphi = c->h_red[2], q = c->h_red[3], c1 = c->h_red[4];
+  const double merit0[3] = {c->h_red[5], c->h_red[6], c->h_red[7]};
   if (c1 > 0.0) {
     const double rt = (gphi + 0.5 * std::max(q, 0.0)) / ((1.0 - RHO_FRAC) * c1);
     if (c->rho < rt) c->rho = rt;
   }
   const double rho = c->rho;
   const double dphi = gphi - rho * c1;
-  launch_merit(S, D.x, D.u, D.s, D.g, D.h, D.fs, c->red_partial, c->red_out, st);
-  TRY(read_red(c, 3, st));
-  const double phi0 = (c->h_red[0] - mu * c->h_red[1]) + rho * c->h_red[2];
+  const double phi0 = (merit0[0] - mu * merit0[1]) + rho * merit0[2];
   double alpha = amax;
   int trials = 0;
   while (true) {

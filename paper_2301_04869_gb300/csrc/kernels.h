@@ -45,7 +45,7 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
 // state order), in an extra right-hand-side lane, when zsolve64_folds_b
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
                      double *Z, double *Y, double *Yu, cudaStream_t st, int threads = 256,
-                     const double *g = nullptr, double *b = nullptr);
+                     const double *g = nullptr, double *b = nullptr, int *ezy = nullptr);
 bool zsolve64_folds_b(const DevSym &S);
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
                      float *Z, float *Y, double *Yu, cudaStream_t st, int threads = 256);
@@ -163,7 +163,8 @@ size_t emu_partial_doubles(const EmuPlan &P, int max_groups);
 // power-of-two row balancing of Z, Y (rs: one int per contraction row)
 void launch_emu_rowscale(const EmuPlan &P, const double *Z, const double *Y, int *rs, cudaStream_t st);
 // split one operand (A: scaled by 2^rs, B: by 2^-rs; rs may be null)
-void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st);
+void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st,
+                      const int *ezy = nullptr);
 void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st);
 void launch_emu_assemble(const EmuPlan &P, int N, const double *partial, const double *Yu, const double *diag,
                          double *Khat, cudaStream_t st);

@@ -120,7 +120,8 @@ __device__ __forceinline__ uint32_t digit_bf16(int q) {
 
 __global__ void __launch_bounds__(256, 3) k_emu_split(long long krows, int nu, long long kpad,
                                                       const double *__restrict__ src, const int *__restrict__ rs,
-                                                      int rsign, __nv_bfloat16 *planes, int *exps) {
+                                                      int rsign, __nv_bfloat16 *planes, int *exps,
+                                                      const int *__restrict__ ezy) {
   extern __shared__ __align__(16) uint8_t split_smem[];
   double *tile = reinterpret_cast<double *>(split_smem);  // [GROUP][SPLIT_COLS]
   uint16_t *buf = reinterpret_cast<uint16_t *>(split_smem + (size_t)GROUP * SPLIT_COLS * sizeof(double));
@@ -143,9 +144,20 @@ __global__ void __launch_bounds__(256, 3) k_emu_split(long long krows, int nu, l
       *d = 0.0;
     }
   }
+  // row shifts: given, or from the rows' largest biased exponents of Z
+  // (ezy[k]) and Y (ezy[krows + k]) as k_emu_rowscale forms them
   for (int r = tid; r < GROUP; r += 256) {
     const long long k = rg + r;
-    shf[r] = (rs && k < krows) ? rsign * rs[k] : 0;
+    int sh = 0;
+    if (k < krows) {
+      if (rs) {
+        sh = rs[k];
+      } else if (ezy) {
+        const int ez = ezy[k], ey = ezy[krows + k];
+        sh = (ez > 0 && ey > 0) ? (ey - ez) / 2 : 0;
+      }
+    }
+    shf[r] = rsign * sh;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
@@ -508,14 +520,15 @@ void launch_emu_rowscale(const EmuPlan &P, const double *Z, const double *Y, int
   ipm_count_launch();
 }
 
-void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st) {
+void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st,
+                      const int *ezy) {
   static const bool cap = cudaFuncSetAttribute(emu::k_emu_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)emu::SPLIT_SMEM) == cudaSuccess;
   (void)cap;
   dim3 grid((unsigned)((P.nu + emu::SPLIT_COLS - 1) / emu::SPLIT_COLS), (unsigned)(P.kpad / emu::GROUP));
   emu::k_emu_split<<<grid, 256, emu::SPLIT_SMEM, st>>>(P.krows, P.nu, P.kpad, src, rs, b_side ? -1 : 1,
                                                  (__nv_bfloat16 *)(b_side ? P.b_planes : P.a_planes),
-                                                 b_side ? P.exp_b : P.exp_a);
+                                                 b_side ? P.exp_b : P.exp_a, ezy);
   ipm_count_launch();
 }
 

@@ -271,7 +271,7 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
 template <typename T>
 __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, const double *__restrict__ rd,
                             const double *__restrict__ J, const double *__restrict__ K, T *Z, T *Y, double *Yu,
-                            bool tail_smem, T *sh, const double *__restrict__ gvec, T *bvec) {
+                            bool tail_smem, T *sh, const double *__restrict__ gvec, T *bvec, int *ezy) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, bd = blockDim.x;
   const int nu = S.nu, nx = S.nx, N = S.N;
   // the CTA after the panels of Z (when bvec is given) solves b alone
@@ -443,6 +443,23 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
       else if (col - nx == cc) acc += v;
     }
     if (valid) Ys[(size_t)row * nu + c] = acc;
+    if (ezy) {
+      // largest biased exponents of the row of Z and of Y (the row balancing
+      // of the emulated contraction), over the panels by atomic maximum;
+      // ezy[k] for Z and ezy[N nx + k] for Y, k = sc nx + row
+      unsigned ez = 0, ey = 0;
+      if (valid) {
+        ez = (unsigned)(((unsigned long long)__double_as_longlong((double)Zs[(size_t)row * nu + c]) >> 52) & 0x7FF);
+        ey = (unsigned)(((unsigned long long)__double_as_longlong((double)acc) >> 52) & 0x7FF);
+      }
+      ez = __reduce_max_sync(0xffffffffu, ez);
+      ey = __reduce_max_sync(0xffffffffu, ey);
+      if (lane == 0) {
+        const size_t k = (size_t)sc * nx + row;
+        if (ez) atomicMax(&ezy[k], (int)ez);
+        if (ey) atomicMax(&ezy[(size_t)N * nx + k], (int)ey);
+      }
+    }
   }
   for (int j = warp; j < nu; j += nw) {
     double acc = 0.0;
@@ -463,9 +480,9 @@ __global__ void __launch_bounds__(256, 5) k_zsolve64(DevSym S, const double *__r
                                                   const double *__restrict__ J,
                                                   const double *__restrict__ K, double *Z, double *Y,
                                                   double *Yu, int tail_smem, const double *__restrict__ gvec,
-                                                  double *bvec) {
+                                                  double *bvec, int *ezy) {
   extern __shared__ double shd[];
-  zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd, gvec, bvec);
+  zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd, gvec, bvec, ezy);
 }
 
 __global__ void __launch_bounds__(256, 5) k_zsolve32(DevSym S, const double *__restrict__ LU,
@@ -474,7 +491,7 @@ __global__ void __launch_bounds__(256, 5) k_zsolve32(DevSym S, const double *__r
                                                   const double *__restrict__ K, float *Z, float *Y,
                                                   double *Yu, int tail_smem) {
   extern __shared__ float shf[];
-  zsolve_body<float>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shf, nullptr, (float *)nullptr);
+  zsolve_body<float>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shf, nullptr, (float *)nullptr, nullptr);
 }
 
 // In-place solve of G_x v = b (trans = 0) or G_x^T v = b (trans = 1) for every
@@ -823,7 +840,7 @@ bool zsolve64_folds_b(const DevSym &S) { return S.nd == 0 || zsolve_smem_ok(S, s
 
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J,
                      const double *K, double *Z, double *Y, double *Yu, cudaStream_t st, int threads,
-                     const double *g, double *b) {
+                     const double *g, double *b, int *ezy) {
   const int sm = zsolve_smem_ok(S, sizeof(double));
   if (!zsolve64_folds_b(S)) b = nullptr;
   dim3 grid((S.nu + 31) / 32 + (b ? 1 : 0), S.N);
@@ -831,7 +848,7 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
   // dynamic plus static shared memory may pass the 48 KB default
   static const bool cap = raise_smem_cap(k_zsolve64);
   (void)cap;
-  k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm, g, b); ipm_count_launch();
+  k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm, g, b, ezy); ipm_count_launch();
 }
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
                      const double *K, float *Z, float *Y, double *Yu, cudaStream_t st, int threads) {
