@@ -42,9 +42,9 @@ METRIC = "scenario condensations/s & s per IPM iter (mixed vs FP64 path, 1e-8 KK
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per launch from one ncu capture of the kernel as it stands (profiles/); None once the
 # kernel changes until it is captured again.
-TRAFFIC = {"k_gemm_tn64": 591.243264e6 + 26.54592e6,   # DRAM read + write, one launch, 1000 buses x 64
-           "k_zsolve64": None,  # changed since its last capture
-           "k_emu_schur": 1.13788e9 + 3.627776e6}
+TRAFFIC = {"k_gemm_tn64": 590.125568e6 + 25.997568e6,   # DRAM read + write, one launch, 1000 buses x 64
+           "k_zsolve64": 1.691865e9 + 865.253632e6,
+           "k_emu_schur": 1.137726e9 + 3.871488e6}
 UNIT = "scenario condensations/s"
 
 
@@ -137,12 +137,14 @@ def roofline(phases, dims, peaks, peak_kind, precision):
                 "traffic": TRAFFIC.get("k_gemm_tn64"),
                 "algorithmic": f"{kflops:.4g} flop/launch"}
     if name == "zsolve":
-        flops = 2.0 * dims.nnz_lu * nu * N
+        # the solves with n_u + 1 dense right-hand sides (the columns of G_u and g); the
+        # products Y = K [Z; I] come on top and are not counted
+        flops = 2.0 * dims.nnz_lu * (nu + 1) * N
         ach = flops / per_call_s / 1e12
-        return {"kernel": "k_zsolve64 (FP64 multi-RHS solves + SpMM)", "bound": "alu", "achieved": ach,
+        return {"kernel": "k_zsolve64 (FP64 multi-RHS solves + products with K)", "bound": "alu", "achieved": ach,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
                 "traffic": TRAFFIC.get("k_zsolve64"),
-                "algorithmic": f"{flops:.4g} flop/launch"}
+                "algorithmic": f"{flops:.4g} flop/launch (solves only)"}
     if name == "lu":
         return {"kernel": "k_lu_factor", "bound": "alu", "achieved": None, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": None, "traffic": None}
