@@ -104,7 +104,9 @@ typedef struct {
                             (n_x, n_u, N, precision) for the process */
   int poison;            /* 1: fill every device buffer with NaN when it is allocated (a check
                             that nothing is read before it is written; results must not change) */
-  int reserved[3];
+  int lu_pair;           /* 1 (default): factor G_x on a cluster of two CTAs per scenario when its
+                            dense trailing block fits their shared memory; 0: one CTA */
+  int reserved[2];
   double sigma;          /* centring factor of the adaptive rule (0.1) */
 } ipm_options;
 

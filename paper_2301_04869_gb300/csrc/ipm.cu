@@ -656,7 +656,7 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     ph_end(c, PH_COND, st);
     cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st);
     ph_begin(c, PH_LU, st);
-    launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st);
+    launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st, c->opt.lu_pair != 0);
     ph_end(c, PH_LU, st);
     // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
     launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
@@ -1133,7 +1133,7 @@ ipm_status do_warm_start(ipm_ctx *c, const float *pred, cudaStream_t st) {
   launch_functions(S, D.x, D.u, D.P, D.Q, D.g, D.h, D.fs, st);
   launch_derivatives(S, D, st);
   CK(cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st));
-  launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st);
+  launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st, c->opt.lu_pair != 0);
   launch_warm_yrhs(S, D, c->kpx, st);
   launch_gather_pos(S.N, S.nx, S.iperm, c->kpx, c->apos, 1.0, st);
   launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
@@ -1171,6 +1171,7 @@ ipm_status ipm_default_options(ipm_options *opt) {
   opt->solve_threads = 0;
   opt->graphs = 0;
   opt->autotune = 0;
+  opt->lu_pair = 1;
   opt->barrier_rule = IPM_BARRIER_ADAPTIVE;
   opt->sigma = 0.1;
   return IPM_OK;
@@ -1197,7 +1198,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
       c->opt.max_iter < 0 || c->opt.max_refine < 0 ||
       (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
       (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
-      (c->opt.poison != 0 && c->opt.poison != 1) ||
+      (c->opt.poison != 0 && c->opt.poison != 1) || (c->opt.lu_pair != 0 && c->opt.lu_pair != 1) ||
       (c->opt.barrier_rule == IPM_BARRIER_ADAPTIVE && !(c->opt.sigma > 0 && c->opt.sigma < 1))) {
     delete c;
     return IPM_ERR_ARG;

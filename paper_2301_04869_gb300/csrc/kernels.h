@@ -40,7 +40,7 @@ void launch_ugrad(const DevSym &S, DevWork &D, double *gLu, cudaStream_t st);
 
 // kernels_lu.cu
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
-                      cudaStream_t st);
+                      cudaStream_t st, bool allow_pair = true);
 // g, b (optional, [N][n_x]): also b = G_x^{-1} g in position order (g in
 // state order), in an extra right-hand-side lane, when zsolve64_folds_b
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,

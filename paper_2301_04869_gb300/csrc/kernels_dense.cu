@@ -267,9 +267,9 @@ __global__ void k_syrk_trail(int n, int k0, double *A) {
 // Per block column k0 (32 wide): (a) every CTA with panel rows loads L_kk and
 // solves its rows x L_kk^T = a (a warp per row, lane = column, shuffles; the
 // multipliers L_jt / L_tt are formed once per CTA so each step is one
-// shuffle and one multiply-add); (b) the lower 16 x 16 tiles of the trailing
-// matrix are updated, CTA 0 taking the three that make up the next
-// diagonal block and factoring it right away, the others round-robin over
+// shuffle and one multiply-add); (b) the trailing matrix is updated: CTA 0
+// forms the next diagonal block in one pass straight into shared memory and
+// factors it right away, the other lower 16 x 16 tiles go round-robin to
 // the remaining CTAs.
 constexpr int CT = 16;  // trailing-update tile
 
@@ -334,21 +334,45 @@ __global__ void __launch_bounds__(256) k_chol_coop(int n, double *A, int *flags)
     grid.sync();
     // (b) trailing update; tiles with bi, bj < 2 form the next diagonal block
     const int nt = (rest + CT - 1) / CT;
-    const int nd = nt >= 2 ? 3 : 1;
-    const int ntl = nt * (nt + 1) / 2 - nd;
+    const int ndt = nt >= 2 ? 3 : 1;
+    const int ntl = nt * (nt + 1) / 2 - ndt;
     if (bk == 0) {
-      for (int q = 0; q < nd; ++q) {
-        const int bi = q == 0 ? 0 : 1, bj = q == 2 ? 1 : 0;
-        syrk_tile16(n, k0, nb, r0 + bi * CT, r0 + bj * CT, A, a, b2);
-      }
       if (G == 1)
         for (int t = 0; t < ntl; ++t) {
           int bi = 2, rem = t;
           while (rem > bi) { rem -= bi + 1; ++bi; }
           syrk_tile16(n, k0, nb, r0 + bi * CT, r0 + rem * CT, A, a, b2);
         }
+      // the next diagonal block, A_dd - L_d L_d^T, straight into shared
+      // memory (one pass over its lower part), then factored and stored
+      const int nb2 = min(CB, rest);
       __syncthreads();
-      potrf_tile(n, r0, A, flags, a, &rs_sh);
+      for (int e = tid; e < CB * nb; e += blockDim.x) {
+        const int rr = e / nb, t = e % nb;
+        b2[rr][t] = rr < nb2 ? A[(size_t)(r0 + rr) * n + k0 + t] : 0.0;
+      }
+      __syncthreads();
+      for (int e = tid; e < nb2 * nb2; e += blockDim.x) {
+        const int i = e / nb2, j = e % nb2;
+        if (j > i) continue;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int t = 0;
+        for (; t + 4 <= nb; t += 4) {
+          s0 = fma(b2[i][t], b2[j][t], s0);
+          s1 = fma(b2[i][t + 1], b2[j][t + 1], s1);
+          s2 = fma(b2[i][t + 2], b2[j][t + 2], s2);
+          s3 = fma(b2[i][t + 3], b2[j][t + 3], s3);
+        }
+        for (; t < nb; ++t) s0 = fma(b2[i][t], b2[j][t], s0);
+        a[i][j] = A[(size_t)(r0 + i) * n + r0 + j] - ((s0 + s1) + (s2 + s3));
+      }
+      __syncthreads();
+      potrf_block(nb2, flags, a, &rs_sh);
+      for (int e = tid; e < nb2 * nb2; e += blockDim.x) {
+        const int i = e / nb2, j = e % nb2;
+        A[(size_t)(r0 + i) * n + r0 + j] = (j <= i) ? a[i][j] : 0.0;
+      }
+      __syncthreads();
     } else {
       for (int t = bk - 1; t < ntl; t += G - 1) {
         // t-th lower tile in rows bi >= 2: row bi holds bi + 1 tiles

@@ -797,7 +797,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
 }  // namespace
 
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool allow_pair) {
   // trailing sub-block held in shared memory: as large as fits next to the
   // kernel's static shared memory (170 x 170 doubles on GB300)
   static const int ns_max = [] {
@@ -822,7 +822,7 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
   }();
   const int np = (S.nd + 15) / 16, ldl = ((np + 1) / 2) * 16;
   const size_t pair_smem = (size_t)S.nd * (ldl + 16) * sizeof(double);
-  if (S.nd > 0 && pair_smem <= pair_cap) {
+  if (allow_pair && S.nd > 0 && pair_smem <= pair_cap) {
     k_lu_factor_pair<<<2 * S.N, 512, pair_smem, st>>>(S, nL, J, LU, rd, flags, 1e-14);
     ipm_count_launch();
     return;

@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("solve_threads", ctypes.c_int), ("barrier_rule", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3),
+                ("lu_pair", ctypes.c_int), ("reserved", ctypes.c_int * 2),
                 ("sigma", ctypes.c_double)]
 
 
@@ -161,7 +161,7 @@ def _cnet(net):
 
 
 def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, barrier_rule=None, sigma=None,
-                 graphs=False, autotune=False, solve_threads=0, poison=False):
+                 graphs=False, autotune=False, solve_threads=0, poison=False, lu_pair=True):
     lib = load()
     opt = Options()
     lib.ipm_default_options(ctypes.byref(opt))
@@ -177,6 +177,7 @@ def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, bar
     opt.autotune = int(bool(autotune))
     opt.solve_threads = int(solve_threads)
     opt.poison = int(bool(poison))
+    opt.lu_pair = int(bool(lu_pair))
     return opt
 
 
@@ -184,13 +185,14 @@ class Solver:
     """One context: a network with N load scenarios on the current GPU."""
 
     def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
-                 barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0, poison=False):
+                 barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0, poison=False,
+                 lu_pair=True):
         lib = load()
         self._lib = lib
         self._keep, cnet = _cnet(net)
         opt = make_options(precision=precision, tol=tol, max_iter=max_iter, max_refine=max_refine,
                            barrier_rule=barrier_rule, sigma=sigma, graphs=graphs, autotune=autotune,
-                           solve_threads=solve_threads, poison=poison)
+                           solve_threads=solve_threads, poison=poison, lu_pair=lu_pair)
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]
