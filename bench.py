@@ -137,14 +137,16 @@ def roofline(phases, dims, peaks, peak_kind, precision):
                 "traffic": TRAFFIC.get("k_gemm_tn64"),
                 "algorithmic": f"{kflops:.4g} flop/launch"}
     if name == "zsolve":
-        # the solves with n_u + 1 dense right-hand sides (the columns of G_u and g); the
-        # products Y = K [Z; I] come on top and are not counted
-        flops = 2.0 * dims.nnz_lu * (nu + 1) * N
+        # the solves with n_u + 1 dense right-hand sides (the columns of G_u and g) and the
+        # products Y = K_x [Z; I], Y_u = K_u [Z; I]
+        solve = 2.0 * dims.nnz_lu * (nu + 1) * N
+        prod = 2.0 * (dims.nnz_kx + dims.nnz_ku) * nu * N
+        flops = solve + prod
         ach = flops / per_call_s / 1e12
         return {"kernel": "k_zsolve64 (FP64 multi-RHS solves + products with K)", "bound": "alu", "achieved": ach,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
                 "traffic": TRAFFIC.get("k_zsolve64"),
-                "algorithmic": f"{flops:.4g} flop/launch (solves only)"}
+                "algorithmic": f"{flops:.4g} flop/launch ({solve:.4g} solves + {prod:.4g} products with K)"}
     if name == "lu":
         return {"kernel": "k_lu_factor", "bound": "alu", "achieved": None, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": None, "traffic": None}

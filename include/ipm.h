@@ -122,6 +122,8 @@ typedef struct {
   long long state_len, step_len;
   long long nnz_lu;      /* stored entries of the static-pivot LU of G_x */
   int lu_levels;         /* level-schedule depth of the LU / triangular solves */
+  int nnz_kx, nnz_ku;    /* entries of the rows of [K_xx K_xu] and [K_ux] per scenario (the
+                            products Y = K_x [Z; I], Y_u = K_u [Z; I]) */
 } ipm_dims;
 
 ipm_status ipm_default_options(ipm_options *opt);

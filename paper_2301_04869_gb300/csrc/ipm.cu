@@ -1261,6 +1261,8 @@ ipm_status ipm_get_dims(const ipm_ctx *c, ipm_dims *o) {
   o->state_len = c->state_len; o->step_len = c->step_len;
   o->nnz_lu = c->S.nnzLU;
   o->lu_levels = c->S.nlev;
+  o->nnz_kx = (int)c->S.kx_col.size();
+  o->nnz_ku = (int)c->S.ku_col.size();
   return IPM_OK;
 }
 

@@ -59,7 +59,8 @@ class Dims(ctypes.Structure):
     _fields_ = [("n_bus", ctypes.c_int), ("n_line", ctypes.c_int), ("n_gen", ctypes.c_int),
                 ("n_scen", ctypes.c_int), ("n_x", ctypes.c_int), ("n_u", ctypes.c_int), ("m", ctypes.c_int),
                 ("state_len", ctypes.c_longlong), ("step_len", ctypes.c_longlong),
-                ("nnz_lu", ctypes.c_longlong), ("lu_levels", ctypes.c_int)]
+                ("nnz_lu", ctypes.c_longlong), ("lu_levels", ctypes.c_int),
+                ("nnz_kx", ctypes.c_int), ("nnz_ku", ctypes.c_int)]
 
 
 _lib = None

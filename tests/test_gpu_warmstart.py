@@ -136,7 +136,7 @@ def test_learned_warm_start_cuts_iterations(gpu):
     print(f"cold {cold['iters'].mean():.2f} warm {warm['iters'].mean():.2f} iterations, "
           f"fallbacks {int(warm['fallback'].sum())}")
     assert warm["iters"].mean() <= 0.8 * cold["iters"].mean(), gain
-    # the FP64 oracle judges converged warm-started points
+    # the FP64 oracle checks converged warm-started points
     for j in (0, 17, 63):
         M = opf.Model(net, pd[j:j + 1], qd[j:j + 1])
         st = pool.ctx[0].split_state(warm["states"][j])
