@@ -681,8 +681,7 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     if (fp64 && c->emu) {
       // exact BF16 slices of the row-balanced Z and Y for the tensor cores
       // (row shifts from the row exponent maxima the solve left in emu_rs)
-      launch_emu_split(c->emuZY, c->Z, false, nullptr, st, c->emu_rs);
-      launch_emu_split(c->emuZY, c->Y, true, nullptr, st, c->emu_rs);
+      launch_emu_split_pair(c->emuZY, c->Z, c->Y, nullptr, st, c->emu_rs);
     } else if (!fp64) {
       // mixed: BF16x3 planes of the FP32 Z and Y
       launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);

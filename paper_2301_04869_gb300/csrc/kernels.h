@@ -165,6 +165,9 @@ void launch_emu_rowscale(const EmuPlan &P, const double *Z, const double *Y, int
 // split one operand (A: scaled by 2^rs, B: by 2^-rs; rs may be null)
 void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st,
                       const int *ezy = nullptr);
+// both operands of K = Z^T Y in one launch (Z: A side, Y: B side)
+void launch_emu_split_pair(const EmuPlan &P, const double *Z, const double *Y, const int *rs, cudaStream_t st,
+                           const int *ezy = nullptr);
 void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st);
 void launch_emu_assemble(const EmuPlan &P, int N, const double *partial, const double *Yu, const double *diag,
                          double *Khat, cudaStream_t st);

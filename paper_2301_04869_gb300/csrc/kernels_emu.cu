@@ -118,10 +118,21 @@ __device__ __forceinline__ uint32_t digit_bf16(int q) {
   return __float_as_uint(__int_as_float(0x4B400000 + q) - 12582912.0f) >> 16;
 }
 
-__global__ void __launch_bounds__(256, 3) k_emu_split(long long krows, int nu, long long kpad,
-                                                      const double *__restrict__ src, const int *__restrict__ rs,
-                                                      int rsign, __nv_bfloat16 *planes, int *exps,
+// One or two operands per launch (blockIdx.z selects src[z], planes[z],
+// exps[z]; the second is the B side, its rows scaled by 2^-rs).
+struct SplitOps {
+  const double *src[2];
+  __nv_bfloat16 *planes[2];
+  int *exps[2];
+};
+
+__global__ void __launch_bounds__(256, 3) k_emu_split(long long krows, int nu, long long kpad, SplitOps ops,
+                                                      const int *__restrict__ rs, int rsign0,
                                                       const int *__restrict__ ezy) {
+  const double *__restrict__ src = ops.src[blockIdx.z];
+  __nv_bfloat16 *planes = ops.planes[blockIdx.z];
+  int *exps = ops.exps[blockIdx.z];
+  const int rsign = blockIdx.z == 0 ? rsign0 : -1;
   extern __shared__ __align__(16) uint8_t split_smem[];
   double *tile = reinterpret_cast<double *>(split_smem);  // [GROUP][SPLIT_COLS]
   uint16_t *buf = reinterpret_cast<uint16_t *>(split_smem + (size_t)GROUP * SPLIT_COLS * sizeof(double));
@@ -520,16 +531,36 @@ void launch_emu_rowscale(const EmuPlan &P, const double *Z, const double *Y, int
   ipm_count_launch();
 }
 
-void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st,
-                      const int *ezy) {
+static void split_launch(const EmuPlan &P, emu::SplitOps ops, int nz, int rsign0, const int *rs, const int *ezy,
+                         cudaStream_t st) {
   static const bool cap = cudaFuncSetAttribute(emu::k_emu_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)emu::SPLIT_SMEM) == cudaSuccess;
   (void)cap;
-  dim3 grid((unsigned)((P.nu + emu::SPLIT_COLS - 1) / emu::SPLIT_COLS), (unsigned)(P.kpad / emu::GROUP));
-  emu::k_emu_split<<<grid, 256, emu::SPLIT_SMEM, st>>>(P.krows, P.nu, P.kpad, src, rs, b_side ? -1 : 1,
-                                                 (__nv_bfloat16 *)(b_side ? P.b_planes : P.a_planes),
-                                                 b_side ? P.exp_b : P.exp_a, ezy);
+  dim3 grid((unsigned)((P.nu + emu::SPLIT_COLS - 1) / emu::SPLIT_COLS), (unsigned)(P.kpad / emu::GROUP),
+            (unsigned)nz);
+  emu::k_emu_split<<<grid, 256, emu::SPLIT_SMEM, st>>>(P.krows, P.nu, P.kpad, ops, rs, rsign0, ezy);
   ipm_count_launch();
+}
+
+void launch_emu_split(const EmuPlan &P, const double *src, bool b_side, const int *rs, cudaStream_t st,
+                      const int *ezy) {
+  emu::SplitOps ops{};
+  ops.src[0] = src;
+  ops.planes[0] = (__nv_bfloat16 *)(b_side ? P.b_planes : P.a_planes);
+  ops.exps[0] = b_side ? P.exp_b : P.exp_a;
+  split_launch(P, ops, 1, b_side ? -1 : 1, rs, ezy, st);
+}
+
+void launch_emu_split_pair(const EmuPlan &P, const double *Z, const double *Y, const int *rs, cudaStream_t st,
+                           const int *ezy) {
+  emu::SplitOps ops{};
+  ops.src[0] = Z;
+  ops.src[1] = Y;
+  ops.planes[0] = (__nv_bfloat16 *)P.a_planes;
+  ops.planes[1] = (__nv_bfloat16 *)P.b_planes;
+  ops.exps[0] = P.exp_a;
+  ops.exps[1] = P.exp_b;
+  split_launch(P, ops, 2, 1, rs, ezy, st);
 }
 
 void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st) {
@@ -594,8 +625,7 @@ extern "C" ipm_status ipm_schur_sum_tc(const double *Z, const double *Y, int n_s
   }
   cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st);
   launch_emu_rowscale(P, Z, Y, rsd, st);
-  launch_emu_split(P, Z, false, rsd, st);
-  launch_emu_split(P, Y, true, rsd, st);
+  launch_emu_split_pair(P, Z, Y, rsd, st);
   launch_emu_schur(P, (double *)part, flags, st);
   launch_emu_assemble(P, n_scen, (const double *)part, nullptr, nullptr, Khat, st);
   if (cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
