@@ -215,6 +215,33 @@ ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
  * a replayed CUDA graph counts its kernel nodes). */
 long long ipm_kernel_launches(void);
 
+/* Host-side symbolic analysis only (no GPU, no context): one of the integer
+ * structures the kernels are driven by, for checks of the host logic (the
+ * static-pivot LU pattern and the schedules built from it).
+ *   IPM_SYM_DIMS: n_x, n_u, t0 (first position of the dense trailing block),
+ *     nd, nnz(L+U), number of solve panels, number of trailing-block product
+ *     lists;
+ *   IPM_SYM_LU_COLPTR, IPM_SYM_LU_ROW: CSC pattern of L+U by elimination
+ *     position (a slot is an index into lu_row);
+ *   IPM_SYM_FR_PTR, _FR_COL, _FR_LSLOT: L by rows (columns k < i, their slots);
+ *   IPM_SYM_GU_PTR, _GU_COL: G_u by rows (positions), u columns;
+ *   IPM_SYM_ZP_*: the per-panel forward schedules of the multi-RHS solve
+ *     (level offsets per panel, level pointers, rows, product pointers,
+ *     product columns and slots, zero-row pointers and rows, trailing-row
+ *     product pointers, columns and slots);
+ *   IPM_SYM_TW_*: the products of the sparse pivots into the trailing block
+ *     (list lengths; L slot, U slot and flushed entry slot or -1 per product,
+ *     product q of list t at q * lists + t).
+ * Writes min(cap, size) values to out (out may be NULL) and the size to *len.
+ * Errors: IPM_ERR_ARG for an invalid network or structure id. */
+enum {
+  IPM_SYM_DIMS = 0, IPM_SYM_LU_COLPTR, IPM_SYM_LU_ROW, IPM_SYM_FR_PTR, IPM_SYM_FR_COL, IPM_SYM_FR_LSLOT,
+  IPM_SYM_GU_PTR, IPM_SYM_GU_COL, IPM_SYM_ZP_LEV_OFF, IPM_SYM_ZP_LEV_PTR, IPM_SYM_ZP_ROWS, IPM_SYM_ZP_EPTR,
+  IPM_SYM_ZP_COL, IPM_SYM_ZP_SLOT, IPM_SYM_ZP_ZPTR, IPM_SYM_ZP_ZROWS, IPM_SYM_ZP_TPTR, IPM_SYM_ZP_TCOL,
+  IPM_SYM_ZP_TSLOT, IPM_SYM_TW_LEN, IPM_SYM_TW_L, IPM_SYM_TW_U, IPM_SYM_TW_E, IPM_SYM_COUNT
+};
+ipm_status ipm_symbolic_export(const ipm_network *net, int which, int *out, long long cap, long long *len);
+
 /* Replace the scenario loads of a context (same network and N) and reset the
  * cold-start state.  pd, qd: host [n_scen][n_bus].  Reuses every symbolic
  * structure and device workspace (no allocation).  Errors: IPM_ERR_ARG on

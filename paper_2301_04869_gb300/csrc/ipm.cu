@@ -1158,6 +1158,16 @@ bool finite_nonneg(const double *p, size_t n) {
 }  // namespace
 
 // ===========================================================================
+void host_net(const ipm_network *net, HostNet &h) {
+  h.n = net->n_bus; h.L = net->n_line; h.ng = net->n_gen;
+  h.fr.assign(net->from, net->from + h.L); h.to.assign(net->to, net->to + h.L);
+  h.gen.assign(net->gen_bus, net->gen_bus + h.ng);
+  h.r.assign(net->r, net->r + h.L); h.x.assign(net->x, net->x + h.L); h.b.assign(net->b, net->b + h.L);
+  h.pmax.assign(net->pmax, net->pmax + h.ng); h.qmax.assign(net->qmax, net->qmax + h.ng);
+  h.c2.assign(net->c2, net->c2 + h.ng); h.c1.assign(net->c1, net->c1 + h.ng);
+  h.vmin.assign(net->vmin, net->vmin + h.n); h.vmax.assign(net->vmax, net->vmax + h.n);
+}
+
 extern "C" {
 
 ipm_status ipm_default_options(ipm_options *opt) {
@@ -1203,13 +1213,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
     return IPM_ERR_ARG;
   }
   HostNet h;
-  h.n = net->n_bus; h.L = net->n_line; h.ng = net->n_gen;
-  h.fr.assign(net->from, net->from + h.L); h.to.assign(net->to, net->to + h.L);
-  h.gen.assign(net->gen_bus, net->gen_bus + h.ng);
-  h.r.assign(net->r, net->r + h.L); h.x.assign(net->x, net->x + h.L); h.b.assign(net->b, net->b + h.L);
-  h.pmax.assign(net->pmax, net->pmax + h.ng); h.qmax.assign(net->qmax, net->qmax + h.ng);
-  h.c2.assign(net->c2, net->c2 + h.ng); h.c1.assign(net->c1, net->c1 + h.ng);
-  h.vmin.assign(net->vmin, net->vmin + h.n); h.vmax.assign(net->vmax, net->vmax + h.n);
+  host_net(net, h);
   bool ok = true;
   for (int k = 0; k < h.ng; ++k)
     if (!(h.pmax[k] > 0) || !(h.qmax[k] >= 0) || !std::isfinite(h.c2[k]) || !std::isfinite(h.c1[k])) ok = false;
@@ -1551,6 +1555,50 @@ ipm_status ipm_warm_start(ipm_ctx *c, const float *pred, void *stream) {
 }
 
 long long ipm_kernel_launches(void) { return g_ipm_launches.load(); }
+
+ipm_status ipm_symbolic_export(const ipm_network *net, int which, int *out, long long cap, long long *len) {
+  if (!net || !len || which < 0 || which >= IPM_SYM_COUNT || cap < 0 || net->n_bus < 2 || net->n_line < 1 ||
+      net->n_gen < 1 || !net->from || !net->to || !net->gen_bus || !net->r || !net->x || !net->b ||
+      !net->pmax || !net->qmax || !net->c2 || !net->c1 || !net->vmin || !net->vmax)
+    return IPM_ERR_ARG;
+  HostNet h;
+  host_net(net, h);
+  Sym S;
+  std::string err;
+  if (!build_symbolic(h, 1, S, err)) return IPM_ERR_ARG;
+  std::vector<int> v;
+  const std::vector<int> *src = &v;
+  switch (which) {
+    case IPM_SYM_DIMS: v = {S.nx, S.nu, S.t0, S.nd, S.nnzLU, S.zp_npan, LU_LISTS}; break;
+    case IPM_SYM_LU_COLPTR: src = &S.lu_colptr; break;
+    case IPM_SYM_LU_ROW: src = &S.lu_row; break;
+    case IPM_SYM_FR_PTR: src = &S.fr_ptr; break;
+    case IPM_SYM_FR_COL: src = &S.fr_col; break;
+    case IPM_SYM_FR_LSLOT: src = &S.fr_lslot; break;
+    case IPM_SYM_GU_PTR: src = &S.gu_ptr; break;
+    case IPM_SYM_GU_COL: src = &S.gu_col; break;
+    case IPM_SYM_ZP_LEV_OFF: src = &S.zp_lev_off; break;
+    case IPM_SYM_ZP_LEV_PTR: src = &S.zp_lev_ptr; break;
+    case IPM_SYM_ZP_ROWS: src = &S.zp_rows; break;
+    case IPM_SYM_ZP_EPTR: src = &S.zp_eptr; break;
+    case IPM_SYM_ZP_COL: src = &S.zp_col; break;
+    case IPM_SYM_ZP_SLOT: src = &S.zp_slot; break;
+    case IPM_SYM_ZP_ZPTR: src = &S.zp_zptr; break;
+    case IPM_SYM_ZP_ZROWS: src = &S.zp_zrows; break;
+    case IPM_SYM_ZP_TPTR: src = &S.zp_tptr; break;
+    case IPM_SYM_ZP_TCOL: src = &S.zp_tcol; break;
+    case IPM_SYM_ZP_TSLOT: src = &S.zp_tslot; break;
+    case IPM_SYM_TW_LEN: src = &S.tw_len; break;
+    case IPM_SYM_TW_L: src = &S.tw_l; break;
+    case IPM_SYM_TW_U: src = &S.tw_u; break;
+    case IPM_SYM_TW_E: src = &S.tw_e; break;
+    default: return IPM_ERR_ARG;
+  }
+  *len = (long long)src->size();
+  if (out)
+    for (long long i = 0; i < std::min(cap, *len); ++i) out[i] = (*src)[(size_t)i];
+  return IPM_OK;
+}
 
 ipm_status ipm_set_profiling(ipm_ctx *c, int on) {
   if (!c) return IPM_ERR_ARG;

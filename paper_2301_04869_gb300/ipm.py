@@ -108,6 +108,8 @@ def load():
         "ipm_warm_target": (c_int, [vp, vp, vp]),
         "ipm_warm_start": (c_int, [vp, vp, vp]),
         "ipm_kernel_launches": (c_ll, []),
+        "ipm_symbolic_export": (c_int, [ctypes.POINTER(Network), c_int, ctypes.POINTER(ctypes.c_int), c_ll,
+                                        ctypes.POINTER(c_ll)]),
         "ipm_batch_default_options": (c_int, [ctypes.POINTER(BatchOptions)]),
         "ipm_solve_batch": (c_int, [ctypes.POINTER(vp), c_int, ctypes.POINTER(vp), ctypes.POINTER(BatchOptions),
                                     _I, _D, _I, _D]),
@@ -126,6 +128,30 @@ def load():
 def kernel_launches():
     """Kernels libipm.so has launched in this process (all contexts)."""
     return int(load().ipm_kernel_launches())
+
+
+SYM_NAMES = ["dims", "lu_colptr", "lu_row", "fr_ptr", "fr_col", "fr_lslot", "gu_ptr", "gu_col", "zp_lev_off",
+             "zp_lev_ptr", "zp_rows", "zp_eptr", "zp_col", "zp_slot", "zp_zptr", "zp_zrows", "zp_tptr", "zp_tcol",
+             "zp_tslot", "tw_len", "tw_l", "tw_u", "tw_e"]
+
+
+def symbolic_export(net, name):
+    """One integer structure of the host-side symbolic analysis of `net`
+    (ipm_symbolic_export; no GPU needed) as an int32 array."""
+    lib = load()
+    keep, cnet = _cnet(net)
+    which = SYM_NAMES.index(name)
+    n = ctypes.c_longlong(0)
+    st = lib.ipm_symbolic_export(ctypes.byref(cnet), which, None, 0, ctypes.byref(n))
+    if st != IPM_OK:
+        raise IPMError(st, "ipm_symbolic_export failed")
+    out = np.empty(n.value, dtype=np.int32)
+    st = lib.ipm_symbolic_export(ctypes.byref(cnet), which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 out.size, ctypes.byref(n))
+    if st != IPM_OK:
+        raise IPMError(st, "ipm_symbolic_export failed")
+    del keep
+    return out
 
 
 def _ptr(a, ct):
