@@ -42,6 +42,35 @@ def test_default_options(lib):
     o = ipm.Options()
     assert lib.ipm_default_options(ctypes.byref(o)) == 0
     assert o.tol == 1e-8 and o.max_iter == 200 and o.precision == ipm.PREC_FP64
+    assert o.lu_pair == 1 and o.graphs == 0 and o.autotune == 0 and o.poison == 0
+
+
+@pytest.mark.parametrize("field,value", [("precision", 3), ("solve_threads", 64), ("graphs", 2), ("autotune", -1),
+                                         ("poison", 2), ("lu_pair", 2), ("tol", 0.0), ("max_iter", -1)])
+def test_rejects_bad_options(lib, field, value):
+    """Invalid options are rejected before the device is touched."""
+    net = synth.make_network(30, 6, seed=0)
+    pd, qd = synth.make_scenarios(net, 2, 0.05, seed=1)
+    o = ipm.Options()
+    lib.ipm_default_options(ctypes.byref(o))
+    setattr(o, field, value)
+    keep, cnet = ipm._cnet(net)
+    h = ctypes.c_void_p()
+    pd = np.ascontiguousarray(pd)
+    qd = np.ascontiguousarray(qd)
+    st = lib.ipm_create(ctypes.byref(cnet), pd.shape[0], pd.ctypes.data_as(ipm._D), qd.ctypes.data_as(ipm._D),
+                        ctypes.byref(o), ctypes.byref(h))
+    assert st == 1 and not h.value  # IPM_ERR_ARG
+
+
+def test_symbolic_export_rejects_bad_ids(lib):
+    net = synth.make_network(30, 6, seed=0)
+    keep, cnet = ipm._cnet(net)
+    n = ctypes.c_longlong(0)
+    assert lib.ipm_symbolic_export(ctypes.byref(cnet), -1, None, 0, ctypes.byref(n)) == 1
+    assert lib.ipm_symbolic_export(ctypes.byref(cnet), len(ipm.SYM_NAMES), None, 0, ctypes.byref(n)) == 1
+    assert lib.ipm_symbolic_export(None, 0, None, 0, ctypes.byref(n)) == 1
+    assert lib.ipm_symbolic_export(ctypes.byref(cnet), 0, None, 0, ctypes.byref(n)) == 0 and n.value == 7
 
 
 def _create(lib, net, pd, qd):
