@@ -25,6 +25,7 @@ struct DevSym {
   const int *fw_lev_ptr, *fw_rows, *fr_ptr, *fr_col, *fr_lslot, *fr_uslot;
   const int *bw_lev_ptr, *bw_rows, *br_ptr, *br_col, *br_uslot, *br_lslot;
   const int *fs_lev_ptr, *fs_rows, *bs_lev_ptr, *bs_rows;
+  const int4 *fs4, *bs4, *fr4, *br4;  // packed single-RHS sweeps (symbolic.cpp)
   const int *gu_ptr, *gu_col, *gu_src, *gut_ptr, *gut_col, *gut_src;
   const int *kx_ptr, *kx_col, *kx_src, *ku_ptr, *ku_col, *ku_src;
   int zp_npan;  // forward schedules per 32-column panel of Z (symbolic.cpp)

@@ -116,6 +116,13 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   TRY(upload(c, &d.lu_diag, S.lu_diag)); TRY(upload(c, &d.lu_init, S.lu_init));
   TRY(upload(c, &d.tail_slot, S.tail_slot));
   TRY(upload(c, &d.fs_lev_ptr, S.fs_lev_ptr)); TRY(upload(c, &d.fs_rows, S.fs_rows));
+  {
+    const int *q = nullptr;
+    TRY(upload(c, &q, S.fs4)); d.fs4 = reinterpret_cast<const int4 *>(q);
+    TRY(upload(c, &q, S.bs4)); d.bs4 = reinterpret_cast<const int4 *>(q);
+    TRY(upload(c, &q, S.fr4)); d.fr4 = reinterpret_cast<const int4 *>(q);
+    TRY(upload(c, &q, S.br4)); d.br4 = reinterpret_cast<const int4 *>(q);
+  }
   TRY(upload(c, &d.bs_lev_ptr, S.bs_lev_ptr)); TRY(upload(c, &d.bs_rows, S.bs_rows));
   TRY(upload(c, &d.f_lev_ptr, S.f_lev_ptr)); TRY(upload(c, &d.f_piv_ptr, S.f_piv_ptr)); TRY(upload(c, &d.f_piv, S.f_piv));
   TRY(upload(c, &d.f_tgt, S.f_tgt)); TRY(upload(c, &d.f_op_ptr, S.f_op_ptr)); TRY(upload(c, &d.f_op_l, S.f_op_l));

@@ -60,6 +60,10 @@ struct Sym {
   long long n_tail_ops = 0;
   std::vector<int> fw_lev_ptr, fw_rows, fr_ptr, fr_col, fr_lslot, fr_uslot;
   std::vector<int> bw_lev_ptr, bw_rows, br_ptr, br_col, br_uslot, br_lslot;
+  // packed single-RHS sweeps (4 ints each): per scheduled row {row, first, end, 0}
+  // (fs4: forward sparse rows, bs4: backward), per product {col, slot, transposed slot, 0}
+  // (fr4 over fr_*, br4 over br_*)
+  std::vector<int> fs4, bs4, fr4, br4;
   // sparse operators by position (x rows) or u rows
   std::vector<int> gu_ptr, gu_col, gu_src;
   std::vector<int> gut_ptr, gut_col, gut_src;

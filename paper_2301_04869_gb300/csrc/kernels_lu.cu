@@ -507,24 +507,27 @@ __device__ __forceinline__ double group_sum(double p) {
 }
 
 // One level of sparse rows, GS lanes per row: x[row] = (x[row] - sum_f
-// A[slot[f]] x[col[f]]) * (scale ? r[row] : 1) over f in [ptr[row],
-// ptr[row+1]) with col[f] < cend.  Rows of a level are independent; the
-// loop bounds are uniform over the CTA (shuffles).
+// A[slot_f] x[col_f]) * (scale ? r[row] : 1) over the row's products.  A
+// scheduled row is one 16-byte record {row, first, end} and a product one
+// {col, slot, transposed slot}, so each row costs three dependent loads
+// (record, product, value).  Rows of a level are independent; the loop
+// bounds are uniform over the CTA (shuffles).
 template <int GS>
-__device__ __forceinline__ void solve_level(const int *__restrict__ rows, int e0, int e1,
-                                            const int *__restrict__ ptr, const int *__restrict__ col,
-                                            const int *__restrict__ slot, int cend, const double *__restrict__ A,
-                                            const double *__restrict__ r, bool scale, double *x) {
+__device__ __forceinline__ void solve_level(const int4 *__restrict__ rows, int e0, int e1,
+                                            const int4 *__restrict__ prod, bool trans_slot,
+                                            const double *__restrict__ A, const double *__restrict__ r, bool scale,
+                                            double *x) {
   const int grp = threadIdx.x / GS, sub = threadIdx.x % GS, ngrp = blockDim.x / GS;
   for (int eb = e0; eb < e1; eb += ngrp) {
     const int e = eb + grp;
     double part = 0.0;
     int row = -1;
     if (e < e1) {
-      row = rows[e];
-      for (int f = ptr[row] + sub; f < ptr[row + 1]; f += GS) {
-        const int c = col[f];
-        if (c < cend) part = fma(A[slot[f]], x[c], part);
+      const int4 R = rows[e];
+      row = R.x;
+      for (int f = R.y + sub; f < R.z; f += GS) {
+        const int4 P = prod[f];
+        part = fma(A[trans_slot ? P.z : P.y], x[P.x], part);
       }
     }
     part = group_sum<GS>(part);
@@ -548,11 +551,9 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
     for (int i = tid; i < nx; i += bd) x[i] = vs[i];
     __syncthreads();
   }
-  const int *fsl = trans ? S.fr_uslot : S.fr_lslot;
-  const int *bsl = trans ? S.br_lslot : S.br_uslot;
   // forward sparse rows (few entries each): four lanes per row
   for (int l = 0; l < S.nlev_fs; ++l) {
-    solve_level<4>(S.fs_rows, S.fs_lev_ptr[l], S.fs_lev_ptr[l + 1], S.fr_ptr, S.fr_col, fsl, nx, A, r, trans != 0, x);
+    solve_level<4>(S.fs4, S.fs_lev_ptr[l], S.fs_lev_ptr[l + 1], S.fr4, trans != 0, A, r, trans != 0, x);
     __syncthreads();
   }
   if (nd > 0) {
@@ -567,8 +568,8 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
         if (i < nd) {
           const int row = t0 + i;
           for (int f = S.fr_ptr[row] + sub; f < S.fr_ptr[row + 1]; f += 8) {
-            const int c = S.fr_col[f];
-            if (c < t0) part = fma(A[fsl[f]], x[c], part);
+            const int4 P = S.fr4[f];
+            if (P.x < t0) part = fma(A[trans ? P.z : P.y], x[P.x], part);
           }
         }
         part = group_sum<8>(part);
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
   }
   // backward sparse rows: eight lanes per row
   for (int l = 0; l < S.nlev_bs; ++l) {
-    solve_level<8>(S.bs_rows, S.bs_lev_ptr[l], S.bs_lev_ptr[l + 1], S.br_ptr, S.br_col, bsl, nx, A, r, trans == 0, x);
+    solve_level<8>(S.bs4, S.bs_lev_ptr[l], S.bs_lev_ptr[l + 1], S.br4, trans != 0, A, r, trans == 0, x);
     __syncthreads();
   }
   if (in_smem)

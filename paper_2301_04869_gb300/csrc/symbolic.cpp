@@ -470,6 +470,10 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
       if (any) S.bs_lev_ptr.push_back((int)S.bs_rows.size());
     }
     S.nlev_bs = (int)S.bs_lev_ptr.size() - 1;
+    for (int i : S.fs_rows) S.fs4.insert(S.fs4.end(), {i, S.fr_ptr[i], S.fr_ptr[i + 1], 0});
+    for (int i : S.bs_rows) S.bs4.insert(S.bs4.end(), {i, S.br_ptr[i], S.br_ptr[i + 1], 0});
+    for (size_t f = 0; f < S.fr_col.size(); ++f) S.fr4.insert(S.fr4.end(), {S.fr_col[f], S.fr_lslot[f], S.fr_uslot[f], 0});
+    for (size_t f = 0; f < S.br_col.size(); ++f) S.br4.insert(S.br4.end(), {S.br_col[f], S.br_uslot[f], S.br_lslot[f], 0});
   }
   // ---- G_u (rows: positions) and its transpose (rows: u) ----
   const int nu = S.nu;
