@@ -215,6 +215,14 @@ ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
  * a replayed CUDA graph counts its kernel nodes). */
 long long ipm_kernel_launches(void);
 
+/* Self-test of the failure path of the bounded device waits: one thread
+ * waits on an mbarrier that nothing arrives at, gives up after `polls` polls
+ * (1 .. 2^22) and raises the timeout flag, exactly as the waits of the
+ * tensor-core kernels do (there with 2^22 polls).  Returns IPM_ERR_TIMEOUT
+ * when the wait gave up (the expected outcome) and leaves the device usable;
+ * IPM_ERR_ARG for a poll count out of range. */
+ipm_status ipm_selftest_bounded_wait(long long polls, void *stream);
+
 /* Host-side symbolic analysis only (no GPU, no context): one of the integer
  * structures the kernels are driven by, for checks of the host logic (the
  * static-pivot LU pattern and the schedules built from it).

@@ -588,6 +588,45 @@ size_t emu_partial_doubles(const EmuPlan &P, int max_groups) {
 }
 
 // ---------------------------------------------------------------------------
+// The failure path of the bounded device waits, exercised without a fault:
+// one thread waits on an mbarrier that nothing arrives at, gives up after
+// `polls` polls and raises FLAG_TIMEOUT, as every wait of the tcgen05 kernels
+// does (they use the same wait with a larger limit).
+namespace emu {
+__global__ void k_wait_selftest(long long polls, int *flags) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_limit(&bar, 0, polls)) flags[FLAG_TIMEOUT] = 1;
+}
+}  // namespace emu
+
+extern "C" ipm_status ipm_selftest_bounded_wait(long long polls, void *stream) {
+  if (polls < 1 || polls > (1LL << 22)) return IPM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *flags = nullptr;
+  int hf[FLAG_COUNT] = {0};
+  if (cudaMalloc(&flags, FLAG_COUNT * sizeof(int)) != cudaSuccess) return IPM_ERR_OOM;
+  ipm_status rc = IPM_OK;
+  if (cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st) != cudaSuccess) rc = IPM_ERR_CUDA;
+  if (rc == IPM_OK) {
+    emu::k_wait_selftest<<<1, 32, 0, st>>>(polls, flags);
+    ipm_count_launch();
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = IPM_ERR_CUDA;
+    else if (hf[FLAG_TIMEOUT])
+      rc = IPM_ERR_TIMEOUT;
+  }
+  cudaFree(flags);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
 // Stand-alone entry point (include/ipm.h): the emulated contraction on
 // caller-owned device matrices, for checking the kernel on arbitrary data.
 extern "C" ipm_status ipm_schur_sum_tc(const double *Z, const double *Y, int n_scen, int n_x, int n_u,

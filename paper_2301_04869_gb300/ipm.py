@@ -108,6 +108,7 @@ def load():
         "ipm_warm_target": (c_int, [vp, vp, vp]),
         "ipm_warm_start": (c_int, [vp, vp, vp]),
         "ipm_kernel_launches": (c_ll, []),
+        "ipm_selftest_bounded_wait": (c_int, [c_ll, vp]),
         "ipm_symbolic_export": (c_int, [ctypes.POINTER(Network), c_int, ctypes.POINTER(ctypes.c_int), c_ll,
                                         ctypes.POINTER(c_ll)]),
         "ipm_batch_default_options": (c_int, [ctypes.POINTER(BatchOptions)]),
@@ -123,6 +124,11 @@ def load():
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def selftest_bounded_wait(polls, stream=None):
+    """Status of ipm_selftest_bounded_wait (IPM_ERR_TIMEOUT expected)."""
+    return int(load().ipm_selftest_bounded_wait(int(polls), _stream(stream)))
 
 
 def kernel_launches():
