@@ -157,17 +157,23 @@ def roofline(phases, dims, peaks, peak_kind, precision):
             "frac": ach / peaks["hbm_gbs"], "traffic": None}
 
 
-def cpu_baseline(workload, n_sample=8, iters=2):
-    """The oracle, as it stands, on a bounded sample: `iters` IPM iterations
-    from the cold start on the first `n_sample` scenarios of the workload."""
+def cpu_baseline(workload, n_sample=8, min_s=10.0, max_iters=40):
+    """The oracle, as it stands, on a bounded sample: IPM iterations from the
+    cold start on the first `n_sample` scenarios of the workload, until about
+    `min_s` seconds of CPU work (at least 2, at most `max_iters` iterations;
+    a converged solve restarts from the cold start)."""
     from oracle import ipm as oipm
     from oracle import opf
     net, pd, qd = synth.workload(workload, n_scen=n_sample)
     M = opf.Model(net, pd, qd)
     st = oipm.initial_state(M)
+    iters = 0
     t0 = time.perf_counter()
-    for _ in range(iters):
-        oipm.iterate(M, st)
+    while iters < max_iters and (iters < 2 or time.perf_counter() - t0 < min_s):
+        conv, _ = oipm.iterate(M, st)
+        iters += 1
+        if conv:
+            st = oipm.initial_state(M)
     dt = time.perf_counter() - t0
     return {"value": n_sample * iters / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{iters} IPM iterations from the cold start on {n_sample} of the workload's scenarios "
