@@ -6,16 +6,18 @@
 // group of 512 contraction rows and every column j, an operand column is
 // scaled by a power of two 2^-e (e = ilogb(max |.|) + 2, so |x| 2^-e < 1/2),
 // rounded to a multiple of 2^-56 and written as eight 7-bit integer slices,
-//     x 2^-e = sum_{t=1..8} q_t 2^-7t + r,   q_t integer, |q_t| <= 64,
-//     |r| <= 2^-57,
+//     x 2^-e = sum_{t=1..8} q_t 2^-7t + r,   q_t integer, |q_t| <= 64
+//     (q_2..q_8 in [-64, 63]),  |r| <= 2^-57,
 // each exact in BF16.  A product of slices q_t q'_u is an integer of at most
 // 2^12; the pairs with t + u = L + 2 (L = 0..7, 36 pairs in all) accumulate
 // in their own FP32 TMEM accumulator ("level" L), whose partial sums over
 // 512 rows stay integers of at most 8 * 2^12 * 512 = 2^24 and are therefore
 // exact.  The dropped pairs and the remainders weigh about 2^-52 of the
 // product of the group's largest entries of the two columns, per row; rows
-// are balanced first (k_emu_rowscale) so that those largest entries belong
-// to the same rows as far as a power-of-two row scaling can arrange.  After
+// are balanced first (row shifts from the rows' largest exponents of Z and
+// Y: taken by the multi-RHS solve on the IPM path, by k_emu_rowscale on
+// caller data) so that those largest entries belong to the same rows as far
+// as a power-of-two row scaling can arrange.  After
 // each group the epilogue combines the eight levels into two exact 64-bit
 // integers (levels 0-5 and levels 6-7), converts their sum to FP64 (two
 // roundings) and accumulates it, scaled by 2^(e_A + e_B - 49), in FP64.

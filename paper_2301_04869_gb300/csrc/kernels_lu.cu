@@ -7,10 +7,14 @@
 // 1-2: T_x = -G_x^{-1} G_u V, [L_x; L_u] = K [T_x; V]).  Here V runs over
 // all Cartesian vectors at once, split into RHS panels of 32 columns.
 //
-// Scheduling: every CTA owns one scenario (LU, single-vector solves) or one
-// (scenario, RHS panel) pair (multi-RHS solves) and walks the level schedule
-// of the shared pattern with __syncthreads() between levels; no grid-wide
-// synchronisation and no inter-CTA waits.
+// Scheduling: the LU runs on a cluster of two CTAs per scenario (cluster
+// barriers between its steps; a one-CTA kernel when the trailing block does
+// not fit the pair's shared memory), the single-vector solves on one CTA per
+// scenario, the multi-RHS solves on one CTA per (scenario, RHS panel) pair
+// plus one per scenario for b; each walks a level schedule of the shared
+// pattern with __syncthreads() between levels.  No grid-wide
+// synchronisation and no waits between CTAs other than the cluster
+// barriers.
 #include <atomic>
 
 #include "dev.cuh"
