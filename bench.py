@@ -215,6 +215,13 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def fallback_count(sol):
+    """Iterations of a mixed-precision context that were condensed again in
+    FP64 so far (its IPM_Q_INFO fallback counter; 0 on the FP64 paths)."""
+    from paper_2301_04869_gb300 import ipm
+    return int(sol.ipm_get_quantity(ipm.Q_INFO)[10])
+
+
 def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush, want_e2e=True):
     """Time `steps` IPM iterations of one precision path (device events per step,
     L2 flushed between steps; graphs and autotuned launch shapes on), then the
@@ -235,6 +242,11 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
 
         for _ in range(warmup):
             step()
+        # checkpoint: the phase pass and the end-to-end pass restart from it,
+        # so all three passes time the same iterates
+        ck = torch.empty(dims.state_len, dtype=torch.float64, device="cuda")
+        sol.ipm_get_state(ck, stream=stream)
+        fb0 = fallback_count(sol)
         _, launches0 = sol.timers()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
@@ -256,12 +268,14 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
         if world > 1:
             torch.distributed.barrier()
         _, launches1 = sol.timers()
+        fallbacks = fallback_count(sol) - fb0
         tot_ms = sum(a.elapsed_time(b) for a, b in ev)
         if world > 1:
             t = torch.tensor([tot_ms], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             tot_ms = float(t.item())
         # phase breakdown (events between phases; graphs are off while profiling)
+        sol.ipm_set_state(ck, stream=stream)
         sol.ipm_set_profiling(2)
         for k in range(steps):
             flush.fill_(float(k))
@@ -275,9 +289,12 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
             # host memory, one IPM iteration, state out to host memory, every step
             host = torch.empty(dims.state_len, dtype=torch.float64, pin_memory=True)
             hnp = host.numpy()
+            # the same iterates as the device-timed pass: start from its checkpoint
+            sol.ipm_set_state(ck, stream=stream)
             sol.ipm_get_state(hnp, stream=stream)
+            torch.cuda.synchronize()
             e2e = []
-            for k in range(max(3, steps // 2)):
+            for k in range(steps):
                 flush.fill_(float(k))
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -297,6 +314,7 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
     cond = ("condense_K", "lu", "zsolve", "split", "gemm") + (("reduced_rhs",) if precision == "mixed" else ())
     cond_ms = sum(per[p] for p in cond)
     return dict(sol=sol, dims=dims, N=N, tot_ms=tot_ms, value=world * N * steps / (tot_ms / 1e3),
+                fallbacks=fallbacks,
                 ms_per_step=tot_ms / steps, phases=phases, phases_ms_per_step=per,
                 condense_only=N / (cond_ms / 1e3) if cond_ms > 0 else None,
                 launches=launches1 - launches0, clocks=clk.summary(), e2e=e2e_val)
@@ -323,7 +341,7 @@ def run_ours(args):
                 r = measure_path(ipm, net, pd, qd, p, max(5, args.steps // 2), args.warmup, world, local, flush,
                                  want_e2e=False)
                 others[p] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
-                             "condense_only": r["condense_only"],
+                             "condense_only": r["condense_only"], "fp64_fallback_iterations": r["fallbacks"],
                              "phases_ms_per_step": {k: round(v, 3) for k, v in r["phases_ms_per_step"].items()},
                              "clocks": r["clocks"]}
                 del r
@@ -337,7 +355,8 @@ def run_ours(args):
                                if rl["bound"] == "tensor" else f"{pk} MEASURED_PEAKS.json hbm_gbs"))
     cb = cpu_baseline(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
     paths = {args.precision: {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"],
-                              "condense_only": main["condense_only"]}}
+                              "condense_only": main["condense_only"],
+                              "fp64_fallback_iterations": main["fallbacks"]}}
     paths.update(others)
     line = {
         "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -358,7 +377,8 @@ def run_ours(args):
         "roofline": rl,
         "cpu_baseline": cb,
         "e2e": {"value": main["e2e"], "unit": UNIT, "h2d_bytes_per_step": 8 * dims.state_len,
-                "d2h_bytes_per_step": 8 * dims.state_len},
+                "d2h_bytes_per_step": 8 * dims.state_len,
+                "note": "the same iterates as value (restarted from the timed pass's checkpoint)"},
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],
     }

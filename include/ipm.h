@@ -145,7 +145,16 @@ const char *ipm_last_error(const ipm_ctx *ctx);
 ipm_status ipm_init_state(ipm_ctx *ctx, void *stream);
 
 /* Copy a full state in/out (layout above).  on_device != 0: the pointer is a
- * device pointer, else a host pointer (pinned or pageable). */
+ * device pointer, else a host pointer (pinned or pageable).
+ * The state is the primal-dual point of the interior-point method of §2.2:
+ * the primal variables (x, u, s) of the slacked problem eq. (3), the
+ * multipliers y of g = 0 and z of h + s = 0 in the Lagrangian eq. (4), the
+ * bound multipliers (the paper's kappa, lambda, nu of eq. (4); here one per
+ * finite side of each two-sided box, the paper having one-sided bounds only),
+ * the barrier parameter mu of the smoothed complementarity X kappa = mu e of
+ * eq. (5), and the line-search penalty rho and last inertia shift (state of
+ * the rule set the paper leaves to MadNLP, §2.2).  Errors: IPM_ERR_ARG on a
+ * NULL pointer, IPM_ERR_CUDA on a failed copy. */
 ipm_status ipm_set_state(ipm_ctx *ctx, const double *state, int on_device, void *stream);
 ipm_status ipm_get_state(ipm_ctx *ctx, double *state, int on_device, void *stream);
 
@@ -163,7 +172,18 @@ ipm_status ipm_condense_scenarios(ipm_ctx *ctx, void *stream);
 
 /* Factor K_hat + delta_w (sum_i Z_i^T Z_i + I) -- i.e. the reduced matrix of
  * K + delta_w I -- by dense FP64 Cholesky.  *is_pd = 1 on success, 0 when a
- * pivot is not positive (correct inertia <=> K_hat positive definite). */
+ * pivot is not positive.
+ * K_hat = Z^T K Z of Prop. 2.3 (eq. (11)) is the Schur complement S_uu of the
+ * block-angular condensed system (Prop. 2.4, with the A_i^{-1} of eq. (15));
+ * once summed over scenarios (§3.2, "Global reduction"), it is factored
+ * densely (§4.2: a LAPACK factorization on the GPU, a small share of the
+ * time).  With every G_x^i invertible, the condensed matrix of eq. (8)
+ * has inertia (N n_x + n_u, N n_x, 0) exactly when S_uu is positive definite
+ * (Haynsworth's inertia additivity over the Schur complement; each A_i has
+ * inertia (n_x, n_x, 0)), so a successful factorization is the inertia test.
+ * The paper does not describe inertia correction: delta_w adds delta_w I to
+ * the W block of eq. (6) (IPOPT's rule, the reading the library takes).
+ * Errors: IPM_ERR_STATE before ipm_condense_scenarios. */
 ipm_status ipm_factor_schur(ipm_ctx *ctx, double delta_w, int *is_pd, void *stream);
 
 /* Solve the Newton system eq. (6) through eq. (11) and the recoveries of
@@ -175,10 +195,22 @@ ipm_status ipm_solve_kkt(ipm_ctx *ctx, double *step, double *refine_resid, void 
 /* One full interior-point iteration (evaluate, test convergence, update mu,
  * condense, factor with inertia correction, solve, fraction to boundary,
  * backtracking line search, update).  *converged = 1 when the current point
- * already meets E_0 <= tol (no step is then taken); *kkt_err = E_0 there. */
+ * already meets E_0 <= tol (no step is then taken); *kkt_err = E_0 there.
+ * §2.2: one Newton step on the KKT conditions eq. (5) with the complementarity
+ * smoothed by mu, its direction the solution of the augmented system eq. (6),
+ * obtained here through the condensation of Prop. 2.1 and the reduction of
+ * Prop. 2.3.  The paper delegates the step-length, barrier and stopping rules
+ * to MadNLP (Nocedal & Wright ch. 19); the library takes fraction to the
+ * boundary, an l1-merit backtracking line search and E_0 of Waechter and
+ * Biegler as its reading.  Errors: IPM_ERR_NOT_PD, IPM_ERR_LINESEARCH,
+ * IPM_ERR_SINGULAR_GX, IPM_ERR_TIMEOUT, IPM_ERR_CUDA. */
 ipm_status ipm_step(ipm_ctx *ctx, int *converged, double *kkt_err, void *stream);
 
-/* Run ipm_step until convergence or max_iter.  *iters = Newton steps taken. */
+/* Run ipm_step until convergence or max_iter.  *iters = Newton steps taken.
+ * §4.2 solves every instance "to a KKT residual" of the IPM of §2.2; the
+ * library stops at E_0 <= opt.tol (1e-8), E_0 = max(scaled dual residual of
+ * eq. (5a)-(5c), primal residual of eq. (5d)-(5e), scaled complementarity of
+ * eq. (5f)-(5h)).  Errors: those of ipm_step, IPM_ERR_MAXITER. */
 ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
 
 /* Diagnostics for tests: copy an internal quantity to host memory.
@@ -192,7 +224,10 @@ ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
  *        dual, primal, compl max, compl min, s_d, s_c), IPM_Q_INFO (10 doubles:
  *        alpha, alpha_max, alpha_z, delta, trials, rho, mu_used, refinement
  *        iterations, refinement relative residual, 1 if the iteration fell back
- *        to the FP64 condensation),
+ *        to the FP64 condensation; if cap allows, then the number of
+ *        iterations since ipm_create that fell back to the FP64
+ *        condensation, and the number of emulated contractions redone on
+ *        the FP64 units),
  *        IPM_Q_TIMERS (2*IPM_N_PHASES doubles: accumulated device milliseconds
  *        and call counts per phase, see ipm_set_profiling; a further double,
  *        if cap allows, is the total number of kernels the library launched).
@@ -383,7 +418,13 @@ ipm_status ipm_schur_sum_tc(const double *Z, const double *Y, int n_scen, int n_
  * IPM_SCHUR_NOALLOC_MAX_NU does not fit and returns IPM_ERR_ARG without
  * launching anything.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array: calls
+ * first call before any stream capture.  Under CUDA's default lazy module
+ * loading the array (with the module's code) is committed to device memory
+ * by that first lookup, not when the library is loaded: make the first call
+ * before another pool claims the device's memory, or set
+ * CUDA_MODULE_LOADING=EAGER so the array is committed at load time.  A CUDA
+ * error already pending on the calling thread is reported as IPM_ERR_CUDA
+ * before anything is launched (and left pending).  All calls share the array: calls
  * that overlap on the GPU race and must be serialised by the caller.
  * Errors: IPM_ERR_ARG (null pointer, non-positive size, n_u too large),
  * IPM_ERR_CUDA (symbol lookup or launch failed). */

@@ -1392,6 +1392,9 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
   if (which == IPM_Q_INFO) {
     if (!need(10)) return IPM_ERR_ARG;
     std::memcpy(out, c->info, 10 * sizeof(double));
+    // optional tail: counts since the context was created
+    if (cap >= 11) out[10] = (double)c->n_fallback;       // mixed: iterations condensed again in FP64
+    if (cap >= 12) out[11] = (double)c->n_emu_fallback;   // FP64_TC: contractions redone on the FP64 units
     return IPM_OK;
   }
   if (scen < 0 || scen >= N) return IPM_ERR_ARG;

@@ -127,6 +127,9 @@ extern "C" ipm_status ipm_schur_sum_noalloc(const double *Z, const double *Y, co
   const long long ntiles = (long long)nt1 * (nt1 + 1) / 2;
   const long long tile_doubles = (long long)NT * NT;
   if (n_u > IPM_SCHUR_NOALLOC_MAX_NU || ntiles * tile_doubles > kScratchDoubles) return IPM_ERR_ARG;
+  // an error left pending by earlier work on this thread is not ours to
+  // clear or report as ours: refuse before launching anything
+  if (cudaPeekAtLastError() != cudaSuccess) return IPM_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IPM_ERR_CUDA;
   double *scratch = nullptr;
@@ -149,11 +152,12 @@ extern "C" ipm_status ipm_schur_sum_noalloc(const double *Z, const double *Y, co
   cudaStream_t st = (cudaStream_t)stream;
   dim3 grid((unsigned)ntiles, (unsigned)ngroups);
   k_schur_partial_na<<<grid, 256, 0, st>>>(n_x, n_u, n_scen, spg, nt1, Z, Y, scratch);
+  if (cudaGetLastError() != cudaSuccess) return IPM_ERR_CUDA;  // this launch's own error
   ipm_count_launch();
   const long long tot = (long long)n_u * n_u;
   k_schur_assemble_na<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n_u, n_scen, ngroups, (int)ntiles, nt1,
                                                                       scratch, Yu, diag, Khat);
-  ipm_count_launch();
   if (cudaGetLastError() != cudaSuccess) return IPM_ERR_CUDA;
+  ipm_count_launch();
   return IPM_OK;
 }
