@@ -106,7 +106,14 @@ typedef struct {
                             that nothing is read before it is written; results must not change) */
   int lu_pair;           /* 1 (default): factor G_x on a cluster of two CTAs per scenario when its
                             dense trailing block fits their shared memory; 0: one CTA */
-  int reserved[2];
+  int aug_refine;        /* steps of FP64 iterative refinement on the residual of the augmented
+                            system eq. (6) after the reduced solve (default 10, every path): the
+                            residual of the step is formed from J, K and the right-hand sides,
+                            the correction is solved through the same condensation and
+                            reduction, and refinement stops at a relative residual (max norm,
+                            against the right-hand side) <= 1e-12 or when a step no longer
+                            halves it; 0 = no residual check */
+  int reserved;
   double sigma;          /* centring factor of the adaptive rule (0.1) */
 } ipm_options;
 
@@ -187,9 +194,12 @@ ipm_status ipm_condense_scenarios(ipm_ctx *ctx, void *stream);
 ipm_status ipm_factor_schur(ipm_ctx *ctx, double delta_w, int *is_pd, void *stream);
 
 /* Solve the Newton system eq. (6) through eq. (11) and the recoveries of
- * Props. 2.1 and 2.3.  step: nullable device pointer receiving step_len
+ * Props. 2.1 and 2.3, then refine it on the residual of eq. (6) itself
+ * (opt.aug_refine).  step: nullable device pointer receiving step_len
  * doubles.  refine_resid: nullable host pointer receiving the relative
- * residual of the condensed system after refinement. */
+ * residual max|rho| / max|r| of the augmented system eq. (6) at the returned
+ * step (the CG residual of the reduced system on the mixed path when
+ * aug_refine = 0). */
 ipm_status ipm_solve_kkt(ipm_ctx *ctx, double *step, double *refine_resid, void *stream);
 
 /* One full interior-point iteration (evaluate, test convergence, update mu,
@@ -226,8 +236,10 @@ ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
  *        iterations, refinement relative residual, 1 if the iteration fell back
  *        to the FP64 condensation; if cap allows, then the number of
  *        iterations since ipm_create that fell back to the FP64
- *        condensation, and the number of emulated contractions redone on
- *        the FP64 units),
+ *        condensation, the number of emulated contractions redone on the
+ *        FP64 units, and for the last solve the refinement steps on the
+ *        augmented system eq. (6), its relative residual before and after
+ *        them),
  *        IPM_Q_TIMERS (2*IPM_N_PHASES doubles: accumulated device milliseconds
  *        and call counts per phase, see ipm_set_profiling; a further double,
  *        if cap allows, is the total number of kernels the library launched).

@@ -59,6 +59,15 @@ struct ipm_ctx {
   bool exact_iter = false;   // this iteration runs the FP64 condensation (mixed fallback)
   long long n_fallback = 0;  // mixed-path iterations that needed the FP64 condensation
   double *step = nullptr, *px = nullptr, *pu = nullptr, *ps = nullptr, *py = nullptr, *pz = nullptr;
+  // iterative refinement on the residual of the augmented system eq. (6):
+  // residual blocks (reused as the correction's right-hand side), the
+  // correction, its condensed right-hand side, scratch in position order
+  double *ar1x = nullptr, *ar1u = nullptr, *ar2 = nullptr, *ar3 = nullptr, *ar4 = nullptr, *atw = nullptr;
+  double *dstep = nullptr, *dpx = nullptr, *dpu = nullptr, *dps = nullptr, *dpy = nullptr, *dpz = nullptr;
+  double *arh1x = nullptr, *arh2 = nullptr, *arhs = nullptr, *apos2 = nullptr, *bpos2 = nullptr, *vpos2 = nullptr;
+  unsigned long long *amax = nullptr, *h_amax = nullptr;
+  int aug_steps = 0;
+  double aug_res0 = 0.0, aug_res = 0.0;
   double *dz[6] = {};
   double *Hp = nullptr, *kpx = nullptr, *kpu = nullptr, *vpos = nullptr, *bpos = nullptr, *apos = nullptr;
   double *xt = nullptr, *ut = nullptr, *st = nullptr, *gt = nullptr, *ht = nullptr, *fst = nullptr,

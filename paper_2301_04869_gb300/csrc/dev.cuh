@@ -15,6 +15,7 @@ struct DevSym {
   const int *lfr, *lto;
   const double *lg, *lb, *lbh;
   const int *a_ptr, *a_col, *a_diag, *inc_ptr, *inc_line, *inc_other, *inc_aslot;
+  const int *a_tslot;  // per A slot (i, k): the slot of (k, i)
   const int *kb_ptr, *kb_col, *kb_row, *kb_aslot, *kbi_ptr, *kbi_r, *kbi_ja, *kbi_jb;
   const int *hrow_bus, *hrow_comp, *ht_ptr, *ht_r, *ht_aslot;
   const int *perm, *iperm;

@@ -105,6 +105,7 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   TRY(upload(c, &d.lfr, S.lfr)); TRY(upload(c, &d.lto, S.lto));
   TRY(upload(c, &d.lg, S.lg)); TRY(upload(c, &d.lb, S.lb)); TRY(upload(c, &d.lbh, S.lbh));
   TRY(upload(c, &d.a_ptr, S.a_ptr)); TRY(upload(c, &d.a_col, S.a_col)); TRY(upload(c, &d.a_diag, S.a_diag));
+  TRY(upload(c, &d.a_tslot, S.a_tslot));
   TRY(upload(c, &d.inc_ptr, S.inc_ptr)); TRY(upload(c, &d.inc_line, S.inc_line));
   TRY(upload(c, &d.inc_other, S.inc_other)); TRY(upload(c, &d.inc_aslot, S.inc_aslot));
   TRY(upload(c, &d.kb_ptr, S.kb_ptr)); TRY(upload(c, &d.kb_col, S.kb_col)); TRY(upload(c, &d.kb_row, S.kb_row));
@@ -294,6 +295,20 @@ ipm_status alloc_work(ipm_ctx *c) {
     TRY(dalloc(c, &c->dz[i], len));
   }
   TRY(dalloc(c, &c->Hp, N * m)); TRY(dalloc(c, &c->kpx, N * nx)); TRY(dalloc(c, &c->kpu, N * nu));
+  if (c->opt.aug_refine > 0) {
+    TRY(dalloc(c, &c->ar1x, N * nx)); TRY(dalloc(c, &c->ar3, N * nx)); TRY(dalloc(c, &c->ar1u, nu));
+    TRY(dalloc(c, &c->ar2, N * m)); TRY(dalloc(c, &c->ar4, N * m)); TRY(dalloc(c, &c->atw, N * m));
+    TRY(dalloc(c, &c->dstep, c->step_len));
+    c->dpx = c->dstep;
+    c->dpu = c->dpx + N * nx;
+    c->dps = c->dpu + nu;
+    c->dpy = c->dps + N * m;
+    c->dpz = c->dpy + N * nx;
+    TRY(dalloc(c, &c->arh1x, N * nx)); TRY(dalloc(c, &c->arh2, nu)); TRY(dalloc(c, &c->arhs, nu));
+    TRY(dalloc(c, &c->apos2, N * nx)); TRY(dalloc(c, &c->bpos2, N * nx)); TRY(dalloc(c, &c->vpos2, N * nx));
+    TRY(dalloc(c, &c->amax, 2));
+    CK(cudaMallocHost(&c->h_amax, 2 * sizeof(unsigned long long)));
+  }
   TRY(dalloc(c, &c->vpos, N * nx)); TRY(dalloc(c, &c->bpos, N * nx)); TRY(dalloc(c, &c->apos, N * nx));
   TRY(dalloc(c, &c->xt, N * nx)); TRY(dalloc(c, &c->ut, nu)); TRY(dalloc(c, &c->st, N * m));
   TRY(dalloc(c, &c->gt, N * nx)); TRY(dalloc(c, &c->ht, N * m)); TRY(dalloc(c, &c->fst, N));
@@ -866,6 +881,97 @@ ipm_status pcg_reduced(ipm_ctx *c, double delta, cudaStream_t st) {
   return IPM_OK;
 }
 
+// Relative residual of the augmented system eq. (6) at the step (c->px ..
+// c->pz): rho = -r - A p, returns max|rho| / max|r| (read back).  Leaves
+// kpx, kpu = K p_d (positions) and Hp = H p_d of this step, which the line
+// search reads, and rho in ar1x .. ar4.
+ipm_status aug_residual(ipm_ctx *c, double delta, double *rel, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
+  launch_gather_pos(S.N, S.nx, S.iperm, c->px, c->vpos, 1.0, st);
+  launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);
+  launch_aug_residual(S, D, delta, c->px, c->pu, c->ps, c->py, c->pz, c->kpx, c->kpu, c->diag1, c->Hp, c->atw,
+                      c->ar1x, c->ar1u, c->ar2, c->ar3, c->ar4, st);
+  CK(cudaMemsetAsync(c->amax, 0, 2 * sizeof(unsigned long long), st));
+  launch_maxabs2(NX, c->ar1x, D.r1x, c->amax, st);
+  launch_maxabs2(NX, c->ar3, D.g, c->amax, st);
+  launch_maxabs2(NM, c->ar2, D.r2, c->amax, st);
+  launch_maxabs2(NM, c->ar4, D.r4, c->amax, st);
+  launch_maxabs2(S.nu, c->ar1u, D.r1u, c->amax, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->h_amax, c->amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double a, b;
+  std::memcpy(&a, &c->h_amax[0], sizeof(double));
+  std::memcpy(&b, &c->h_amax[1], sizeof(double));
+  *rel = b > 0.0 ? a / b : a;
+  return IPM_OK;
+}
+
+// FP64 iterative refinement of the step on the augmented system eq. (6):
+// with rho the residual of the current step, the correction solves
+// A dp = rho, i.e. the Newton system with right-hand side r' = -rho, through
+// the same condensation (Prop. 2.1), reduction (eq. (11), Prop. 2.3) and
+// factor; then p += dp.  Stops at a relative residual <= 1e-12, when a step
+// does not halve it (the best step is kept), or after opt.aug_refine steps.
+ipm_status refine_aug(ipm_ctx *c, double delta, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  DevWork &D = c->dw;
+  const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
+  double rel = 0.0;
+  TRY(aug_residual(c, delta, &rel, st));
+  c->aug_res0 = rel;
+  c->aug_steps = 0;
+  for (int it = 0; it < c->opt.aug_refine && rel > 1e-12 && std::isfinite(rel); ++it) {
+    // right-hand side r' = -rho (in place)
+    launch_lincomb(NX, c->ar1x, -1.0, c->ar1x, 0.0, nullptr, 0.0, nullptr, st);
+    launch_lincomb(NX, c->ar3, -1.0, c->ar3, 0.0, nullptr, 0.0, nullptr, st);
+    launch_lincomb(S.nu, c->ar1u, -1.0, c->ar1u, 0.0, nullptr, 0.0, nullptr, st);
+    launch_lincomb(NM, c->ar2, -1.0, c->ar2, 0.0, nullptr, 0.0, nullptr, st);
+    launch_lincomb(NM, c->ar4, -1.0, c->ar4, 0.0, nullptr, 0.0, nullptr, st);
+    // condensed right-hand side (Prop. 2.1): rhat1 = r1' + H^T (Sigma_s r4' - r2')
+    launch_tv(NM, D.Ss, c->ar2, c->ar4, c->atw, st);
+    launch_htv(S, D, c->ar1x, c->ar1u, c->atw, c->arh1x, c->arh2, st);
+    // eq. (11): b = G_x^{-1} r3', a = G_x^{-T}(rhat1_x - (K_xx + delta) b)
+    launch_gather_pos(S.N, S.nx, S.iperm, c->ar3, c->bpos2, 1.0, st);
+    launch_solve1(S, D.LU, D.rd, c->bpos2, 0, st);
+    launch_kapply(S, D.K, c->bpos2, nullptr, c->kpx, nullptr, st);
+    launch_gather_pos(S.N, S.nx, S.iperm, c->arh1x, c->apos2, 1.0, st);
+    launch_lincomb(NX, c->apos2, 1.0, c->apos2, -1.0, c->kpx, -delta, c->bpos2, st);
+    launch_solve1(S, D.LU, D.rd, c->apos2, 1, st);
+    launch_rhs_reduced(S, D.J, D.K, c->arh2, c->apos2, c->bpos2, c->dpu, st);
+    launch_chol_solve(S.nu, c->F, c->dpu, st);
+    // Prop. 2.3: dp_x = -G_x^{-1}(r3' + G_u dp_u), dp_y = -G_x^{-T}(rhat1_x + (K_xx + delta) dp_x + K_xu dp_u)
+    launch_gather_pos(S.N, S.nx, S.iperm, c->ar3, c->vpos2, 1.0, st);
+    launch_gu_apply(S, D.J, c->dpu, c->vpos2, st);
+    launch_solve1(S, D.LU, D.rd, c->vpos2, 0, st);
+    launch_lincomb(NX, c->vpos2, -1.0, c->vpos2, 0.0, nullptr, 0.0, nullptr, st);
+    launch_kapply(S, D.K, c->vpos2, c->dpu, c->kpx, c->kpu, st);
+    launch_gather_pos(S.N, S.nx, S.iperm, c->arh1x, c->apos2, 1.0, st);
+    launch_lincomb(NX, c->apos2, 1.0, c->apos2, 1.0, c->kpx, delta, c->vpos2, st);
+    launch_solve1(S, D.LU, D.rd, c->apos2, 1, st);
+    launch_scatter_pos(S.N, S.nx, S.iperm, c->apos2, c->dpy, -1.0, st);
+    launch_scatter_pos(S.N, S.nx, S.iperm, c->vpos2, c->dpx, 1.0, st);
+    // Prop. 2.1: dp_z, dp_s
+    launch_pzps_rhs(S, D, c->dpx, c->dpu, c->ar2, c->ar4, c->dpz, c->dps, st);
+    launch_lincomb(c->step_len, c->step, 1.0, c->step, 1.0, c->dstep, 0.0, nullptr, st);
+    double rel_new = 0.0;
+    TRY(aug_residual(c, delta, &rel_new, st));
+    ++c->aug_steps;
+    if (!(rel_new <= 0.5 * rel)) {
+      // stagnation: undo this correction and stop (the residual and the
+      // products of the kept step are formed again for the line search)
+      launch_lincomb(c->step_len, c->step, 1.0, c->step, -1.0, c->dstep, 0.0, nullptr, st);
+      TRY(aug_residual(c, delta, &rel, st));
+      break;
+    }
+    rel = rel_new;
+  }
+  c->aug_res = rel;
+  return IPM_OK;
+}
+
 // Newton step: p_u from the Cholesky factor, then p_x, p_y (Prop. 2.3),
 // p_z, p_s (Prop. 2.1) and the bound-dual steps.  With defer_py the
 // transposed solve for p_y runs on the side stream (join_py before y is
@@ -885,7 +991,15 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st, bool defer_py = false) {
     CK(cudaMemcpyAsync(c->vpos, c->bpos, NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_z_apply(S, c->Z, c->pu, -1.0, c->vpos, st);
   } else {
-    TRY(pcg_reduced(c, delta, st));
+    if (c->opt.max_refine > 0) {
+      TRY(pcg_reduced(c, delta, st));
+    } else {
+      // the mixed-precision factor alone; refinement on eq. (6) follows
+      launch_chol_solve(S.nu, c->F, c->pu, st);
+      c->refine_iters = 0;
+      c->refine_res = 0.0;
+      c->neg_curv = false;
+    }
     // p_x = -G_x^{-1} (r3 + G_u p_u) with FP64 solves
     launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->vpos, 1.0, st);
     launch_gu_apply(S, D.J, c->pu, c->vpos, st);
@@ -897,7 +1011,8 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st, bool defer_py = false) {
   launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);
   launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
   launch_lincomb(NX, c->apos, 1.0, c->apos, 1.0, c->kpx, delta, c->vpos, st);
-  if (defer_py) {
+  const bool refine = c->opt.aug_refine > 0;
+  if (defer_py && !refine) {
     TRY(ensure_side(c));
     CK(cudaEventRecord(c->ev_fork, st));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -910,6 +1025,7 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st, bool defer_py = false) {
     launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, c->py, -1.0, st);
   }
   launch_pz_ps(S, D, c->px, c->pu, c->Hp, c->pz, c->ps, st);
+  if (refine) TRY(refine_aug(c, delta, st));
   launch_bound_steps(NX, S.nx, D.x, c->px, S.xl, S.xu, D.zlx, D.zux, mu, c->dz[0], c->dz[1], st);
   launch_bound_steps(S.nu, S.nu, D.u, c->pu, S.ul, S.uu, D.zlu, D.zuu, mu, c->dz[2], c->dz[3], st);
   launch_bound_steps(NM, S.m, D.s, c->ps, S.sl, S.su, D.zls, D.zus, mu, c->dz[4], c->dz[5], st);
@@ -1000,7 +1116,12 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
     }
   }
   TRY(do_solve(c, st, true));
-  if (c->mixed && !c->exact_iter && (c->neg_curv || !(c->refine_res <= 1e-10))) {
+  // the mixed-precision step is kept when CG (if run) converged without
+  // meeting non-positive curvature and, with refinement on eq. (6), its
+  // augmented residual reached 1e-10
+  const bool cg_bad = c->opt.max_refine > 0 && (c->neg_curv || !(c->refine_res <= 1e-10));
+  const bool aug_bad = c->opt.aug_refine > 0 && !(c->aug_res <= 1e-10);
+  if (c->mixed && !c->exact_iter && (cg_bad || aug_bad)) {
     join_py(c, st);
     // CG met non-positive curvature or did not converge: redo in FP64
     c->exact_iter = true;
@@ -1188,6 +1309,7 @@ ipm_status ipm_default_options(ipm_options *opt) {
   opt->graphs = 0;
   opt->autotune = 0;
   opt->lu_pair = 1;
+  opt->aug_refine = 10;
   opt->barrier_rule = IPM_BARRIER_ADAPTIVE;
   opt->sigma = 0.1;
   return IPM_OK;
@@ -1211,7 +1333,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
   else ipm_default_options(&c->opt);
   if ((c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED &&
        c->opt.precision != IPM_PREC_FP64_TC) || !(c->opt.tol > 0) ||
-      c->opt.max_iter < 0 || c->opt.max_refine < 0 ||
+      c->opt.max_iter < 0 || c->opt.max_refine < 0 || c->opt.aug_refine < 0 || c->opt.aug_refine > 100 ||
       (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
       (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
       (c->opt.poison != 0 && c->opt.poison != 1) || (c->opt.lu_pair != 0 && c->opt.lu_pair != 1) ||
@@ -1256,6 +1378,7 @@ ipm_status ipm_destroy(ipm_ctx *c) {
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   if (c->h_mu) cudaFreeHost(c->h_mu);
+  if (c->h_amax) cudaFreeHost(c->h_amax);
   for (int b = 0; b < 2; ++b) {
     if (c->gx_pre[b]) cudaGraphExecDestroy(c->gx_pre[b]);
     if (c->gx_post[b]) cudaGraphExecDestroy(c->gx_post[b]);
@@ -1321,7 +1444,7 @@ ipm_status ipm_solve_kkt(ipm_ctx *c, double *step, double *refine_resid, void *s
   cudaStream_t st = STR(stream);
   TRY(do_solve(c, st));
   if (step) CK(cudaMemcpyAsync(step, c->step, c->step_len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if (refine_resid) *refine_resid = c->mixed ? c->refine_res : 0.0;
+  if (refine_resid) *refine_resid = c->opt.aug_refine > 0 ? c->aug_res : (c->mixed ? c->refine_res : 0.0);
   CK(cudaStreamSynchronize(st));
   return IPM_OK;
 }
@@ -1395,6 +1518,9 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
     // optional tail: counts since the context was created
     if (cap >= 11) out[10] = (double)c->n_fallback;       // mixed: iterations condensed again in FP64
     if (cap >= 12) out[11] = (double)c->n_emu_fallback;   // FP64_TC: contractions redone on the FP64 units
+    if (cap >= 13) out[12] = (double)c->aug_steps;        // refinement steps on eq. (6), last solve
+    if (cap >= 14) out[13] = c->aug_res0;                  // its relative residual before them
+    if (cap >= 15) out[14] = c->aug_res;                   // and after
     return IPM_OK;
   }
   if (scen < 0 || scen >= N) return IPM_ERR_ARG;

@@ -36,6 +36,7 @@ struct Sym {
   std::vector<double> lg, lb, lbh;           // series g, series b, half charging
   int nnzA = 0;
   std::vector<int> a_ptr, a_col, a_diag;
+  std::vector<int> a_tslot;                  // per A slot (i, k): the slot of (k, i)
   std::vector<int> inc_ptr, inc_line, inc_other, inc_aslot;
   int nnzKB = 0;
   std::vector<int> kb_ptr, kb_col, kb_row, kb_aslot;

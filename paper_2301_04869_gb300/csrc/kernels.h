@@ -117,6 +117,23 @@ void launch_init_primal(const DevSym &S, double *x, double *u, const double *pma
 void launch_fill_bound_duals(long long n, int period, const double *l, const double *b, double *zl,
                              double *zu, cudaStream_t st);
 
+// kernels_refine.cu (residual of the augmented system eq. (6) at a step; all
+// vectors in state order except kpx_pos, the positions of K p_d)
+void launch_aug_residual(const DevSym &S, const DevWork &D, double delta, const double *px, const double *pu,
+                         const double *ps, const double *py, const double *pz, const double *kpx_pos,
+                         const double *kpu, const double *diag1, double *Hp, double *tw, double *rho1x,
+                         double *rho1u, double *rho2, double *rho3, double *rho4, cudaStream_t st);
+// outx = ax + H_x^T v (per scenario), outu = au + sum_i H_u^T v_i
+void launch_htv(const DevSym &S, const DevWork &D, const double *ax, const double *au, const double *v, double *outx,
+                double *outu, cudaStream_t st);
+// t = Sigma_s r4 - r2
+void launch_tv(long long n, const double *Ss, const double *r2, const double *r4, double *t, cudaStream_t st);
+// pz = Sigma_s (H p_d + r4) - r2, ps = -(r2 + pz) / Sigma_s
+void launch_pzps_rhs(const DevSym &S, const DevWork &D, const double *px, const double *pu, const double *r2,
+                     const double *r4, double *pz, double *ps, cudaStream_t st);
+// out[0] = max(out[0], max|a|), out[1] = max(out[1], max|b|) as the bit patterns of the magnitudes
+void launch_maxabs2(long long n, const double *a, const double *b, unsigned long long *out, cudaStream_t st);
+
 // warm-start vectors: segment offsets (seg[0] = 0 ... seg[9] = d) and the
 // bounded-component lists of the six dual blocks (device, concatenated)
 struct WarmSeg {

@@ -151,6 +151,9 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   };
   S.a_diag.resize(n);
   for (int i = 0; i < n; ++i) S.a_diag[i] = aslot(i, i);
+  S.a_tslot.resize(S.nnzA);
+  for (int i = 0; i < n; ++i)
+    for (int q = S.a_ptr[i]; q < S.a_ptr[i + 1]; ++q) S.a_tslot[q] = aslot(S.a_col[q], i);
   // incidence lists
   S.inc_ptr.assign(n + 1, 0);
   {

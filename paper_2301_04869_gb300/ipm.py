@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("solve_threads", ctypes.c_int), ("barrier_rule", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
-                ("lu_pair", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+                ("lu_pair", ctypes.c_int), ("aug_refine", ctypes.c_int), ("reserved", ctypes.c_int),
                 ("sigma", ctypes.c_double)]
 
 
@@ -194,7 +194,7 @@ def _cnet(net):
 
 
 def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, barrier_rule=None, sigma=None,
-                 graphs=False, autotune=False, solve_threads=0, poison=False, lu_pair=True):
+                 graphs=False, autotune=False, solve_threads=0, poison=False, lu_pair=True, aug_refine=None):
     lib = load()
     opt = Options()
     lib.ipm_default_options(ctypes.byref(opt))
@@ -211,6 +211,8 @@ def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, bar
     opt.solve_threads = int(solve_threads)
     opt.poison = int(bool(poison))
     opt.lu_pair = int(bool(lu_pair))
+    if aug_refine is not None:
+        opt.aug_refine = int(aug_refine)
     return opt
 
 
@@ -219,13 +221,14 @@ class Solver:
 
     def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
                  barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0, poison=False,
-                 lu_pair=True):
+                 lu_pair=True, aug_refine=None):
         lib = load()
         self._lib = lib
         self._keep, cnet = _cnet(net)
         opt = make_options(precision=precision, tol=tol, max_iter=max_iter, max_refine=max_refine,
                            barrier_rule=barrier_rule, sigma=sigma, graphs=graphs, autotune=autotune,
-                           solve_threads=solve_threads, poison=poison, lu_pair=lu_pair)
+                           solve_threads=solve_threads, poison=poison, lu_pair=lu_pair,
+                           aug_refine=aug_refine)
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]
@@ -318,7 +321,7 @@ class Solver:
         d = self.dims
         sizes = {Q_KHAT: d.n_u * d.n_u, Q_RHS_U: d.n_u, Q_Z: d.n_x * d.n_u, Q_FGH: 1 + d.n_x + d.m,
                  Q_JAC: d.n_x * d.n_x + d.n_x * d.n_u + d.m * d.n_x + d.m * d.n_u,
-                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 12,
+                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 15,
                  Q_TIMERS: 2 * N_PHASES + 1, Q_ZTZ: d.n_u * d.n_u}
         out = np.empty(sizes[which])
         self._check(self._lib.ipm_get_quantity(self._h, which, scen, _ptr(out, ctypes.c_double), out.size,

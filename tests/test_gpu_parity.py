@@ -2,9 +2,15 @@
 
 Every comparison evaluates both sides at the same iterate (the oracle's,
 copied in with ipm_set_state) and checks the normwise relative error
-max|gpu - oracle| / max|oracle| <= 1e-10 (the FP64 parity bar), per output.
-Cases span one scenario (30 buses), a ragged small batch (60 buses, 5
-scenarios), and the 1000-bus network with 4 and 64 scenarios."""
+max|gpu - oracle| / max|oracle| per output.  Kernel outputs (derivatives,
+condensed blocks, Z, K_hat, the reduced right-hand side) meet the FP64 parity
+bar 1e-10.  The Newton step is the solution of a linear system: two
+backward-stable FP64 solves of it (the GPU's static-pivot LU and Cholesky,
+the oracle's SuperLU and LAPACK) each carry a forward error of order
+kappa(K_hat) eps, so its bar is max(1e-10, 10 kappa_2(K_hat) eps) with
+kappa from the oracle's K_hat at that iterate (the measured errors sit at
+0.3 - 3 kappa eps).  Cases span one scenario (30 buses), a ragged small batch
+(60 buses, 5 scenarios), and the 1000-bus network with 4 and 64 scenarios."""
 import numpy as np
 import pytest
 
@@ -14,6 +20,12 @@ from paper_2301_04869_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
+EPS = float(np.finfo(np.float64).eps)
+
+
+def step_bar(Khat):
+    """Parity bar of a Newton step: max(1e-10, 10 kappa_2(K_hat) eps)."""
+    return max(TOL, 10.0 * float(np.linalg.cond(Khat)) * EPS)
 
 
 def rel(a, b):
@@ -134,8 +146,12 @@ def test_newton_step_parity(gpu, name, delta, precision):
     C = kkt.condense(M, st, D, st["mu"], delta)
     L = kkt.cholesky_pd(C.Khat)
     p = kkt.reduced_step(M, st, D, C, L)
+    bar = step_bar(C.Khat)
     for k in ("px", "pu", "ps", "py", "pz"):
-        assert rel(g[k], p[k]) <= 1e-9, k
+        assert rel(g[k], p[k]) <= bar, (k, rel(g[k], p[k]), bar)
+    # the step the library returns was checked on the augmented system eq. (6)
+    info = sol.ipm_get_quantity(gpu.Q_INFO)
+    assert info[14] <= 1e-12, info[12:15]
 
 
 @pytest.mark.parametrize("precision", PRECS)
@@ -161,15 +177,19 @@ def test_full_solve_same_iterations_1000_N4(gpu, precision):
     k_g, e_g = sol.ipm_solve()
     assert k_g == k_o
     assert e_g <= 1e-8
-    # near mu -> 0 the iterates agree only to the conditioning of the KKT
-    # system (~1e-9 relative at mu = 2.5e-9); two points that both meet
-    # E_0 <= 1e-8 may then differ by more than the per-kernel bar
+    # the GPU's final point judged by the oracle: its own optimality error
+    # there must meet the tolerance too
     s = sol.split_state(sol.ipm_get_state())
-    np.testing.assert_allclose(s["u"], st_o["u"], rtol=0, atol=1e-5)
+    st_g = {k: s[k] for k in ("x", "u", "s", "y", "z", "zl_x", "zu_x", "zl_u", "zu_u", "zl_s", "zu_s")}
+    errs = oipm.kkt_errors(M, st_g, kkt.eval_all(M, st_g))
+    assert oipm.e_mu(errs, 0.0) <= 1e-8, errs
+    # near mu -> 0 the iterates agree only to the conditioning of the KKT
+    # system (~1e-9 relative at mu = 2.5e-9, kappa(K_hat) ~ 1e7)
+    np.testing.assert_allclose(s["u"], st_o["u"], rtol=0, atol=1e-6)
 
 
 def test_trajectory_matches_per_iteration(gpu):
-    """Iterate-by-iterate: after each GPU step the state stays within 1e-9
+    """Iterate-by-iterate: after each GPU step the state stays within 1e-8
     (relative) of the oracle's, on a 5-scenario problem."""
     net, pd, qd, M, st0 = case("60bus_N5")
     M = opf.Model(net, pd, qd)
@@ -187,34 +207,105 @@ def test_trajectory_matches_per_iteration(gpu):
         assert abs(s["mu"] - st["mu"]) <= 1e-8 * st["mu"]
 
 
-def test_config_1000bus_64_scenarios_components(gpu):
-    """The full 1000-bus / 64-scenario workload at one iterate: K_hat, the
-    reduced right-hand side and the Newton step."""
+_n64 = {}
+
+
+def n64_iterate(k):
+    """The 1000-bus / 64-scenario workload at the oracle's k-th iterate, with
+    the oracle's condensation (delta = 0), inertia-corrected factor and step."""
+    if k not in _n64:
+        net, pd, qd = synth.workload("opf1000_n64")
+        M = opf.Model(net, pd, qd)
+        st = oipm.initial_state(M)
+        for _ in range(k):
+            oipm.iterate(M, st)
+        D = kkt.eval_all(M, st)
+        C0 = kkt.condense(M, st, D, st["mu"], 0.0)
+        C, L, delta = oipm.factor_with_inertia_correction(M, dict(st), D, st["mu"])
+        p = kkt.reduced_step(M, st, D, C, L)
+        _n64[k] = (net, pd, qd, M, st, C0, C, delta, p)
+    return _n64[k]
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("k", [2, 12])
+def test_config_1000bus_64_scenarios_components(gpu, precision, k):
+    """The full 1000-bus / 64-scenario workload (231 row groups of the
+    emulated contraction) at an early (delta > 0) and a late iterate: K_hat,
+    Z of the first and last scenario and the reduced right-hand side at 1e-10,
+    all five blocks of the Newton step at the step bar."""
     import torch
-    net, pd, qd = synth.workload("opf1000_n64")
-    M = opf.Model(net, pd, qd)
-    st = oipm.initial_state(M)
-    for _ in range(2):
-        oipm.iterate(M, st)
-    sol = gpu.Solver(net, pd, qd)
-    sol.ipm_set_state(sol.pack_state(st))
+    net, pd, qd, M, st, C0, C, delta, p = n64_iterate(k)
+    sol = solver_for(gpu, net, pd, qd, st, precision)
     sol.ipm_eval_derivatives()
     sol.ipm_condense_scenarios()
-    D = kkt.eval_all(M, st)
-    C0 = kkt.condense(M, st, D, st["mu"], 0.0, keep_Z=False)
-    nu = sol.dims.n_u
+    nx, nu = sol.dims.n_x, sol.dims.n_u
     assert rel(sol.ipm_get_quantity(gpu.Q_KHAT).reshape(nu, nu), C0.Khat) <= TOL
     assert rel(sol.ipm_get_quantity(gpu.Q_RHS_U), C0.rhs_u) <= TOL
+    for i in (0, M.N - 1):
+        assert rel(sol.ipm_get_quantity(gpu.Q_Z, i).reshape(nx, nu), C0.Z[i]) <= TOL, i
     # the oracle's inertia correction at this iterate (delta may be > 0)
-    C, L, delta = oipm.factor_with_inertia_correction(M, dict(st), D, st["mu"])
     assert sol.ipm_factor_schur(0.0) == (delta == 0.0)
     assert sol.ipm_factor_schur(delta)
     step = torch.empty(sol.dims.step_len, dtype=torch.float64, device="cuda")
     sol.ipm_solve_kkt(step)
     g = sol.split_step(step.cpu().numpy())
-    p = kkt.reduced_step(M, st, D, C, L)
-    for k in ("px", "pu", "py"):
-        assert rel(g[k], p[k]) <= 1e-9, k
+    bar = step_bar(C.Khat)
+    for key in ("px", "pu", "ps", "py", "pz"):
+        assert rel(g[key], p[key]) <= bar, (key, rel(g[key], p[key]), bar)
+
+
+def solver_for(gpu, net, pd, qd, st, precision):
+    prec = {"fp64": gpu.PREC_FP64, "fp64_tc": gpu.PREC_FP64_TC, "mixed": gpu.PREC_MIXED}[precision]
+    sol = gpu.Solver(net, pd, qd, precision=prec)
+    sol.ipm_set_state(sol.pack_state(st))
+    return sol
+
+
+@pytest.mark.parametrize("k", [2, 12])
+def test_config_1000bus_64_scenarios_mixed(gpu, k):
+    """The mixed path on the same iterates, at its per-quantity bars: Z from
+    FP32 solves and K_hat from BF16x3 products 1e-5; the reduced right-hand
+    side (FP64 solves) 1e-10; the Newton step after FP64 refinement on the
+    augmented system eq. (6) at the FP64 step bar."""
+    import torch
+    net, pd, qd, M, st, C0, C, delta, p = n64_iterate(k)
+    sol = solver_for(gpu, net, pd, qd, st, "mixed")
+    sol.ipm_eval_derivatives()
+    sol.ipm_condense_scenarios()
+    nx, nu = sol.dims.n_x, sol.dims.n_u
+    assert rel(sol.ipm_get_quantity(gpu.Q_KHAT).reshape(nu, nu), C0.Khat) <= 1e-5
+    assert rel(sol.ipm_get_quantity(gpu.Q_RHS_U), C0.rhs_u) <= TOL
+    for i in (0, M.N - 1):
+        assert rel(sol.ipm_get_quantity(gpu.Q_Z, i).reshape(nx, nu), C0.Z[i]) <= 1e-5, i
+    assert sol.ipm_factor_schur(delta)
+    step = torch.empty(sol.dims.step_len, dtype=torch.float64, device="cuda")
+    sol.ipm_solve_kkt(step)
+    g = sol.split_step(step.cpu().numpy())
+    bar = step_bar(C.Khat)
+    for key in ("px", "pu", "ps", "py", "pz"):
+        assert rel(g[key], p[key]) <= bar, (key, rel(g[key], p[key]), bar)
+
+
+@pytest.mark.slow
+def test_full_solve_same_iterations_1000_N64(gpu):
+    """The benchmarked workload (1000 buses, 64 scenarios) solved from the cold
+    start: the FP64 and FP64_TC paths reach E_0 <= 1e-8 in the same number of
+    iterations as the oracle, and the oracle judges their final points."""
+    net, pd, qd = synth.workload("opf1000_n64")
+    M = opf.Model(net, pd, qd)
+    st_o, k_o, _ = oipm.solve(M)
+    for prec in (gpu.PREC_FP64, gpu.PREC_FP64_TC):
+        sol = gpu.Solver(net, pd, qd, precision=prec)
+        k_g, e_g = sol.ipm_solve()
+        assert k_g == k_o, (prec, k_g, k_o)
+        assert e_g <= 1e-8
+        s = sol.split_state(sol.ipm_get_state())
+        st_g = {k: s[k] for k in ("x", "u", "s", "y", "z", "zl_x", "zu_x", "zl_u", "zu_u", "zl_s", "zu_s")}
+        errs = oipm.kkt_errors(M, st_g, kkt.eval_all(M, st_g))
+        assert oipm.e_mu(errs, 0.0) <= 1e-8, (prec, errs)
+        np.testing.assert_allclose(s["u"], st_o["u"], rtol=0, atol=1e-6)
+        sol.close()
 
 
 def test_singular_state_jacobian(gpu):
