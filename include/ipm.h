@@ -71,7 +71,13 @@ typedef enum {
  * (Y_ff = Y_tt = y + j b/2, Y_ft = Y_tf = -y, y = 1/(r + j x)).
  * gen_bus[0] must be 0: generator 0 is the slack (its Pg is the dependent
  * function P_0 + Pd_0).  Pg bounds are [0, pmax]; Qg bounds [-qmax, qmax];
- * V bounds [vmin, vmax] at every bus. */
+ * V bounds [vmin, vmax] at every bus.  rate: NULL (no line-flow limits,
+ * m = n_gen + 1) or [n_line] positive finite apparent-power ratings: the
+ * operational constraints of §4.1.1 then include |S_f|^2 <= rate^2 and
+ * |S_t|^2 <= rate^2 at both ends of every line, 2 n_line more rows of h
+ * (m = n_gen + 1 + 2 n_line, the count of the paper's instance table): row
+ * n_gen + 1 + l is the from end of line l, row n_gen + 1 + n_line + l its to
+ * end, each h = P^2 + Q^2 of the power entering the line there. */
 typedef struct {
   int n_bus, n_line, n_gen;
   const int *from, *to;        /* [n_line] */
@@ -80,6 +86,7 @@ typedef struct {
   const double *pmax, *qmax;   /* [n_gen] */
   const double *c2, *c1;       /* [n_gen] cost c2 Pg^2 + c1 Pg */
   const double *vmin, *vmax;   /* [n_bus] */
+  const double *rate;          /* [n_line] or NULL */
 } ipm_network;
 
 enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1, IPM_PREC_FP64_TC = 2 };
@@ -302,6 +309,18 @@ ipm_status ipm_symbolic_export(const ipm_network *net, int which, int *out, long
  * structure and device workspace (no allocation).  Errors: IPM_ERR_ARG on
  * non-finite or negative loads. */
 ipm_status ipm_set_loads(ipm_ctx *ctx, const double *pd, const double *qd, void *stream);
+
+/* Line contingencies (§4.1.1: every scenario is assigned its own loads and
+ * potential contingencies, line tripping).  trip: host [n_scen], the index
+ * of the line out of service in that scenario, or -1 for none (NULL: every
+ * line back in service).  A tripped line contributes zeros to that
+ * scenario's injections, flows, Jacobians and Hessian; the sparsity
+ * patterns stay those of the intact network, so the symbolic analysis, the
+ * static-pivot LU order and every workspace are reused.  Resets the cold
+ * start like ipm_set_loads.  Errors: IPM_ERR_ARG for an index out of range
+ * or a line whose loss disconnects the network (G_x would be singular),
+ * checked on the host before anything changes. */
+ipm_status ipm_set_contingencies(ipm_ctx *ctx, const int *trip, void *stream);
 
 /* ---- Multi-instance runner ------------------------------------------------
  * Many independent instances (networks of any size, any scenario counts) on

@@ -12,8 +12,12 @@ with
   u   = (|V| at generator buses, Pg at non-slack generators)      n_u = 2n_g-1
   g_i = (P-balance at buses 1..n-1, Q-balance at non-generator buses)
   h_i = (Qg of every generator, Pg of the slack generator)        m = n_g+1
+        and, when the network carries line ratings, the line-flow limits
+        of §4.1.1 as |S_f,l|^2 and |S_t,l|^2 (apparent power at both ends of
+        every line, bounded above by rate_l^2)          m = n_g+1+2L
   f_i = (1/N) * generation cost (slack Pg is a function of x_i, u)
-These sizes reproduce every row of the paper's Table "MATPOWER instances".
+These sizes reproduce every row of the paper's Table "MATPOWER instances" and
+the nvar / ncon columns of its Table of instance dimensions (with limits).
 
 Derivatives use complex-matrix notation on the bus admittance matrix
 Y = sum over lines of the pi-model stamps.  With V = v*exp(j*theta),
@@ -50,23 +54,91 @@ class Layout:
         # u = (v at gen buses, Pg_1..Pg_{ng-1})
         self.uv_in_a = n + gb
         self.nu = 2 * self.ng - 1
-        self.m = self.ng + 1
-        # h rows: Q at gen buses, then P at bus 0
+        # h rows: Q at gen buses, then P at bus 0, then (with ratings) the
+        # squared apparent flow at the from end of every line, then at the
+        # to end
         self.h_in_a = np.concatenate([n + gb, [0]])
+        self.rated = getattr(net, "rate", None) is not None
+        self.L = int(np.asarray(net.fr).shape[0])
+        self.m = self.ng + 1 + (2 * self.L if self.rated else 0)
 
 
-def admittance(net):
+def admittance(net, on=None):
     """Bus admittance matrix of the pi-model lines (no taps, no shunts):
-    Y_ff = Y_tt = y + j b/2, Y_ft = Y_tf = -y with y = 1/(r + j x)."""
+    Y_ff = Y_tt = y + j b/2, Y_ft = Y_tf = -y with y = 1/(r + j x).
+    on: optional 0/1 status per line (a line out of service stamps nothing)."""
     n = net.n_bus
     y = 1.0 / (net.r + 1j * net.x)
     ysh = 0.5j * net.b
+    if on is not None:
+        y, ysh = y * on, ysh * on
     f = np.asarray(net.fr, dtype=np.int64)
     t = np.asarray(net.to, dtype=np.int64)
     rows = np.concatenate([f, t, f, t])
     cols = np.concatenate([f, t, t, f])
     vals = np.concatenate([y + ysh, y + ysh, -y, -y])
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def branch_admittance(net, on=None):
+    """From- and to-end branch admittance matrices (L x n) of the pi model:
+    I_f = Y_f V with Y_f[l, f] = y + j b/2, Y_f[l, t] = -y (and the mirror for
+    the to end), and the end selectors C_f, C_t (L x n).  on: optional 0/1
+    status per line (a line out of service carries no current)."""
+    n = net.n_bus
+    y = 1.0 / (net.r + 1j * net.x)
+    ysh = 0.5j * net.b
+    if on is not None:
+        y, ysh = y * on, ysh * on
+    f = np.asarray(net.fr, dtype=np.int64)
+    t = np.asarray(net.to, dtype=np.int64)
+    L = f.size
+    ls = np.arange(L)
+    Yf = sp.csr_matrix((np.concatenate([y + ysh, -y]), (np.concatenate([ls, ls]), np.concatenate([f, t]))),
+                       shape=(L, n))
+    Yt = sp.csr_matrix((np.concatenate([y + ysh, -y]), (np.concatenate([ls, ls]), np.concatenate([t, f]))),
+                       shape=(L, n))
+    Cf = sp.csr_matrix((np.ones(L), (ls, f)), shape=(L, n))
+    Ct = sp.csr_matrix((np.ones(L), (ls, t)), shape=(L, n))
+    return Yf, Yt, Cf, Ct
+
+
+def branch_flows(Yb, Cb, theta, v):
+    """Complex power entering the lines at one end: S = (C V) o conj(Y_b V)."""
+    V = v * np.exp(1j * theta)
+    return (Cb @ V) * np.conj(Yb @ V)
+
+
+def branch_flows_cs(Yb, Cb, theta, v):
+    """(P, Q) of branch_flows written with cos/sin, analytic in (theta, v) for
+    complex-step differentiation: with m the end's bus and k = the other,
+    S = sum_k v_m v_k conj(Y_lk) e^{j(th_m - th_k)}."""
+    Yc = Yb.tocoo()
+    mb = Cb.tocsr().indices.astype(np.int64)  # one entry per row: the end's bus
+    l, k = Yc.row, Yc.col
+    m = mb[l]
+    d = theta[m] - theta[k]
+    vv = v[m] * v[k]
+    G, B = Yc.data.real, Yc.data.imag
+    P = np.zeros(Cb.shape[0], dtype=np.result_type(theta, v))
+    Q = np.zeros(Cb.shape[0], dtype=np.result_type(theta, v))
+    np.add.at(P, l, vv * (G * np.cos(d) + B * np.sin(d)))
+    np.add.at(Q, l, vv * (G * np.sin(d) - B * np.cos(d)))
+    return P, Q
+
+
+def dSb_da(Yb, Cb, theta, v):
+    """Jacobian of the branch flows S = (C V) o conj(Y_b V) w.r.t. theta and
+    v (complex sparse L x n each): with D_a = diag(dV/da),
+      dS/da = diag(conj(Y_b V)) C D_a + diag(C V) conj(Y_b) conj(D_a)."""
+    V = v * np.exp(1j * theta)
+    Ib = Yb @ V
+    Dth = sp.diags(1j * V)
+    Dv = sp.diags(V / v)
+    dI = sp.diags(np.conj(Ib))
+    dV = sp.diags(Cb @ V)
+    Ybc = Yb.conj()
+    return (dI @ Cb @ Dth + dV @ Ybc @ Dth.conj()).tocsr(), (dI @ Cb @ Dv + dV @ Ybc @ Dv.conj()).tocsr()
 
 
 def bus_voltage(lay, x, u):
@@ -135,9 +207,15 @@ def hess_weighted_S(Y, theta, v, lamP, lamQ):
     where dV/dtheta = jV, dV/dv = V/v, d2V/dtheta2 = -V,
     d2V/dtheta dv = jV/v, d2V/dv2 = 0.
     Returns a real sparse (2n x 2n) matrix."""
-    V = v * np.exp(1j * theta)
     mu = lamP - 1j * lamQ
-    M = sp.diags(mu) @ Y.conj()
+    return hess_re_vmv(sp.diags(mu) @ Y.conj(), theta, v)
+
+
+def hess_re_vmv(M, theta, v):
+    """Hessian w.r.t. a = (theta, v) of F = Re(V^T M conj(V)) for a complex
+    sparse n x n matrix M, by the product rule of hess_weighted_S."""
+    V = v * np.exp(1j * theta)
+    M = sp.csr_matrix(M)
     MVc = M @ np.conj(V)
     MtV = M.T @ V
     Dp = {"t": 1j * V, "v": V / v}
@@ -160,13 +238,21 @@ class Model:
     """Per-scenario functions and derivatives of one network.
 
     pd, qd: float64[N, n] scenario loads.  Objective weight 1/N per scenario
-    (the paper minimises the average cost, §2.1)."""
+    (the paper minimises the average cost, §2.1).  trip: optional int[N], the
+    line out of service in each scenario or -1 (line-tripping contingencies,
+    §4.1.1): that scenario's admittances leave the line out."""
 
-    def __init__(self, net, pd, qd):
+    def __init__(self, net, pd, qd, trip=None):
         self.net = net
         self.lay = Layout(net)
-        self.Y = admittance(net)
         self.pd = np.atleast_2d(np.asarray(pd, dtype=np.float64))
+        N = self.pd.shape[0]
+        self.trip = None if trip is None else np.asarray(trip, dtype=np.int64)
+        self._Y, self._B = {}, {}
+        self.Y = admittance(net)
+        if self.lay.rated:
+            self.rate = np.asarray(net.rate, dtype=np.float64)
+        assert self.trip is None or self.trip.shape == (N,)
         self.qd = np.atleast_2d(np.asarray(qd, dtype=np.float64))
         self.N = self.pd.shape[0]
         L = self.lay
@@ -178,11 +264,37 @@ class Model:
         self.xu = np.concatenate([np.full(n - 1, inf), net.vmax[L.pq]])
         self.ul = np.concatenate([net.vmin[L.gen_bus], np.zeros(ng - 1)])
         self.uu = np.concatenate([net.vmax[L.gen_bus], net.pmax[1:]])
-        # h in [hmin, hmax]  ->  s = -h in [-hmax, -hmin]
+        # h in [hmin, hmax]  ->  s = -h in [-hmax, -hmin]; a flow row is
+        # bounded above only (|S|^2 <= rate^2)
         hmin = np.concatenate([-net.qmax, [0.0]])
         hmax = np.concatenate([net.qmax, [net.pmax[0]]])
+        if L.rated:
+            hmin = np.concatenate([hmin, np.full(2 * L.L, -inf)])
+            hmax = np.concatenate([hmax, np.tile(self.rate ** 2, 2)])
         self.sl = -hmax
         self.su = -hmin
+
+    def _on(self, i):
+        if self.trip is None or self.trip[i] < 0:
+            return None
+        on = np.ones(self.lay.L)
+        on[self.trip[i]] = 0.0
+        return on
+
+    def Y_of(self, i):
+        """Bus admittance matrix of scenario i."""
+        t = -1 if self.trip is None else int(self.trip[i])
+        if t not in self._Y:
+            self._Y[t] = admittance(self.net, self._on(i))
+        return self._Y[t]
+
+    def branches_of(self, i):
+        """((Y_f, C_f), (Y_t, C_t)) of scenario i."""
+        t = -1 if self.trip is None else int(self.trip[i])
+        if t not in self._B:
+            Yf, Yt, Cf, Ct = branch_admittance(self.net, self._on(i))
+            self._B[t] = ((Yf, Cf), (Yt, Ct))
+        return self._B[t]
 
     # -- functions -------------------------------------------------------
     def functions(self, i, x, u, cs=False):
@@ -192,9 +304,9 @@ class Model:
         n, ng = L.n, L.ng
         th, v = bus_voltage(L, x, u)
         if cs:
-            P, Q = injections_cs(self.Y, th, v)
+            P, Q = injections_cs(self.Y_of(i), th, v)
         else:
-            S = injections(self.Y, th, v)
+            S = injections(self.Y_of(i), th, v)
             P, Q = S.real, S.imag
         pd, qd = self.pd[i], self.qd[i]
         Pg = np.zeros(n, dtype=P.dtype)
@@ -202,8 +314,18 @@ class Model:
         gP = P + pd - Pg
         gQ = Q + qd
         g = np.concatenate([gP[1:], gQ[L.pq]])
-        h = np.concatenate([gQ[L.gen_bus], [P[0] + pd[0]]])
-        pg0 = h[-1]
+        pg0 = P[0] + pd[0]
+        h = np.concatenate([gQ[L.gen_bus], [pg0]])
+        if L.rated:
+            flows = []
+            for Yb, Cb in self.branches_of(i):
+                if cs:
+                    Pb, Qb = branch_flows_cs(Yb, Cb, th, v)
+                else:
+                    Sb = branch_flows(Yb, Cb, th, v)
+                    Pb, Qb = Sb.real, Sb.imag
+                flows.append(Pb * Pb + Qb * Qb)
+            h = np.concatenate([h] + flows)
         pg = u[ng:]
         cost = (np.sum(net.c2[1:] * pg * pg + net.c1[1:] * pg)
                 + net.c2[0] * pg0 * pg0 + net.c1[0] * pg0)
@@ -221,7 +343,7 @@ class Model:
         n, ng, N = L.n, L.ng, self.N
         f, g, h = self.functions(i, x, u)
         th, v = bus_voltage(L, x, u)
-        Sth, Sv = dS_da(self.Y, th, v)
+        Sth, Sv = dS_da(self.Y_of(i), th, v)
         J = sp.bmat([[Sth.real, Sv.real], [Sth.imag, Sv.imag]]).tocsr()  # 2n x 2n
         # column selectors (bus space -> x / u-voltage parts)
         Jx = J[:, L.x_in_a]
@@ -235,9 +357,30 @@ class Model:
         Gu = Ju[L.x_in_a, :]
         Hx = Jx[L.h_in_a, :]
         Hu = Juv[L.h_in_a, :]
+        if L.rated:
+            # flow rows: d|S_b|^2 = 2 (P dP + Q dQ) in bus space
+            th_, v_ = bus_voltage(L, x, u)
+            Hb, Wb = [], None
+            zf = z[ng + 1:ng + 1 + L.L]
+            zt = z[ng + 1 + L.L:]
+            for (Yb, Cb), zb in zip(self.branches_of(i), (zf, zt)):
+                Sb = branch_flows(Yb, Cb, th_, v_)
+                dth, dv = dSb_da(Yb, Cb, th_, v_)
+                dS = sp.hstack([dth, dv]).tocsr()          # L x 2n complex
+                dP, dQ = dS.real, dS.imag
+                Hb.append(2.0 * (sp.diags(Sb.real) @ dP + sp.diags(Sb.imag) @ dQ))
+                # Hessian of sum_l z_l |S_l|^2 = 2 sum z (dP dP^T + dQ dQ^T)
+                #   + Hessian of sum_l (2 z_l P_l) P_l + (2 z_l Q_l) Q_l (weights held)
+                mu_b = 2.0 * zb * (Sb.real - 1j * Sb.imag)
+                Wl = (2.0 * (dP.T @ sp.diags(zb) @ dP + dQ.T @ sp.diags(zb) @ dQ)
+                      + hess_re_vmv(Cb.T @ sp.diags(mu_b) @ Yb.conj(), th_, v_))
+                Wb = Wl if Wb is None else Wb + Wl
+            Hb = sp.vstack(Hb).tocsr()
+            Hx = sp.vstack([Hx, Hb[:, L.x_in_a]])
+            Hu = sp.vstack([Hu, Hb[:, L.uv_in_a]])
         Hu = sp.hstack([Hu, sp.csr_matrix((L.m, ng - 1))]).tocsr()
         # objective gradient
-        pg0 = h[-1]
+        pg0 = h[ng]
         dcost0 = (2 * net.c2[0] * pg0 + net.c1[0]) / N
         gradP0 = J[0, :].toarray().ravel()  # dP_0/da
         grad_a = dcost0 * gradP0
@@ -252,9 +395,11 @@ class Model:
         lamQ[L.pq] += y[n - 1:]
         lamQ[L.gen_bus] += z[:ng]
         lamP[0] += z[ng] + dcost0
-        Ha = hess_weighted_S(self.Y, th, v, lamP, lamQ)
+        Ha = hess_weighted_S(self.Y_of(i), th, v, lamP, lamQ)
         # cost curvature through the slack injection: (2 c2_0 / N) dP0 dP0^T
         Ha = Ha + (2 * net.c2[0] / N) * _outer_sparse(gradP0)
+        if L.rated:
+            Ha = (Ha + Wb).tocsr()
         Wxx = Ha[L.x_in_a, :][:, L.x_in_a]
         Wxuv = Ha[L.x_in_a, :][:, L.uv_in_a]
         Wuvuv = Ha[L.uv_in_a, :][:, L.uv_in_a]

@@ -11,6 +11,7 @@ constexpr int LU_LISTS = 1024;  // lists of trailing-block products of the LU fa
 
 struct DevSym {
   int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b, nlev_f, t0, nd, nlev_fs, nlev_bs;
+  int nflow;  // line-flow rows of h (2 L with ratings, else 0)
   const int *xth, *xv, *uv, *gen_of_bus, *xbus, *xkind;
   const int *lfr, *lto;
   const double *lg, *lb, *lbh;
@@ -34,6 +35,9 @@ struct DevSym {
       *zp_tslot;
   const double *xl, *xu, *ul, *uu, *sl, *su, *c2, *c1;
   const double *pd, *qd;  // [N][n]
+  // line status per (line, scenario), lon[l * N + sc] in {0, 1}, or null
+  // (every line in service): line-tripping contingencies
+  const double *lon;
 };
 
 // Dynamic per-iteration arrays (device).  Vectors are scenario-major
@@ -45,6 +49,10 @@ struct DevWork {
   // evaluation
   double *P, *Q, *g, *h, *fs;    // P,Q [N][n]; g [N][nx]; h [N][m]; fs [N]
   double *J, *W, *JTl;           // J,W [4 nnzA][N]; JTl [N][2n]
+  // line-flow rows (with ratings): d h / d (theta, v) of the row's own-end bus
+  // (w = 0) and other-end bus (w = 1), HF[((f * 2 + w) * 2 + kind) * N + sc]
+  // for flow row f = r - (n_g + 1)
+  double *HF;
   double *K;                     // [4 nnzKB][N]
   double *Sx, *Su, *Ss;          // barrier diagonals
   double *r1x, *r1u, *r2, *r4, *rh1x, *rh2, *tv;  // right-hand sides
@@ -92,6 +100,11 @@ __device__ __forceinline__ double bus_theta(const DevSym &S, const double *x, in
 __device__ __forceinline__ double bus_v(const DevSym &S, const double *x, const double *u, int sc, int i) {
   int q = S.xv[i];
   return q >= 0 ? x[(size_t)sc * S.nx + q] : u[S.uv[i]];
+}
+
+// other-end bus of line-flow row f (from-end rows first, then to-end rows)
+__device__ __forceinline__ int flow_other(const DevSym &S, int f) {
+  return f < S.L ? S.lto[f] : S.lfr[f - S.L];
 }
 
 // flags

@@ -100,6 +100,7 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   d.n = S.n; d.L = S.L; d.ng = S.ng; d.N = S.N; d.nx = S.nx; d.nu = S.nu; d.m = S.m;
   d.nnzA = S.nnzA; d.nnzKB = S.nnzKB; d.nnzLU = S.nnzLU; d.nlev = S.nlev; d.nlev_b = S.nlev_b;
   d.nlev_f = S.nlev_f; d.t0 = S.t0; d.nd = S.nd; d.nlev_fs = S.nlev_fs; d.nlev_bs = S.nlev_bs;
+  d.nflow = S.nflow;
   TRY(upload(c, &d.xth, S.xth)); TRY(upload(c, &d.xv, S.xv)); TRY(upload(c, &d.uv, S.uv));
   TRY(upload(c, &d.gen_of_bus, S.gen_of_bus)); TRY(upload(c, &d.xbus, S.xbus)); TRY(upload(c, &d.xkind, S.xkind));
   TRY(upload(c, &d.lfr, S.lfr)); TRY(upload(c, &d.lto, S.lto));
@@ -179,6 +180,8 @@ ipm_status alloc_work(ipm_ctx *c) {
   TRY(dalloc(c, &D.P, N * n)); TRY(dalloc(c, &D.Q, N * n)); TRY(dalloc(c, &D.g, N * nx));
   TRY(dalloc(c, &D.h, N * m)); TRY(dalloc(c, &D.fs, N));
   TRY(dalloc(c, &D.J, 4LL * S.nnzA * N)); TRY(dalloc(c, &D.W, 4LL * S.nnzA * N));
+  D.HF = nullptr;
+  if (S.nflow > 0) TRY(dalloc(c, &D.HF, 4LL * S.nflow * N));
   TRY(dalloc(c, &D.JTl, 2 * N * n)); TRY(dalloc(c, &D.K, 4LL * S.nnzKB * N));
   TRY(dalloc(c, &D.Sx, N * nx)); TRY(dalloc(c, &D.Su, nu)); TRY(dalloc(c, &D.Ss, N * m));
   TRY(dalloc(c, &D.r1x, N * nx)); TRY(dalloc(c, &D.r1u, nu)); TRY(dalloc(c, &D.r2, N * m));
@@ -1294,6 +1297,8 @@ void host_net(const ipm_network *net, HostNet &h) {
   h.pmax.assign(net->pmax, net->pmax + h.ng); h.qmax.assign(net->qmax, net->qmax + h.ng);
   h.c2.assign(net->c2, net->c2 + h.ng); h.c1.assign(net->c1, net->c1 + h.ng);
   h.vmin.assign(net->vmin, net->vmin + h.n); h.vmax.assign(net->vmax, net->vmax + h.n);
+  h.rate.clear();
+  if (net->rate) h.rate.assign(net->rate, net->rate + h.L);
 }
 
 extern "C" {
@@ -1592,8 +1597,26 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
         }
       }
     }
+    std::vector<double> HF;
+    if (S.nflow > 0) {
+      HF.resize((size_t)4 * S.nflow * N);
+      CK(cudaMemcpy(HF.data(), c->dw.HF, HF.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    }
     for (int r = 0; r < m; ++r) {
       const int g = S.hrow_bus[r], cp = S.hrow_comp[r];
+      if (cp >= 2) {  // line-flow row: its two end buses
+        const int f = r - S.ng - 1, l = f % S.L;
+        for (int w = 0; w < 2; ++w) {
+          const int b = w == 0 ? g : (f < S.L ? S.lto[l] : S.lfr[l]);
+          for (int kind = 0; kind < 2; ++kind) {
+            const double v = HF[((size_t)(f * 2 + w) * 2 + kind) * N + scen];
+            const int xi = kind == 0 ? S.xth[b] : S.xv[b];
+            if (xi >= 0) Hx[(size_t)r * nx + xi] = v;
+            else if (kind == 1) Hu[(size_t)r * nu + S.uv[b]] = v;
+          }
+        }
+        continue;
+      }
       for (int cidx = 0; cidx < nx; ++cidx) {
         const int s = aslot(g, S.xbus[cidx]);
         if (s >= 0) Hx[(size_t)r * nx + cidx] = jv(s, cp * 2 + S.xkind[cidx]);
@@ -1661,6 +1684,70 @@ ipm_status ipm_set_loads(ipm_ctx *c, const double *pd, const double *qd, void *s
   cudaStream_t st = STR(stream);
   CK(cudaMemcpyAsync(const_cast<double *>(c->ds.pd), pd, nl * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(const_cast<double *>(c->ds.qd), qd, nl * sizeof(double), cudaMemcpyHostToDevice, st));
+  return do_init(c, st);
+}
+
+ipm_status ipm_set_contingencies(ipm_ctx *c, const int *trip, void *stream) {
+  if (!c) return IPM_ERR_ARG;
+  const Sym &S = c->S;
+  const int N = S.N, L = S.L, n = S.n;
+  std::vector<double> on((size_t)L * N, 1.0);
+  if (trip) {
+    // bridges of the bus graph (depth-first low-link values): tripping one
+    // of them islands part of the network
+    std::vector<std::vector<std::pair<int, int>>> adj(n);
+    for (int l = 0; l < L; ++l) {
+      adj[S.lfr[l]].push_back({S.lto[l], l});
+      adj[S.lto[l]].push_back({S.lfr[l], l});
+    }
+    std::vector<int> disc(n, -1), low(n, 0);
+    std::vector<char> bridge(L, 0);
+    int t = 0;
+    for (int root = 0; root < n; ++root) {
+      if (disc[root] >= 0) continue;
+      struct Fr { int v, pl; size_t k; };
+      std::vector<Fr> stk;
+      disc[root] = low[root] = t++;
+      stk.push_back({root, -1, 0});
+      while (!stk.empty()) {
+        Fr &f = stk.back();
+        if (f.k == adj[f.v].size()) {
+          const int v = f.v, pl = f.pl;
+          stk.pop_back();
+          if (!stk.empty()) {
+            const int p = stk.back().v;
+            low[p] = std::min(low[p], low[v]);
+            if (low[v] > disc[p]) bridge[pl] = 1;
+          }
+          continue;
+        }
+        const auto e = adj[f.v][f.k++];
+        if (e.second == f.pl) continue;
+        if (disc[e.first] < 0) {
+          disc[e.first] = low[e.first] = t++;
+          stk.push_back({e.first, e.second, 0});
+        } else {
+          low[f.v] = std::min(low[f.v], disc[e.first]);
+        }
+      }
+    }
+    for (int s = 0; s < N; ++s) {
+      const int l = trip[s];
+      if (l < -1 || l >= L) return fail(c, IPM_ERR_ARG, "contingency line index out of range");
+      if (l >= 0 && bridge[l]) return fail(c, IPM_ERR_ARG, "tripping this line disconnects the network");
+      if (l >= 0) on[(size_t)l * N + s] = 0.0;
+    }
+  }
+  cudaStream_t st = STR(stream);
+  if (!c->ds.lon) {
+    const double *p = nullptr;
+    TRY(upload(c, &p, on));
+    c->ds.lon = p;
+  } else {
+    CK(cudaMemcpyAsync(const_cast<double *>(c->ds.lon), on.data(), on.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
   return do_init(c, st);
 }
 

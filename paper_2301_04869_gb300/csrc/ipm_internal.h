@@ -14,6 +14,7 @@ struct HostNet {
   int n = 0, L = 0, ng = 0;
   std::vector<int> fr, to, gen;
   std::vector<double> r, x, b, pmax, qmax, c2, c1, vmin, vmax;
+  std::vector<double> rate;  // [L] line ratings, or empty (no line-flow limits)
 };
 
 // Symbolic structures built once per network (S1).  Index conventions:
@@ -41,6 +42,10 @@ struct Sym {
   int nnzKB = 0;
   std::vector<int> kb_ptr, kb_col, kb_row, kb_aslot;
   std::vector<int> kbi_ptr, kbi_r, kbi_ja, kbi_jb;
+  // per h row: the bus and component of an injection row (comp 0 = P,
+  // 1 = Q), or for a line-flow row the bus of its end and comp 2 (from end)
+  // or 3 (to end); line-flow rows are n_g + 1 + e L + l (e = 0 from, 1 to)
+  int nflow = 0;                             // 2 L with ratings, else 0
   std::vector<int> hrow_bus, hrow_comp;      // per h row
   std::vector<int> ht_ptr, ht_r, ht_aslot;   // per bus: h rows touching it
   // static-pivot LU of G_x (positions)

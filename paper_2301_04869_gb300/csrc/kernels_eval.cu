@@ -8,7 +8,10 @@
 //   Q = -(b + b_c/2) v_m^2 - v_m v_o (g sin d - b cos d),   d = th_m - th_o
 // to the injections of its bus; derivatives below are those of these two
 // closed forms (the CPU oracle instead differentiates S = V conj(Y V) in
-// complex-matrix form).
+// complex-matrix form).  With line ratings, the line-flow rows of h
+// (§4.1.1) are h = P^2 + Q^2 of one line end, owned by the thread of that
+// end's bus: its first derivatives 2 (P dP + Q dQ) and the Hessian
+// 2 (dP dP^T + dQ dQ^T + P d2P + Q d2Q) come from the same closed forms.
 #include <atomic>
 
 #include "dev.cuh"
@@ -58,6 +61,41 @@ __device__ __forceinline__ double Qtovo(const LineEnd &e) { return e.vm * e.A; }
 __device__ __forceinline__ double Qvmvm(const LineEnd &e) { return -2.0 * e.bb; }
 __device__ __forceinline__ double Qvmvo(const LineEnd &e) { return -e.B; }
 
+// d2 P and d2 Q of a line end w.r.t. two of its variables, indexed
+// 0 = theta_m, 1 = v_m, 2 = theta_o, 3 = v_o (m: the end's bus, o: the other)
+__device__ __forceinline__ void d2PQ(const LineEnd &e, int a, int b, double &p, double &q) {
+  if (a > b) { const int t = a; a = b; b = t; }
+  const int k = a * 4 + b;
+  switch (k) {
+    case 0: p = Ptmtm(e); q = Qtmtm(e); break;   // tm tm
+    case 1: p = Ptmvm(e); q = Qtmvm(e); break;   // tm vm
+    case 2: p = Ptmto(e); q = Qtmto(e); break;   // tm to
+    case 3: p = Ptmvo(e); q = Qtmvo(e); break;   // tm vo
+    case 5: p = Pvmvm(e); q = Qvmvm(e); break;   // vm vm
+    case 6: p = Ptovm(e); q = Qtovm(e); break;   // vm to
+    case 7: p = Pvmvo(e); q = Qvmvo(e); break;   // vm vo
+    case 10: p = Ptoto(e); q = Qtoto(e); break;  // to to
+    case 11: p = Ptovo(e); q = Qtovo(e); break;  // to vo
+    default: p = 0.0; q = 0.0; break;            // vo vo: P, Q are linear in v_o
+  }
+}
+__device__ __forceinline__ double d1P(const LineEnd &e, int a) {
+  return a == 0 ? e.dPtm : a == 1 ? e.dPvm : a == 2 ? e.dPto : e.dPvo;
+}
+__device__ __forceinline__ double d1Q(const LineEnd &e, int a) {
+  return a == 0 ? e.dQtm : a == 1 ? e.dQvm : a == 2 ? e.dQto : e.dQvo;
+}
+// second derivative of h = P^2 + Q^2 of a line end
+__device__ __forceinline__ double d2flow(const LineEnd &e, int a, int b) {
+  double p2, q2;
+  d2PQ(e, a, b, p2, q2);
+  return 2.0 * (d1P(e, a) * d1P(e, b) + d1Q(e, a) * d1Q(e, b) + e.P * p2 + e.Q * q2);
+}
+// flow row of the end of line l at bus i (from-end rows first, then to-end rows)
+__device__ __forceinline__ int flow_row(const DevSym &S, int l, int i) {
+  return S.ng + 1 + (i == S.lfr[l] ? 0 : S.L) + l;
+}
+
 // multipliers of the P and Q injections of bus k in scenario sc: the g row
 // multiplier y, the h row multiplier z, and for the slack bus the cost slope
 // (f_i = cost/N depends on x through Pg_0 = P_0 + Pd_0).
@@ -85,9 +123,11 @@ __global__ void k_functions(DevSym S, const double *__restrict__ x, const double
     double sn, cs;
     sincos(thi - bus_theta(S, x, sc, k), &sn, &cs);
     LineEnd le;
-    line_end(vi, bus_v(S, x, u, sc, k), cs, sn, S.lg[l], S.lb[l], S.lbh[l], le);
+    const double on = S.lon ? S.lon[(size_t)l * S.N + sc] : 1.0;  // 0: line out of service
+    line_end(vi, bus_v(S, x, u, sc, k), cs, sn, on * S.lg[l], on * S.lb[l], on * S.lbh[l], le);
     p += le.P;
     q += le.Q;
+    if (S.nflow) h[(size_t)sc * S.m + flow_row(S, l, i)] = le.P * le.P + le.Q * le.Q;
   }
   const size_t bi = (size_t)sc * S.n + i;
   P[bi] = p;
@@ -106,7 +146,7 @@ __global__ void k_functions(DevSym S, const double *__restrict__ x, const double
 
 __global__ void k_derivatives(DevSym S, const double *__restrict__ x, const double *__restrict__ u,
                               const double *__restrict__ y, const double *__restrict__ z,
-                              const double *__restrict__ h, double *J, double *W, double *JTl) {
+                              const double *__restrict__ h, double *J, double *W, double *JTl, double *HF) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= S.n * S.N) return;
   const int i = t / S.N, sc = t - i * S.N, N = S.N;
@@ -121,8 +161,12 @@ __global__ void k_derivatives(DevSym S, const double *__restrict__ x, const doub
     double sn, cs;
     sincos(thi - bus_theta(S, x, sc, k), &sn, &cs);
     LineEnd own, oth;
-    line_end(vi, vk, cs, sn, S.lg[l], S.lb[l], S.lbh[l], own);
-    line_end(vk, vi, cs, -sn, S.lg[l], S.lb[l], S.lbh[l], oth);
+    // a line out of service (contingency) stamps nothing: every quantity of a
+    // line end is linear in its admittances g, b, b_c/2
+    const double on = S.lon ? S.lon[(size_t)l * N + sc] : 1.0;
+    const double lg = on * S.lg[l], lb = on * S.lb[l], lbh = on * S.lbh[l];
+    line_end(vi, vk, cs, sn, lg, lb, lbh, own);
+    line_end(vk, vi, cs, -sn, lg, lb, lbh, oth);
     const double lPk = lam_P(S, y, z, h, sc, k), lQk = lam_Q(S, y, z, sc, k);
     jd0 += own.dPtm; jd1 += own.dPvm; jd2 += own.dQtm; jd3 += own.dQvm;
     J[((size_t)q * 4 + 0) * N + sc] = own.dPto;
@@ -138,6 +182,26 @@ __global__ void k_derivatives(DevSym S, const double *__restrict__ x, const doub
     W[((size_t)q * 4 + 3) * N + sc] = lPi * Pvmvo(own) + lQi * Qvmvo(own) + lPk * Pvmvo(oth) + lQk * Qvmvo(oth);
     gt += lPi * own.dPtm + lQi * own.dQtm + lPk * oth.dPto + lQk * oth.dQto;
     gv += lPi * own.dPvm + lQi * own.dQvm + lPk * oth.dPvo + lQk * oth.dQvo;
+    if (S.nflow) {
+      // flow rows of both ends of line l: h_own (this thread's row) and h_oth;
+      // row i of W and of J^T lambda gets the terms in (theta_i, v_i)
+      const int ro = flow_row(S, l, i), rk = flow_row(S, l, k);
+      const double zo = z[(size_t)sc * S.m + ro], zk = z[(size_t)sc * S.m + rk];
+      const int fo = ro - S.ng - 1;
+      for (int a = 0; a < 4; ++a)
+        HF[((size_t)(fo * 2 + (a >> 1)) * 2 + (a & 1)) * N + sc] =
+            2.0 * (own.P * d1P(own, a) + own.Q * d1Q(own, a));
+      // own end: i is m (0, 1), k is o (2, 3); other end: i is o, k is m
+      gt += zo * 2.0 * (own.P * own.dPtm + own.Q * own.dQtm) + zk * 2.0 * (oth.P * oth.dPto + oth.Q * oth.dQto);
+      gv += zo * 2.0 * (own.P * own.dPvm + own.Q * own.dQvm) + zk * 2.0 * (oth.P * oth.dPvo + oth.Q * oth.dQvo);
+      wtt += zo * d2flow(own, 0, 0) + zk * d2flow(oth, 2, 2);
+      wtv += zo * d2flow(own, 0, 1) + zk * d2flow(oth, 2, 3);
+      wvv += zo * d2flow(own, 1, 1) + zk * d2flow(oth, 3, 3);
+      W[((size_t)q * 4 + 0) * N + sc] += zo * d2flow(own, 0, 2) + zk * d2flow(oth, 2, 0);
+      W[((size_t)q * 4 + 1) * N + sc] += zo * d2flow(own, 0, 3) + zk * d2flow(oth, 2, 1);
+      W[((size_t)q * 4 + 2) * N + sc] += zo * d2flow(own, 1, 2) + zk * d2flow(oth, 3, 0);
+      W[((size_t)q * 4 + 3) * N + sc] += zo * d2flow(own, 1, 3) + zk * d2flow(oth, 3, 1);
+    }
   }
   const int d = S.a_diag[i];
   J[((size_t)d * 4 + 0) * N + sc] = jd0;
@@ -198,10 +262,18 @@ __global__ void k_condense(DevSym S, DevWork D) {
     const int r = S.kbi_r[e], c = S.hrow_comp[r], ja = S.kbi_ja[e], jb = S.kbi_jb[e];
     double w = D.Ss[(size_t)sc * S.m + r];
     if (r == S.ng) w += 2.0 * S.c2[0] / N;
-    const double ha0 = D.J[((size_t)ja * 4 + c * 2 + 0) * N + sc];
-    const double ha1 = D.J[((size_t)ja * 4 + c * 2 + 1) * N + sc];
-    const double hb0 = D.J[((size_t)jb * 4 + c * 2 + 0) * N + sc];
-    const double hb1 = D.J[((size_t)jb * 4 + c * 2 + 1) * N + sc];
+    double ha0, ha1, hb0, hb1;
+    if (c < 2) {
+      ha0 = D.J[((size_t)ja * 4 + c * 2 + 0) * N + sc];
+      ha1 = D.J[((size_t)ja * 4 + c * 2 + 1) * N + sc];
+      hb0 = D.J[((size_t)jb * 4 + c * 2 + 0) * N + sc];
+      hb1 = D.J[((size_t)jb * 4 + c * 2 + 1) * N + sc];
+    } else {  // line-flow row: ja, jb index HF
+      ha0 = D.HF[((size_t)ja * 2 + 0) * N + sc];
+      ha1 = D.HF[((size_t)ja * 2 + 1) * N + sc];
+      hb0 = D.HF[((size_t)jb * 2 + 0) * N + sc];
+      hb1 = D.HF[((size_t)jb * 2 + 1) * N + sc];
+    }
     k0 += w * ha0 * hb0;
     k1 += w * ha0 * hb1;
     k2 += w * ha1 * hb0;
@@ -231,12 +303,14 @@ __global__ void k_rhs_s(DevSym S, DevWork D, const double *mu_d) {
 }
 
 // (H^T v) at bus variable (a, kind) of scenario sc
-__device__ __forceinline__ double HT_at(const DevSym &S, const double *J, const double *v, int sc,
-                                        int a, int kind) {
+__device__ __forceinline__ double HT_at(const DevSym &S, const double *J, const double *HF, const double *v,
+                                        int sc, int a, int kind) {
   double acc = 0.0;
   for (int e = S.ht_ptr[a]; e < S.ht_ptr[a + 1]; ++e) {
-    const int r = S.ht_r[e];
-    acc += v[(size_t)sc * S.m + r] * J[((size_t)S.ht_aslot[e] * 4 + S.hrow_comp[r] * 2 + kind) * S.N + sc];
+    const int r = S.ht_r[e], c = S.hrow_comp[r];
+    const double hv = c < 2 ? J[((size_t)S.ht_aslot[e] * 4 + c * 2 + kind) * S.N + sc]
+                            : HF[((size_t)S.ht_aslot[e] * 2 + kind) * S.N + sc];
+    acc += v[(size_t)sc * S.m + r] * hv;
   }
   return acc;
 }
@@ -250,7 +324,7 @@ __global__ void k_rhs_x(DevSym S, DevWork D, const double *mu_d) {
   const int a = S.xbus[j], kind = S.xkind[j];
   const double r1 = D.JTl[(size_t)sc * 2 * S.n + kind * S.n + a] + bgrad_of(D.x[t], S.xl[j], S.xu[j], mu);
   D.r1x[t] = r1;
-  D.rh1x[t] = r1 + HT_at(S, D.J, D.tv, sc, a, kind);
+  D.rh1x[t] = r1 + HT_at(S, D.J, D.HF, D.tv, sc, a, kind);
 }
 
 // u gradient of sum_i (f_i + y_i^T g_i + z_i^T h_i), summed over scenarios in
@@ -263,7 +337,7 @@ __global__ void k_ugrad(DevSym S, DevWork D, double *gLu, double *HTt_u) {
     const int a = S.hrow_bus[j];
     for (int sc = 0; sc < S.N; ++sc) {
       acc += D.JTl[(size_t)sc * 2 * S.n + S.n + a];
-      if (HTt_u) acc2 += HT_at(S, D.J, D.tv, sc, a, 1);
+      if (HTt_u) acc2 += HT_at(S, D.J, D.HF, D.tv, sc, a, 1);
     }
   } else {
     const int k = j - S.ng + 1, a = S.hrow_bus[k];
@@ -294,7 +368,7 @@ void launch_functions(const DevSym &S, const double *x, const double *u, double 
   k_functions<<<nblk((long long)S.n * S.N, 128), 128, 0, st>>>(S, x, u, P, Q, g, h, fs); ipm_count_launch();
 }
 void launch_derivatives(const DevSym &S, DevWork &D, cudaStream_t st) {
-  k_derivatives<<<nblk((long long)S.n * S.N, 128), 128, 0, st>>>(S, D.x, D.u, D.y, D.z, D.h, D.J, D.W, D.JTl); ipm_count_launch();
+  k_derivatives<<<nblk((long long)S.n * S.N, 128), 128, 0, st>>>(S, D.x, D.u, D.y, D.z, D.h, D.J, D.W, D.JTl, D.HF); ipm_count_launch();
 }
 void launch_sigmas(const DevSym &S, DevWork &D, cudaStream_t st) {
   long long tot = (long long)S.N * S.nx + (long long)S.N * S.m + S.nu;

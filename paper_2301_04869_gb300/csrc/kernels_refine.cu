@@ -13,7 +13,8 @@
 //   (W + Sigma_p) p_d = K p_d - H^T (Sigma_s H p_d)
 // and rho_d = -r1 - K p_d - delta p_d - G^T p_y - H^T (p_z - Sigma_s H p_d).
 // Every product here walks the Jacobian values J stored per bus-adjacency
-// slot, in a fixed order (no atomics): thread per (scenario, row).
+// slot (and the line-flow rows' HF), in a fixed order (no atomics): thread
+// per (scenario, row).
 #include "dev.cuh"
 #include "kernels.h"
 
@@ -34,14 +35,34 @@ __device__ __forceinline__ double row_mult(const DevSym &S, const double *ly, co
 
 // (G^T ly + H^T lz) at bus variable (a, kind) of scenario sc: every row
 // (i, c) with i adjacent to a (or a itself) contributes dF_(i,c)/d(a,kind)
-// times its multiplier.  The Pg columns are handled by the callers.
-__device__ __forceinline__ double jt_at(const DevSym &S, const double *J, const double *ly, const double *lz,
+// times its multiplier, and so does every line-flow row with an end at a.
+// The Pg columns are handled by the callers.
+__device__ __forceinline__ double jt_at(const DevSym &S, const DevWork &D, const double *ly, const double *lz,
                                         int sc, int a, int kind) {
   double acc = 0.0;
   for (int q = S.a_ptr[a]; q < S.a_ptr[a + 1]; ++q) {
     const int i = S.a_col[q], tq = S.a_tslot[q];
-    acc += J[((size_t)tq * 4 + 0 * 2 + kind) * S.N + sc] * row_mult(S, ly, lz, sc, i, 0);
-    acc += J[((size_t)tq * 4 + 1 * 2 + kind) * S.N + sc] * row_mult(S, ly, lz, sc, i, 1);
+    acc += D.J[((size_t)tq * 4 + 0 * 2 + kind) * S.N + sc] * row_mult(S, ly, lz, sc, i, 0);
+    acc += D.J[((size_t)tq * 4 + 1 * 2 + kind) * S.N + sc] * row_mult(S, ly, lz, sc, i, 1);
+  }
+  if (S.nflow)
+    for (int e = S.ht_ptr[a]; e < S.ht_ptr[a + 1]; ++e) {
+      const int r = S.ht_r[e];
+      if (S.hrow_comp[r] < 2) continue;
+      acc += D.HF[((size_t)S.ht_aslot[e] * 2 + kind) * S.N + sc] * lz[(size_t)sc * S.m + r];
+    }
+  return acc;
+}
+
+// (H p_d) of line-flow row f of scenario sc
+__device__ __forceinline__ double flowrow(const DevSym &S, const double *HF, const double *px, const double *pu,
+                                          int sc, int f, int own) {
+  double acc = 0.0;
+  for (int w = 0; w < 2; ++w) {
+    const int b = w == 0 ? own : flow_other(S, f);
+    const double pth = b >= 1 ? px[(size_t)sc * S.nx + S.xth[b]] : 0.0;
+    const double pv = S.xv[b] >= 0 ? px[(size_t)sc * S.nx + S.xv[b]] : pu[S.uv[b]];
+    acc += HF[((size_t)(f * 2 + w) * 2 + 0) * S.N + sc] * pth + HF[((size_t)(f * 2 + w) * 2 + 1) * S.N + sc] * pv;
   }
   return acc;
 }
@@ -67,7 +88,8 @@ __global__ void k_res_h(DevSym S, DevWork D, const double *px, const double *pu,
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)S.N * S.m) return;
   const int sc = (int)(t / S.m), r = (int)(t - (long long)sc * S.m);
-  const double hp = jrow(S, D.J, px, pu, sc, S.hrow_bus[r], S.hrow_comp[r]);
+  const double hp = S.hrow_comp[r] < 2 ? jrow(S, D.J, px, pu, sc, S.hrow_bus[r], S.hrow_comp[r])
+                                       : flowrow(S, D.HF, px, pu, sc, r - S.ng - 1, S.hrow_bus[r]);
   Hp[t] = hp;
   rho2[t] = -D.r2[t] - D.Ss[t] * ps[t] - pz[t];
   rho4[t] = -D.r4[t] - hp - ps[t];
@@ -84,7 +106,7 @@ __global__ void k_res_x(DevSym S, DevWork D, double delta, const double *px, con
   const int a = S.xbus[j], kind = S.xkind[j];
   rho3[t] = -D.g[t] - jrow(S, D.J, px, pu, sc, a, kind);
   const double kp = kpx_pos[(size_t)sc * S.nx + S.perm[j]];
-  rho1x[t] = -D.r1x[t] - kp - delta * px[t] - jt_at(S, D.J, py, tw, sc, a, kind);
+  rho1x[t] = -D.r1x[t] - kp - delta * px[t] - jt_at(S, D, py, tw, sc, a, kind);
 }
 
 // u rows (scenarios summed in index order):
@@ -96,7 +118,7 @@ __global__ void k_res_u(DevSym S, DevWork D, double delta, const double *pu, con
   double acc = 0.0;
   if (j < S.ng) {
     const int a = S.hrow_bus[j];  // generator j's bus; v there is u_j
-    for (int sc = 0; sc < S.N; ++sc) acc += kpu[(size_t)sc * S.nu + j] + jt_at(S, D.J, py, tw, sc, a, 1);
+    for (int sc = 0; sc < S.N; ++sc) acc += kpu[(size_t)sc * S.nu + j] + jt_at(S, D, py, tw, sc, a, 1);
   } else {
     const int k = j - S.ng + 1, a = S.hrow_bus[k];
     for (int sc = 0; sc < S.N; ++sc) acc += kpu[(size_t)sc * S.nu + j] - row_mult(S, py, tw, sc, a, 0);
@@ -109,7 +131,7 @@ __global__ void k_htv_x(DevSym S, DevWork D, const double *a, const double *v, d
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)S.N * S.nx) return;
   const int sc = (int)(t / S.nx), j = (int)(t - (long long)sc * S.nx);
-  out[t] = a[t] + jt_at(S, D.J, nullptr, v, sc, S.xbus[j], S.xkind[j]);
+  out[t] = a[t] + jt_at(S, D, nullptr, v, sc, S.xbus[j], S.xkind[j]);
 }
 
 // u rows of the same, summed over scenarios: out = a + sum_i H_u^T v_i
@@ -119,7 +141,7 @@ __global__ void k_htv_u(DevSym S, DevWork D, const double *a, const double *v, d
   double acc = 0.0;
   if (j < S.ng) {
     const int bus = S.hrow_bus[j];
-    for (int sc = 0; sc < S.N; ++sc) acc += jt_at(S, D.J, nullptr, v, sc, bus, 1);
+    for (int sc = 0; sc < S.N; ++sc) acc += jt_at(S, D, nullptr, v, sc, bus, 1);
   } else {
     const int k = j - S.ng + 1, bus = S.hrow_bus[k];
     for (int sc = 0; sc < S.N; ++sc) acc -= row_mult(S, nullptr, v, sc, bus, 0);
@@ -140,7 +162,8 @@ __global__ void k_pzps_rhs(DevSym S, DevWork D, const double *px, const double *
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)S.N * S.m) return;
   const int sc = (int)(t / S.m), r = (int)(t - (long long)sc * S.m);
-  const double hp = jrow(S, D.J, px, pu, sc, S.hrow_bus[r], S.hrow_comp[r]);
+  const double hp = S.hrow_comp[r] < 2 ? jrow(S, D.J, px, pu, sc, S.hrow_bus[r], S.hrow_comp[r])
+                                       : flowrow(S, D.HF, px, pu, sc, r - S.ng - 1, S.hrow_bus[r]);
   const double z = D.Ss[t] * (hp + r4[t]) - r2[t];
   pz[t] = z;
   ps[t] = -(r2[t] + z) / D.Ss[t];

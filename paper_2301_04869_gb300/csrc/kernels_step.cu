@@ -420,11 +420,21 @@ __global__ void k_pz_ps(DevSym S, DevWork D, const double *px, const double *pu,
   const int sc = (int)(t / S.m), r = (int)(t - (long long)sc * S.m);
   const int gb = S.hrow_bus[r], c = S.hrow_comp[r];
   double acc = 0.0;
-  for (int q = S.a_ptr[gb]; q < S.a_ptr[gb + 1]; ++q) {
-    const int b = S.a_col[q];
-    const double pth = b >= 1 ? px[(size_t)sc * S.nx + S.xth[b]] : 0.0;
-    const double pv = S.xv[b] >= 0 ? px[(size_t)sc * S.nx + S.xv[b]] : pu[S.uv[b]];
-    acc += D.J[((size_t)q * 4 + c * 2 + 0) * S.N + sc] * pth + D.J[((size_t)q * 4 + c * 2 + 1) * S.N + sc] * pv;
+  if (c < 2) {
+    for (int q = S.a_ptr[gb]; q < S.a_ptr[gb + 1]; ++q) {
+      const int b = S.a_col[q];
+      const double pth = b >= 1 ? px[(size_t)sc * S.nx + S.xth[b]] : 0.0;
+      const double pv = S.xv[b] >= 0 ? px[(size_t)sc * S.nx + S.xv[b]] : pu[S.uv[b]];
+      acc += D.J[((size_t)q * 4 + c * 2 + 0) * S.N + sc] * pth + D.J[((size_t)q * 4 + c * 2 + 1) * S.N + sc] * pv;
+    }
+  } else {  // line-flow row: its two end buses
+    const int f = r - S.ng - 1;
+    for (int w = 0; w < 2; ++w) {
+      const int b = w == 0 ? gb : flow_other(S, f);
+      const double pth = b >= 1 ? px[(size_t)sc * S.nx + S.xth[b]] : 0.0;
+      const double pv = S.xv[b] >= 0 ? px[(size_t)sc * S.nx + S.xv[b]] : pu[S.uv[b]];
+      acc += D.HF[((size_t)(f * 2 + w) * 2 + 0) * S.N + sc] * pth + D.HF[((size_t)(f * 2 + w) * 2 + 1) * S.N + sc] * pv;
+    }
   }
   Hp[t] = acc;
   const double z = D.Ss[t] * (acc + D.r4[t]) - D.r2[t];

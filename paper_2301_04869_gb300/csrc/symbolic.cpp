@@ -93,9 +93,11 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
     if (S.gen_of_bus[g] >= 0) { err = "two generators on one bus"; return false; }
     S.gen_of_bus[g] = k;
   }
+  if (!net.rate.empty() && (int)net.rate.size() != L) { err = "bad rate array size"; return false; }
   for (int l = 0; l < L; ++l) {
     int a = net.fr[l], b = net.to[l];
     if (a < 0 || a >= n || b < 0 || b >= n || a == b) { err = "bad line endpoints"; return false; }
+    if (!net.rate.empty() && !(net.rate[l] > 0 && std::isfinite(net.rate[l]))) { err = "bad line rating"; return false; }
     double z2 = net.r[l] * net.r[l] + net.x[l] * net.x[l];
     if (!(z2 > 0) || !std::isfinite(z2) || !std::isfinite(net.b[l])) { err = "bad line impedance"; return false; }
   }
@@ -107,7 +109,8 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
     if (S.gen_of_bus[i] < 0) S.xv[i] = nx++;
   S.nx = nx;
   S.nu = 2 * ng - 1;
-  S.m = ng + 1;
+  S.nflow = net.rate.empty() ? 0 : 2 * L;
+  S.m = ng + 1 + S.nflow;
   for (int k = 0; k < ng; ++k) S.uv[net.gen[k]] = k;
   S.xbus.assign(nx, -1); S.xkind.assign(nx, -1);
   for (int i = 0; i < n; ++i) {
@@ -175,15 +178,37 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   S.hrow_bus.resize(S.m); S.hrow_comp.resize(S.m);
   for (int k = 0; k < ng; ++k) { S.hrow_bus[k] = net.gen[k]; S.hrow_comp[k] = 1; }
   S.hrow_bus[ng] = 0; S.hrow_comp[ng] = 0;
+  // line-flow rows (§4.1.1): |S|^2 at the from end of every line, then at the to end
+  for (int f = 0; f < S.nflow; ++f) {
+    const int l = f % L;
+    S.hrow_bus[ng + 1 + f] = f < L ? net.fr[l] : net.to[l];
+    S.hrow_comp[ng + 1 + f] = f < L ? 2 : 3;
+  }
+  // buses an h row depends on, and the H-value index of each: an injection
+  // row touches the A row of its bus (index: the A slot), a flow row its two
+  // end buses (index f * 2 + w, w = 0 own end, 1 other end)
+  auto hrow_touch = [&](int r, std::vector<std::pair<int, int>> &tb) {
+    tb.clear();
+    if (r <= ng) {
+      const int g = S.hrow_bus[r];
+      for (int p = S.a_ptr[g]; p < S.a_ptr[g + 1]; ++p) tb.push_back({S.a_col[p], p});
+    } else {
+      const int f = r - ng - 1, l = f % L;
+      const int own = f < L ? net.fr[l] : net.to[l], oth = f < L ? net.to[l] : net.fr[l];
+      tb.push_back({own, f * 2 + 0});
+      tb.push_back({oth, f * 2 + 1});
+    }
+  };
+  std::vector<std::pair<int, int>> tb;
   // nbhd(g) = {g} u nbr(g), i.e. A row g
   // ---- KB pattern ----
   std::vector<std::map<int, std::vector<int>>> kb(n);  // row bus -> col bus -> h rows
   for (int i = 0; i < n; ++i)
     for (int p = S.a_ptr[i]; p < S.a_ptr[i + 1]; ++p) kb[i][S.a_col[p]];
   for (int r = 0; r < S.m; ++r) {
-    int g = S.hrow_bus[r];
-    for (int p = S.a_ptr[g]; p < S.a_ptr[g + 1]; ++p)
-      for (int q = S.a_ptr[g]; q < S.a_ptr[g + 1]; ++q) kb[S.a_col[p]][S.a_col[q]].push_back(r);
+    hrow_touch(r, tb);
+    for (auto &pa : tb)
+      for (auto &pb : tb) kb[pa.first][pb.first].push_back(r);
   }
   S.kb_ptr.assign(n + 1, 0);
   S.kbi_ptr.push_back(0);
@@ -194,10 +219,15 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
       S.kb_row.push_back(i);
       S.kb_aslot.push_back(aslot(i, j));
       for (int r : kv.second) {
-        int g = S.hrow_bus[r];
+        hrow_touch(r, tb);
+        int ja = -1, jb = -1;
+        for (auto &pa : tb) {
+          if (pa.first == i) ja = pa.second;
+          if (pa.first == j) jb = pa.second;
+        }
         S.kbi_r.push_back(r);
-        S.kbi_ja.push_back(aslot(g, i));
-        S.kbi_jb.push_back(aslot(g, j));
+        S.kbi_ja.push_back(ja);
+        S.kbi_jb.push_back(jb);
       }
       S.kbi_ptr.push_back((int)S.kbi_r.size());
     }
@@ -214,8 +244,8 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   {
     std::vector<std::vector<std::pair<int, int>>> ht(n);
     for (int r = 0; r < S.m; ++r) {
-      int g = S.hrow_bus[r];
-      for (int p = S.a_ptr[g]; p < S.a_ptr[g + 1]; ++p) ht[S.a_col[p]].push_back({r, p});
+      hrow_touch(r, tb);
+      for (auto &pa : tb) ht[pa.first].push_back({r, pa.second});
     }
     S.ht_ptr.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) {
@@ -616,6 +646,12 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   S.sl.assign(S.m, 0.0); S.su.assign(S.m, 0.0);
   for (int k = 0; k < ng; ++k) { S.sl[k] = -net.qmax[k]; S.su[k] = net.qmax[k]; }
   S.sl[ng] = -net.pmax[0]; S.su[ng] = -0.0;
+  // flow rows: h = |S|^2 <= rate^2 only, so s = -h in [-rate^2, +inf)
+  for (int f = 0; f < S.nflow; ++f) {
+    const double rt = net.rate[f % L];
+    S.sl[ng + 1 + f] = -rt * rt;
+    S.su[ng + 1 + f] = inf;
+  }
   S.c2 = net.c2; S.c1 = net.c1; S.pmax = net.pmax; S.qmax = net.qmax;
   return true;
 }

@@ -41,7 +41,7 @@ class Network(ctypes.Structure):
     _fields_ = [("n_bus", ctypes.c_int), ("n_line", ctypes.c_int), ("n_gen", ctypes.c_int),
                 ("from_", _I), ("to", _I), ("gen_bus", _I),
                 ("r", _D), ("x", _D), ("b", _D), ("pmax", _D), ("qmax", _D),
-                ("c2", _D), ("c1", _D), ("vmin", _D), ("vmax", _D)]
+                ("c2", _D), ("c1", _D), ("vmin", _D), ("vmax", _D), ("rate", _D)]
 
 
 BARRIER_MONOTONE, BARRIER_ADAPTIVE = 0, 1
@@ -93,6 +93,7 @@ def load():
         "ipm_get_quantity": (c_int, [vp, c_int, c_int, _D, c_ll, vp]),
         "ipm_set_profiling": (c_int, [vp, c_int]),
         "ipm_set_loads": (c_int, [vp, _D, _D, vp]),
+        "ipm_set_contingencies": (c_int, [vp, _I, vp]),
         "ipm_mlp_create": (c_int, [c_int, c_int, c_int, c_int, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
         "ipm_mlp_destroy": (c_int, [vp]),
         "ipm_mlp_param_count": (c_ll, [vp]),
@@ -183,13 +184,17 @@ def _cnet(net):
         pmax=np.ascontiguousarray(net.pmax, dtype=np.float64), qmax=np.ascontiguousarray(net.qmax, dtype=np.float64),
         c2=np.ascontiguousarray(net.c2, dtype=np.float64), c1=np.ascontiguousarray(net.c1, dtype=np.float64),
         vmin=np.ascontiguousarray(net.vmin, dtype=np.float64), vmax=np.ascontiguousarray(net.vmax, dtype=np.float64))
+    rate = getattr(net, "rate", None)
+    if rate is not None:
+        keep["rate"] = np.ascontiguousarray(rate, dtype=np.float64)
     k = keep
     cnet = Network(int(net.n_bus), int(k["fr"].size), int(k["gen"].size),
                    _ptr(k["fr"], ctypes.c_int), _ptr(k["to"], ctypes.c_int), _ptr(k["gen"], ctypes.c_int),
                    _ptr(k["r"], ctypes.c_double), _ptr(k["x"], ctypes.c_double), _ptr(k["b"], ctypes.c_double),
                    _ptr(k["pmax"], ctypes.c_double), _ptr(k["qmax"], ctypes.c_double),
                    _ptr(k["c2"], ctypes.c_double), _ptr(k["c1"], ctypes.c_double),
-                   _ptr(k["vmin"], ctypes.c_double), _ptr(k["vmax"], ctypes.c_double))
+                   _ptr(k["vmin"], ctypes.c_double), _ptr(k["vmax"], ctypes.c_double),
+                   _ptr(k["rate"], ctypes.c_double) if "rate" in k else None)
     return keep, cnet
 
 
@@ -316,6 +321,15 @@ class Solver:
         assert pd.shape == (self.N, self.dims.n_bus) and qd.shape == pd.shape
         self._check(self._lib.ipm_set_loads(self._h, _ptr(pd, ctypes.c_double), _ptr(qd, ctypes.c_double),
                                             _stream(stream)))
+
+    def ipm_set_contingencies(self, trip, stream=None):
+        """trip: int per scenario (line out of service, -1 none) or None."""
+        if trip is None:
+            self._check(self._lib.ipm_set_contingencies(self._h, None, _stream(stream)))
+            return
+        t = np.ascontiguousarray(trip, dtype=np.int32)
+        assert t.shape == (self.N,)
+        self._check(self._lib.ipm_set_contingencies(self._h, _ptr(t, ctypes.c_int), _stream(stream)))
 
     def ipm_get_quantity(self, which, scen=0, stream=None):
         d = self.dims

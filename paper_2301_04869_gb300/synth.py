@@ -37,6 +37,8 @@ class Network:
       c2, c1      float64[n_g] quadratic cost coefficients
       vmin, vmax  float64[n]
       pd0, qd0    float64[n] base loads
+      rate        float64[L] apparent-power rating of every line, or None
+                  (no line-flow limits; see ``with_ratings``)
     """
     n_bus: int
     fr: np.ndarray
@@ -55,6 +57,7 @@ class Network:
     qd0: np.ndarray
     load_bus: np.ndarray
     seed: int = 0
+    rate: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
 
     @property
@@ -153,6 +156,87 @@ def make_network(n_bus: int, n_gen: int | None = None, seed: int = 0,
                    pmax=pmax, qmax=qmax, c2=c2, c1=c1,
                    vmin=np.full(n, 0.9), vmax=np.full(n, 1.1),
                    pd0=pd0, qd0=qd0, load_bus=load_bus, seed=seed)
+
+
+def with_ratings(net: Network, flows: np.ndarray, factor: float = 1.2, floor: float = 0.05,
+                 tight: int = 0, tight_factor: float = 0.9) -> Network:
+    """A copy of ``net`` with line ratings (the operational limits of §4.1.1,
+    |S| <= rate at both ends of every line).  The paper's MATPOWER cases carry
+    their own ratings; here they are drawn from a reference flow: ``flows``
+    (float64[L], e.g. the larger end's apparent power at an unconstrained
+    optimum) times ``factor``, at least ``floor`` pu, and the ``tight`` most
+    loaded lines get ``tight_factor`` times their flow instead, so that those
+    limits bind.  Only the ratings are new; every other array is shared."""
+    import copy
+    flows = np.asarray(flows, dtype=np.float64)
+    rate = np.maximum(factor * flows, floor)
+    if tight > 0:
+        top = np.argsort(-flows, kind="stable")[:tight]
+        rate[top] = np.maximum(tight_factor * flows[top], floor)
+    out = copy.copy(net)
+    out.rate = rate
+    out.meta = dict(net.meta)
+    return out
+
+
+def bridges(net: Network) -> np.ndarray:
+    """Boolean mask of the lines whose loss disconnects the network (graph
+    bridges, by depth-first search low-link values)."""
+    n, L = net.n_bus, net.n_line
+    adj = [[] for _ in range(n)]
+    for l in range(L):
+        a, b = int(net.fr[l]), int(net.to[l])
+        adj[a].append((b, l))
+        adj[b].append((a, l))
+    disc = [-1] * n
+    low = [0] * n
+    out = np.zeros(L, dtype=bool)
+    t = 0
+    for root in range(n):
+        if disc[root] >= 0:
+            continue
+        disc[root] = low[root] = t
+        t += 1
+        stack = [(root, -1, iter(adj[root]))]
+        while stack:
+            v, pl, it = stack[-1]
+            nxt = next(it, None)
+            if nxt is None:
+                stack.pop()
+                if stack:
+                    p = stack[-1][0]
+                    low[p] = min(low[p], low[v])
+                    if low[v] > disc[p]:
+                        out[pl] = True
+                continue
+            w, l = nxt
+            if l == pl:
+                continue
+            if disc[w] < 0:
+                disc[w] = low[w] = t
+                t += 1
+                stack.append((w, l, iter(adj[w])))
+            else:
+                low[v] = min(low[v], disc[w])
+    return out
+
+
+def make_contingencies(net: Network, n_scen: int, frac: float = 0.5, seed: int = 2) -> np.ndarray:
+    """Line-tripping contingencies (§4.1.1: a scenario carries its loads and
+    potential line trips): scenario 0 keeps the intact network; each other
+    scenario, with probability ``frac``, loses one line drawn uniformly from
+    the lines whose loss keeps the network connected.  Returns int32[n_scen],
+    the tripped line or -1."""
+    rng = np.random.default_rng(seed)
+    cand = np.flatnonzero(~bridges(net))
+    trip = np.full(int(n_scen), -1, dtype=np.int32)
+    if cand.size == 0:
+        return trip
+    pick = rng.uniform(size=int(n_scen)) < frac
+    lines = rng.choice(cand, size=int(n_scen))
+    trip[pick] = lines[pick]
+    trip[0] = -1
+    return trip
 
 
 def make_scenarios(net: Network, n_scen: int, sigma: float, seed: int = 1):

@@ -69,3 +69,26 @@ def test_stochastic_two_stage_small():
     for i in range(4):
         assert np.abs(D[i]["g"]).max() <= 1e-8
     assert ipm.e_mu(ipm.kkt_errors(M, st, D), 0.0) <= 1e-8
+
+
+def test_line_flow_limits_bind_and_hold():
+    """With line ratings (§4.1.1), the oracle converges to a point whose end
+    flows respect every rating, the three tightened lines sit at their
+    limits, the power flow is satisfied, and the cost is no lower than the
+    unconstrained optimum's."""
+    from ratings import end_flows, rated
+    net, pd, qd = rated(30, 6, 1, 0.0)
+    M = opf.Model(net, pd, qd)
+    st, k, _ = ipm.solve(M)
+    D = kkt.eval_all(M, st)
+    assert ipm.e_mu(ipm.kkt_errors(M, st, D), 0.0) <= 1e-8
+    assert np.abs(D[0]["g"]).max() <= 1e-8
+    fl = end_flows(M, st["x"][0], st["u"])
+    assert np.all(fl <= net.rate * (1 + 1e-7))
+    assert np.sum(fl >= net.rate * (1 - 1e-5)) >= 3
+    plain = synth.make_network(30, 6, seed=0)
+    M0 = opf.Model(plain, pd, qd)
+    st0, _, _ = ipm.solve(M0)
+    f = M.functions(0, st["x"][0], st["u"])[0]
+    f0 = M0.functions(0, st0["x"][0], st0["u"])[0]
+    assert f >= f0 - 1e-9 * abs(f0)

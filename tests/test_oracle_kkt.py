@@ -18,10 +18,17 @@ def _model(N=3, n=30, ng=6, sigma=0.05):
     return opf.Model(net, pd, qd)
 
 
-@pytest.fixture(scope="module")
-def mid_iterate():
-    """A non-trivial interior iterate: 4 IPM iterations from the start."""
-    M = _model()
+@pytest.fixture(scope="module", params=["plain", "rated"])
+def mid_iterate(request):
+    """A non-trivial interior iterate: 4 IPM iterations from the start; the
+    rated variant has the 2L line-flow rows of §4.1.1 in h, three of them
+    binding at the optimum."""
+    if request.param == "rated":
+        from ratings import rated
+        net, pd, qd = rated(30, 6, 3, 0.05)
+        M = opf.Model(net, pd, qd)
+    else:
+        M = _model()
     st = ipm.initial_state(M)
     for _ in range(4):
         ipm.iterate(M, st)
