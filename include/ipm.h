@@ -93,6 +93,8 @@ enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1, IPM_PREC_FP64_TC = 2 };
 
 enum { IPM_BARRIER_MONOTONE = 0, IPM_BARRIER_ADAPTIVE = 1 };
 
+enum { IPM_REDUCTION_DENSE = 0, IPM_REDUCTION_ADJOINT = 1, IPM_REDUCTION_AUTO = 2 };
+
 typedef struct {
   double tol;            /* KKT residual E_0 target (1e-8) */
   int max_iter;          /* 200 */
@@ -120,7 +122,13 @@ typedef struct {
                             reduction, and refinement stops at a relative residual (max norm,
                             against the right-hand side) <= 1e-12 or when a step no longer
                             halves it; 0 = no residual check */
-  int reserved;
+  int reduction;         /* how K_hat = sum_i Z_i^T Y_i is formed on the FP64 paths:
+                            IPM_REDUCTION_DENSE (default) the contraction of Z and Y;
+                            IPM_REDUCTION_ADJOINT the paper's local reduction by adjoint solves
+                            (§3.2: K_hat V = L_u - G_u^T G_x^{-T} L_x with V = I, one more
+                            multi-RHS solve with G_x^T instead of the contraction);
+                            IPM_REDUCTION_AUTO: the autotuner (autotune = 1) times both at the
+                            first condensation and keeps the faster (dense without it) */
   double sigma;          /* centring factor of the adaptive rule (0.1) */
 } ipm_options;
 
@@ -244,9 +252,10 @@ ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
  *        to the FP64 condensation; if cap allows, then the number of
  *        iterations since ipm_create that fell back to the FP64
  *        condensation, the number of emulated contractions redone on the
- *        FP64 units, and for the last solve the refinement steps on the
+ *        FP64 units, for the last solve the refinement steps on the
  *        augmented system eq. (6), its relative residual before and after
- *        them),
+ *        them, then 1 if K_hat is formed by the adjoint-solve reduction, and
+ *        the autotuner's times (ms) of the dense and the adjoint reduction),
  *        IPM_Q_TIMERS (2*IPM_N_PHASES doubles: accumulated device milliseconds
  *        and call counts per phase, see ipm_set_profiling; a further double,
  *        if cap allows, is the total number of kernels the library launched).

@@ -168,6 +168,35 @@ def condense(model, st, D, mu, delta=0.0, keep_Z=True):
     return C
 
 
+def reduce_adjoint(model, C, D, n_batch=None):
+    """K_hat by the paper's local reduction (§3.2, "Local reduction"): for
+    blocks V of n_batch Cartesian basis vectors of R^{n_u} (ceil(n_u /
+    n_batch) blocks, the reading of the garbled "div(n_u, n_batch) + 1"),
+      1. T_x = -(G_x)^{-1} (G_u V)
+      2. [L_x; L_u] = [[K_xx, K_xu], [K_ux, K_uu]] [T_x; V]
+      3. K_hat V = L_u - G_u^T (G_x)^{-T} L_x   (G_u^T: the transpose the
+         printed step omits, fixed by dimensions and Prop. 2.3),
+    summed over scenarios, plus Sigma_u + delta I and the first-stage terms
+    once.  Uses the condensed blocks of ``condense`` (C) and the scenarios'
+    LU factors; returns the n_u x n_u matrix as assembled (not symmetrised)."""
+    nu = model.lay.nu
+    Sx, Su, Ss = C.sig
+    nb = nu if n_batch is None else int(n_batch)
+    out = np.diag(Su + C.delta)
+    for i in range(model.N):
+        d = D[i]
+        Kxx, Kxu, Kuu, _ = C.blocks[i]
+        lu = C.lu[i]
+        Gu = d["Gu"].toarray()
+        for j0 in range(0, nu, nb):
+            V = np.eye(nu)[:, j0:j0 + nb]
+            Tx = -lu.solve(Gu @ V)
+            Lx = Kxx @ Tx + Kxu @ V
+            Lu = Kxu.T @ Tx + Kuu @ V
+            out[:, j0:j0 + nb] += Lu - Gu.T @ lu.solve(Lx, trans="T")
+    return out
+
+
 def cholesky_pd(A):
     """Cholesky factor of a symmetric matrix, or None if not positive definite."""
     try:

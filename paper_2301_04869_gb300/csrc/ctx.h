@@ -36,6 +36,10 @@ struct ipm_ctx {
   double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta); scratch [N][max(nx,nu)]
   double *gLu = nullptr, *HTt_u = nullptr;
   double *pg_curv = nullptr, *pmax_d = nullptr;
+  // the paper's adjoint-solve reduction (IPM_REDUCTION_ADJOINT / _AUTO):
+  // the columns of L_x as vectors [N][n_u][n_x], solved in place with G_x^T
+  bool adjoint = false;
+  double *Wadj = nullptr;
   // FP64 contraction emulated on the tensor cores (IPM_PREC_FP64_TC)
   bool emu = false;
   EmuPlan emuZY, emuZZ;

@@ -196,6 +196,8 @@ ipm_status alloc_work(ipm_ctx *c) {
   if (!c->mixed) {
     TRY(dalloc(c, &c->Z, N * nx * nu));
     TRY(dalloc(c, &c->Y, N * nx * nu));
+    if (c->opt.reduction != IPM_REDUCTION_DENSE) TRY(dalloc(c, &c->Wadj, N * nx * nu));
+    c->adjoint = c->opt.reduction == IPM_REDUCTION_ADJOINT;
     if (c->emu) {
       const long long krows = N * nx;
       const size_t pb = emu_planes_bytes((int)nu, krows);
@@ -467,6 +469,16 @@ ipm_status run_part(ipm_ctx *c, cudaGraphExec_t &gx, long long &gn, Fn fn, cudaS
   return IPM_OK;
 }
 
+// K_hat by the paper's adjoint solves (after the multi-RHS solve left Y, Y_u):
+// the n_u columns of L_x = Y as vectors, G_x^{-T} on each (one CTA per
+// vector), then K_hat = sum_i (Y_u,i - G_u^T W_i) + first-stage diagonal
+void launch_adjoint_reduce(ipm_ctx *c, cudaStream_t st) {
+  const DevSym &S = c->ds;
+  launch_transpose_rows(S.N, S.nx, S.nu, c->Y, c->Wadj, st);
+  launch_solve1_batched(S, c->dw.LU, c->dw.rd, c->Wadj, 1, S.nu, 128, st);
+  launch_adjoint_assemble(S, c->dw.J, c->Yu, c->Wadj, c->diag1, c->Khat, st);
+}
+
 // K_hat contraction of the FP64 branch: partial tiles over ngroups scenario
 // groups (the multi-instance runner may take it over through the hook)
 void fp64_contraction(ipm_ctx *c, cudaStream_t st) {
@@ -491,7 +503,9 @@ struct Tuned {
   int zs_threads;
   long long kchunk;
   int ngroups, tc_groups;
+  bool adjoint;
 };
+void launch_adjoint_reduce(ipm_ctx *c, cudaStream_t st);
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int, int>, Tuned> g_tune_cache;
 
@@ -524,7 +538,7 @@ double time_ms(Fn fn, cudaStream_t st, int reps = 2) {
 ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
   const DevSym &S = c->ds;
   DevWork &D = c->dw;
-  const auto key = std::make_tuple(S.nx, S.nu, S.N, c->mixed ? 1 : (c->emu ? 2 : 0));
+  const auto key = std::make_tuple(S.nx, S.nu, S.N, (c->mixed ? 1 : (c->emu ? 2 : 0)) + 4 * c->opt.reduction);
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tune_cache.find(key);
@@ -532,6 +546,10 @@ ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
       c->zs_threads = it->second.zs_threads;
       c->kchunk = it->second.kchunk;
       c->ngroups = it->second.ngroups;
+      if (c->opt.reduction == IPM_REDUCTION_AUTO && !c->mixed) {
+        c->adjoint = it->second.adjoint;
+        if (c->adjoint) launch_adjoint_reduce(c, st);  // K_hat of this first condensation
+      }
       if (c->emu) {
         emu_regroup(c->emuZY, it->second.tc_groups);
         emu_regroup(c->emuZZ, it->second.tc_groups);
@@ -615,10 +633,32 @@ ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
     tc_regroup(c->planZZ, bestG);
     tc_groups = bestG;
   }
+  // the paper's adjoint-solve reduction against the dense contraction (split,
+  // contraction and assembly of K_hat), both from the same Z, Y, Y_u
+  if (fp64 && c->opt.reduction == IPM_REDUCTION_AUTO) {
+    const double md = time_ms([&] {
+      if (c->emu) {
+        launch_emu_split_pair(c->emuZY, c->Z, c->Y, nullptr, st, c->emu_rs);
+        launch_emu_schur(c->emuZY, c->emupart, D.flags, st);
+        launch_emu_assemble(c->emuZY, S.N, c->emupart, c->Yu, c->diag1, c->Khat, st);
+      } else {
+        launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
+                         c->partial, st);
+        launch_khat_assemble(S.nu, S.N, c->ngroups, c->ntiles, c->nt1, c->partial, c->tile_of, c->Yu, c->diag1,
+                             c->Khat, st);
+      }
+    }, st);
+    const double ma = time_ms([&] { launch_adjoint_reduce(c, st); }, st);
+    c->tune_ms[6] = md;
+    c->tune_ms[7] = ma;
+    c->adjoint = ma < md;
+    // the adjoint K_hat is in place now; the dense one is formed next by
+    // the caller's contraction
+  }
   CK(cudaGetLastError());
   c->tuned = true;
   std::lock_guard<std::mutex> lk(g_tune_mutex);
-  g_tune_cache[key] = Tuned{c->zs_threads, c->kchunk, c->ngroups, tc_groups};
+  g_tune_cache[key] = Tuned{c->zs_threads, c->kchunk, c->ngroups, tc_groups, c->adjoint};
   return IPM_OK;
 }
 
@@ -702,6 +742,14 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
       reduced_rhs_fp64(c, c->side2);
       cudaEventRecord(c->ev_join2, c->side2);
     }
+    if (fp64 && c->adjoint) {
+      // §3.2 local reduction, step 3 for V = I: K_hat = sum_i (L_u - G_u^T G_x^{-T} L_x)
+      ph_begin(c, PH_GEMM, st);
+      launch_adjoint_reduce(c, st);
+      ph_end(c, PH_GEMM, st);
+      cudaStreamWaitEvent(st, c->ev_join2, 0);
+      return;
+    }
     ph_begin(c, PH_SPLIT, st);
     if (fp64 && c->emu) {
       // exact BF16 slices of the row-balanced Z and Y for the tensor cores
@@ -742,16 +790,18 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   } else {
     TRY(run_part(c, c->gx_pre[br], c->gx_pre_n[br], pre, st));
   }
-  ph_begin(c, PH_GEMM, st);
-  if (fp64) fp64_contraction(c, st);
-  else launch_tc_schur(c->planZY, c->tcpart, D.flags, st);
-  TRY(run_part(c, c->gx_post[br], c->gx_post_n[br], post, st));
+  if (!(fp64 && c->adjoint)) {
+    ph_begin(c, PH_GEMM, st);
+    if (fp64) fp64_contraction(c, st);
+    else launch_tc_schur(c->planZY, c->tcpart, D.flags, st);
+    TRY(run_part(c, c->gx_post[br], c->gx_post_n[br], post, st));
+  }
   CK(cudaGetLastError());
   TRY(read_flags(c, st));
   ph_collect(c);
   if (c->h_flags[FLAG_SINGULAR]) return fail(c, IPM_ERR_SINGULAR_GX, "singular pivot in the LU of G_x");
   if (c->h_flags[FLAG_TIMEOUT]) return fail(c, IPM_ERR_TIMEOUT, "a bounded device wait gave up");
-  if (fp64 && c->emu && c->h_flags[FLAG_NONFINITE]) {
+  if (fp64 && c->emu && !c->adjoint && c->h_flags[FLAG_NONFINITE]) {
     // the emulated contraction gave a non-finite value: redo it on the FP64 units
     ++c->n_emu_fallback;
     launch_gemm_tn64((long long)S.N * S.nx, c->kchunk, S.nu, c->ngroups, c->Z, c->Y, c->tiles, c->ntiles,
@@ -1339,6 +1389,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
   if ((c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED &&
        c->opt.precision != IPM_PREC_FP64_TC) || !(c->opt.tol > 0) ||
       c->opt.max_iter < 0 || c->opt.max_refine < 0 || c->opt.aug_refine < 0 || c->opt.aug_refine > 100 ||
+      c->opt.reduction < IPM_REDUCTION_DENSE || c->opt.reduction > IPM_REDUCTION_AUTO ||
       (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
       (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
       (c->opt.poison != 0 && c->opt.poison != 1) || (c->opt.lu_pair != 0 && c->opt.lu_pair != 1) ||
@@ -1526,6 +1577,9 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
     if (cap >= 13) out[12] = (double)c->aug_steps;        // refinement steps on eq. (6), last solve
     if (cap >= 14) out[13] = c->aug_res0;                  // its relative residual before them
     if (cap >= 15) out[14] = c->aug_res;                   // and after
+    if (cap >= 16) out[15] = c->adjoint ? 1.0 : 0.0;       // K_hat by the adjoint-solve reduction
+    if (cap >= 17) out[16] = c->tune_ms[6];                // autotuner: dense reduction (ms)
+    if (cap >= 18) out[17] = c->tune_ms[7];                // autotuner: adjoint reduction (ms)
     return IPM_OK;
   }
   if (scen < 0 || scen >= N) return IPM_ERR_ARG;

@@ -51,6 +51,15 @@ void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const 
                      float *Z, float *Y, double *Yu, cudaStream_t st, int threads = 256);
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st);
+// vps vectors per scenario: v [N * vps][n_x] (position order), one CTA of
+// `threads` (a multiple of 32) per vector
+void launch_solve1_batched(const DevSym &S, const double *LU, const double *rd, double *v, int trans, int vps,
+                           int threads, cudaStream_t st);
+// kernels_adjoint.cu: the paper's local reduction by adjoint solves
+// (K_hat V = L_u - G_u^T G_x^{-T} L_x, §3.2) on all n_u unit vectors at once
+void launch_transpose_rows(int N, int nx, int nu, const double *Y, double *W, cudaStream_t st);
+void launch_adjoint_assemble(const DevSym &S, const double *J, const double *Yu, const double *W, const double *diag,
+                             double *Khat, cudaStream_t st);
 
 // kernels_dense.cu
 void launch_gemm_tn64(long long krows, long long kc, int nu, int ngroups, const double *A, const double *B,

@@ -539,16 +539,18 @@ __device__ __forceinline__ void solve_level(const int4 *__restrict__ rows, int e
   }
 }
 
+// One CTA per vector: vector b of v ([N * vps][n_x], position order) belongs
+// to scenario b / vps (vps vectors per scenario share its factors).
 __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
-                                                double *v, int trans, int in_smem) {
+                                                double *v, int trans, int in_smem, int vps) {
   extern __shared__ double xsm[];
   __shared__ double blk[32][33];
-  const int sc = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const int sc = blockIdx.x / vps, tid = threadIdx.x, bd = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int nx = S.nx, t0 = S.t0, nd = S.nd;
   const double *A = LU + (size_t)sc * S.nnzLU;
   const double *r = rd + (size_t)sc * nx;
-  double *vs = v + (size_t)sc * nx;
+  double *vs = v + (size_t)blockIdx.x * nx;
   // the solution vector of this scenario lives in shared memory when it fits
   double *x = in_smem ? xsm : vs;
   if (in_smem) {
@@ -878,5 +880,21 @@ void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *
   }();
   const int sm = (size_t)S.nx * sizeof(double) <= cap ? 1 : 0;
   const size_t bytes = sm ? (size_t)S.nx * sizeof(double) : 0;
-  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm); ipm_count_launch();
+  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1); ipm_count_launch();
+}
+
+void launch_solve1_batched(const DevSym &S, const double *LU, const double *rd, double *v, int trans, int vps,
+                           int threads, cudaStream_t st) {
+  static const size_t cap = [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_solve1);
+    return raise_smem_cap(k_solve1) ? (size_t)optin - fa.sharedSizeBytes : (size_t)0;
+  }();
+  const int sm = (size_t)S.nx * sizeof(double) <= cap ? 1 : 0;
+  const size_t bytes = sm ? (size_t)S.nx * sizeof(double) : 0;
+  const long long nb = (long long)S.N * vps;
+  k_solve1<<<(unsigned)nb, threads, bytes, st>>>(S, LU, rd, v, trans, sm, vps); ipm_count_launch();
 }

@@ -45,13 +45,14 @@ class Network(ctypes.Structure):
 
 
 BARRIER_MONOTONE, BARRIER_ADAPTIVE = 0, 1
+REDUCTION_DENSE, REDUCTION_ADJOINT, REDUCTION_AUTO = 0, 1, 2
 
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("solve_threads", ctypes.c_int), ("barrier_rule", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
-                ("lu_pair", ctypes.c_int), ("aug_refine", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("lu_pair", ctypes.c_int), ("aug_refine", ctypes.c_int), ("reduction", ctypes.c_int),
                 ("sigma", ctypes.c_double)]
 
 
@@ -199,7 +200,8 @@ def _cnet(net):
 
 
 def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, barrier_rule=None, sigma=None,
-                 graphs=False, autotune=False, solve_threads=0, poison=False, lu_pair=True, aug_refine=None):
+                 graphs=False, autotune=False, solve_threads=0, poison=False, lu_pair=True, aug_refine=None,
+                 reduction=None):
     lib = load()
     opt = Options()
     lib.ipm_default_options(ctypes.byref(opt))
@@ -218,6 +220,8 @@ def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, bar
     opt.lu_pair = int(bool(lu_pair))
     if aug_refine is not None:
         opt.aug_refine = int(aug_refine)
+    if reduction is not None:
+        opt.reduction = int(reduction)
     return opt
 
 
@@ -226,14 +230,14 @@ class Solver:
 
     def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
                  barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0, poison=False,
-                 lu_pair=True, aug_refine=None):
+                 lu_pair=True, aug_refine=None, reduction=None):
         lib = load()
         self._lib = lib
         self._keep, cnet = _cnet(net)
         opt = make_options(precision=precision, tol=tol, max_iter=max_iter, max_refine=max_refine,
                            barrier_rule=barrier_rule, sigma=sigma, graphs=graphs, autotune=autotune,
                            solve_threads=solve_threads, poison=poison, lu_pair=lu_pair,
-                           aug_refine=aug_refine)
+                           aug_refine=aug_refine, reduction=reduction)
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]
@@ -335,7 +339,7 @@ class Solver:
         d = self.dims
         sizes = {Q_KHAT: d.n_u * d.n_u, Q_RHS_U: d.n_u, Q_Z: d.n_x * d.n_u, Q_FGH: 1 + d.n_x + d.m,
                  Q_JAC: d.n_x * d.n_x + d.n_x * d.n_u + d.m * d.n_x + d.m * d.n_u,
-                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 15,
+                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 18,
                  Q_TIMERS: 2 * N_PHASES + 1, Q_ZTZ: d.n_u * d.n_u}
         out = np.empty(sizes[which])
         self._check(self._lib.ipm_get_quantity(self._h, which, scen, _ptr(out, ctypes.c_double), out.size,

@@ -126,3 +126,17 @@ def test_condensed_K_block_structure(mid_iterate):
     Kd = W + H.T @ np.diag(Ss) @ H
     Kb, _ = kkt.condensed_matrix_dense(M, C, D)
     assert np.abs(Kb[:nd, :nd] - Kd).max() <= 1e-12 * np.abs(Kd).max()
+
+
+@pytest.mark.parametrize("n_batch", [None, 4])
+def test_adjoint_reduction_equals_schur(mid_iterate, n_batch):
+    """The paper's three-step local reduction (§3.2) in blocks of n_batch
+    unit vectors gives the Schur complement with the explicit A_i^{-1} of
+    eq. (15), and its result is symmetric to rounding."""
+    M, st = mid_iterate
+    D = kkt.eval_all(M, st)
+    C = kkt.condense(M, st, D, st["mu"], 0.0)
+    R = kkt.reduce_adjoint(M, C, D, n_batch)
+    S = kkt.schur_explicit(M, C, D)
+    assert np.abs(R - S).max() <= 1e-10 * np.abs(S).max()
+    assert np.abs(R - R.T).max() <= 1e-11 * np.abs(R).max()
