@@ -934,24 +934,19 @@ ipm_status pcg_reduced(ipm_ctx *c, double delta, cudaStream_t st) {
   return IPM_OK;
 }
 
-// Relative residual of the augmented system eq. (6) at the step (c->px ..
-// c->pz): rho = -r - A p, returns max|rho| / max|r| (read back).  Leaves
+// Backward error of the step (c->px .. c->pz) on the augmented system eq. (6):
+// rho = -r - A p, returns max|rho| over the largest magnitude among r and
+// the block products A_blk p_blk (read back).  Leaves
 // kpx, kpu = K p_d (positions) and Hp = H p_d of this step, which the line
 // search reads, and rho in ar1x .. ar4.
 ipm_status aug_residual(ipm_ctx *c, double delta, double *rel, cudaStream_t st) {
   const DevSym &S = c->ds;
   DevWork &D = c->dw;
-  const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
   launch_gather_pos(S.N, S.nx, S.iperm, c->px, c->vpos, 1.0, st);
   launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);
-  launch_aug_residual(S, D, delta, c->px, c->pu, c->ps, c->py, c->pz, c->kpx, c->kpu, c->diag1, c->Hp, c->atw,
-                      c->ar1x, c->ar1u, c->ar2, c->ar3, c->ar4, st);
   CK(cudaMemsetAsync(c->amax, 0, 2 * sizeof(unsigned long long), st));
-  launch_maxabs2(NX, c->ar1x, D.r1x, c->amax, st);
-  launch_maxabs2(NX, c->ar3, D.g, c->amax, st);
-  launch_maxabs2(NM, c->ar2, D.r2, c->amax, st);
-  launch_maxabs2(NM, c->ar4, D.r4, c->amax, st);
-  launch_maxabs2(S.nu, c->ar1u, D.r1u, c->amax, st);
+  launch_aug_residual(S, D, delta, c->px, c->pu, c->ps, c->py, c->pz, c->kpx, c->kpu, c->diag1, c->Hp, c->atw,
+                      c->ar1x, c->ar1u, c->ar2, c->ar3, c->ar4, c->amax, st);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->h_amax, c->amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -966,8 +961,9 @@ ipm_status aug_residual(ipm_ctx *c, double delta, double *rel, cudaStream_t st) 
 // with rho the residual of the current step, the correction solves
 // A dp = rho, i.e. the Newton system with right-hand side r' = -rho, through
 // the same condensation (Prop. 2.1), reduction (eq. (11), Prop. 2.3) and
-// factor; then p += dp.  Stops at a relative residual <= 1e-12, when a step
-// does not halve it (the best step is kept), or after opt.aug_refine steps.
+// factor; then p += dp.  Stops at a backward error <= 1e-12 (a backward-
+// stable FP64 solve is already there: no step), when a step does not halve
+// it (the better step is kept), or after opt.aug_refine steps.
 ipm_status refine_aug(ipm_ctx *c, double delta, cudaStream_t st) {
   const DevSym &S = c->ds;
   DevWork &D = c->dw;

@@ -127,11 +127,14 @@ void launch_fill_bound_duals(long long n, int period, const double *l, const dou
                              double *zu, cudaStream_t st);
 
 // kernels_refine.cu (residual of the augmented system eq. (6) at a step; all
-// vectors in state order except kpx_pos, the positions of K p_d)
+// vectors in state order except kpx_pos, the positions of K p_d; amax[0],
+// amax[1] (zeroed by the caller) receive the bit patterns of max |rho| and
+// of the largest magnitude among the right-hand side and the block products)
 void launch_aug_residual(const DevSym &S, const DevWork &D, double delta, const double *px, const double *pu,
                          const double *ps, const double *py, const double *pz, const double *kpx_pos,
                          const double *kpu, const double *diag1, double *Hp, double *tw, double *rho1x,
-                         double *rho1u, double *rho2, double *rho3, double *rho4, cudaStream_t st);
+                         double *rho1u, double *rho2, double *rho3, double *rho4, unsigned long long *amax,
+                         cudaStream_t st);
 // outx = ax + H_x^T v (per scenario), outu = au + sum_i H_u^T v_i
 void launch_htv(const DevSym &S, const DevWork &D, const double *ax, const double *au, const double *v, double *outx,
                 double *outu, cudaStream_t st);

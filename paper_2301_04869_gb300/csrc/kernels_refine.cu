@@ -13,8 +13,13 @@
 //   (W + Sigma_p) p_d = K p_d - H^T (Sigma_s H p_d)
 // and rho_d = -r1 - K p_d - delta p_d - G^T p_y - H^T (p_z - Sigma_s H p_d).
 // Every product here walks the Jacobian values J stored per bus-adjacency
-// slot (and the line-flow rows' HF), in a fixed order (no atomics): thread
-// per (scenario, row).
+// slot (and the line-flow rows' HF), in a fixed order: thread per
+// (scenario, row).  The refinement is judged by a normwise backward error:
+// max |rho| over the largest magnitude among the right-hand side and the
+// products A_block p of each row (r, K p_d, G^T p_y + H^T t, G p_d, H p_d,
+// Sigma_s p_s, p_z, ...); both maxima are gathered by atomic maxima of the
+// magnitudes' bit patterns (order-independent, so the result is
+// deterministic).
 #include "dev.cuh"
 #include "kernels.h"
 
@@ -82,48 +87,98 @@ __device__ __forceinline__ double jrow(const DevSym &S, const double *J, const d
   return acc;
 }
 
+// out[0] = max(out[0], max |a| over the warp), out[1] likewise for b; every
+// lane of the warp calls it (out-of-range lanes with zeros)
+__device__ __forceinline__ void warp_max2(double a, double b, unsigned long long *out) {
+  unsigned long long ma = __double_as_longlong(fabs(a)), mb = __double_as_longlong(fabs(b));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long oa = __shfl_down_sync(0xffffffffu, ma, o);
+    const unsigned long long ob = __shfl_down_sync(0xffffffffu, mb, o);
+    ma = oa > ma ? oa : ma;
+    mb = ob > mb ? ob : mb;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], ma);
+    atomicMax(&out[1], mb);
+  }
+}
+
 // h rows: Hp, rho_s, rho_z and tw = p_z - Sigma_s Hp
 __global__ void k_res_h(DevSym S, DevWork D, const double *px, const double *pu, const double *ps,
-                        const double *pz, double *Hp, double *rho2, double *rho4, double *tw) {
+                        const double *pz, double *Hp, double *rho2, double *rho4, double *tw,
+                        unsigned long long *amax) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)S.N * S.m) return;
-  const int sc = (int)(t / S.m), r = (int)(t - (long long)sc * S.m);
-  const double hp = S.hrow_comp[r] < 2 ? jrow(S, D.J, px, pu, sc, S.hrow_bus[r], S.hrow_comp[r])
-                                       : flowrow(S, D.HF, px, pu, sc, r - S.ng - 1, S.hrow_bus[r]);
-  Hp[t] = hp;
-  rho2[t] = -D.r2[t] - D.Ss[t] * ps[t] - pz[t];
-  rho4[t] = -D.r4[t] - hp - ps[t];
-  tw[t] = pz[t] - D.Ss[t] * hp;
+  double res = 0.0, scl = 0.0;
+  if (t < (long long)S.N * S.m) {
+    const int sc = (int)(t / S.m), r = (int)(t - (long long)sc * S.m);
+    const double hp = S.hrow_comp[r] < 2 ? jrow(S, D.J, px, pu, sc, S.hrow_bus[r], S.hrow_comp[r])
+                                         : flowrow(S, D.HF, px, pu, sc, r - S.ng - 1, S.hrow_bus[r]);
+    Hp[t] = hp;
+    const double sps = D.Ss[t] * ps[t];
+    const double r2 = -D.r2[t] - sps - pz[t], r4 = -D.r4[t] - hp - ps[t];
+    rho2[t] = r2;
+    rho4[t] = r4;
+    tw[t] = pz[t] - D.Ss[t] * hp;
+    res = fmax(fabs(r2), fabs(r4));
+    scl = fmax(fmax(fmax(fabs(D.r2[t]), fabs(sps)), fmax(fabs(pz[t]), fabs(D.r4[t]))), fmax(fabs(hp), fabs(ps[t])));
+  }
+  warp_max2(res, scl, amax);
 }
 
 // x rows (state order): rho_y = -g - G p_d and
 // rho_1x = -r1x - K p_d - delta p_x - G_x^T p_y - H_x^T tw
 __global__ void k_res_x(DevSym S, DevWork D, double delta, const double *px, const double *pu, const double *py,
-                        const double *tw, const double *kpx_pos, double *rho1x, double *rho3) {
+                        const double *tw, const double *kpx_pos, double *rho1x, double *rho3,
+                        unsigned long long *amax) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)S.N * S.nx) return;
-  const int sc = (int)(t / S.nx), j = (int)(t - (long long)sc * S.nx);
-  const int a = S.xbus[j], kind = S.xkind[j];
-  rho3[t] = -D.g[t] - jrow(S, D.J, px, pu, sc, a, kind);
-  const double kp = kpx_pos[(size_t)sc * S.nx + S.perm[j]];
-  rho1x[t] = -D.r1x[t] - kp - delta * px[t] - jt_at(S, D, py, tw, sc, a, kind);
+  double res = 0.0, scl = 0.0;
+  if (t < (long long)S.N * S.nx) {
+    const int sc = (int)(t / S.nx), j = (int)(t - (long long)sc * S.nx);
+    const int a = S.xbus[j], kind = S.xkind[j];
+    const double gp = jrow(S, D.J, px, pu, sc, a, kind);
+    const double r3 = -D.g[t] - gp;
+    rho3[t] = r3;
+    const double kp = kpx_pos[(size_t)sc * S.nx + S.perm[j]];
+    const double jt = jt_at(S, D, py, tw, sc, a, kind);
+    const double r1 = -D.r1x[t] - kp - delta * px[t] - jt;
+    rho1x[t] = r1;
+    res = fmax(fabs(r1), fabs(r3));
+    scl = fmax(fmax(fmax(fabs(D.r1x[t]), fabs(kp)), fmax(fabs(delta * px[t]), fabs(jt))),
+               fmax(fabs(D.g[t]), fabs(gp)));
+  }
+  warp_max2(res, scl, amax);
 }
 
 // u rows (scenarios summed in index order):
 // rho_1u = -r1u - (sum_i kpu_i + diag1 p_u) - delta p_u - sum_i (G_u^T p_y,i + H_u^T tw_i)
 __global__ void k_res_u(DevSym S, DevWork D, double delta, const double *pu, const double *py, const double *tw,
-                        const double *kpu, const double *diag1, double *rho1u) {
+                        const double *kpu, const double *diag1, double *rho1u, unsigned long long *amax) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= S.nu) return;
-  double acc = 0.0;
-  if (j < S.ng) {
-    const int a = S.hrow_bus[j];  // generator j's bus; v there is u_j
-    for (int sc = 0; sc < S.N; ++sc) acc += kpu[(size_t)sc * S.nu + j] + jt_at(S, D, py, tw, sc, a, 1);
-  } else {
-    const int k = j - S.ng + 1, a = S.hrow_bus[k];
-    for (int sc = 0; sc < S.N; ++sc) acc += kpu[(size_t)sc * S.nu + j] - row_mult(S, py, tw, sc, a, 0);
+  double res = 0.0, scl = 0.0;
+  if (j < S.nu) {
+    double acc = 0.0, mag = 0.0;
+    if (j < S.ng) {
+      const int a = S.hrow_bus[j];  // generator j's bus; v there is u_j
+      for (int sc = 0; sc < S.N; ++sc) {
+        const double kq = kpu[(size_t)sc * S.nu + j], jt = jt_at(S, D, py, tw, sc, a, 1);
+        acc += kq + jt;
+        mag = fmax(mag, fmax(fabs(kq), fabs(jt)));
+      }
+    } else {
+      const int k = j - S.ng + 1, a = S.hrow_bus[k];
+      for (int sc = 0; sc < S.N; ++sc) {
+        const double kq = kpu[(size_t)sc * S.nu + j], rm = row_mult(S, py, tw, sc, a, 0);
+        acc += kq - rm;
+        mag = fmax(mag, fmax(fabs(kq), fabs(rm)));
+      }
+    }
+    const double dp = (diag1[j] + delta) * pu[j];
+    const double r1 = -D.r1u[j] - acc - dp;
+    rho1u[j] = r1;
+    res = fabs(r1);
+    scl = fmax(fmax(fabs(D.r1u[j]), mag), fmax(fabs(acc), fabs(dp)));
   }
-  rho1u[j] = -D.r1u[j] - acc - (diag1[j] + delta) * pu[j];
+  warp_max2(res, scl, amax);
 }
 
 // x rows of H^T v (state order): out = a + H_x^T v   (v [N][m])
@@ -198,11 +253,13 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 void launch_aug_residual(const DevSym &S, const DevWork &D, double delta, const double *px, const double *pu,
                          const double *ps, const double *py, const double *pz, const double *kpx_pos,
                          const double *kpu, const double *diag1, double *Hp, double *tw, double *rho1x,
-                         double *rho1u, double *rho2, double *rho3, double *rho4, cudaStream_t st) {
+                         double *rho1u, double *rho2, double *rho3, double *rho4, unsigned long long *amax,
+                         cudaStream_t st) {
   const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
-  k_res_h<<<nblk(NM, 256), 256, 0, st>>>(S, D, px, pu, ps, pz, Hp, rho2, rho4, tw); ipm_count_launch();
-  k_res_x<<<nblk(NX, 256), 256, 0, st>>>(S, D, delta, px, pu, py, tw, kpx_pos, rho1x, rho3); ipm_count_launch();
-  k_res_u<<<nblk(S.nu, 128), 128, 0, st>>>(S, D, delta, pu, py, tw, kpu, diag1, rho1u); ipm_count_launch();
+  k_res_h<<<nblk(NM, 256), 256, 0, st>>>(S, D, px, pu, ps, pz, Hp, rho2, rho4, tw, amax); ipm_count_launch();
+  k_res_x<<<nblk(NX, 256), 256, 0, st>>>(S, D, delta, px, pu, py, tw, kpx_pos, rho1x, rho3, amax);
+  ipm_count_launch();
+  k_res_u<<<nblk(S.nu, 128), 128, 0, st>>>(S, D, delta, pu, py, tw, kpu, diag1, rho1u, amax); ipm_count_launch();
 }
 
 void launch_htv(const DevSym &S, const DevWork &D, const double *ax, const double *au, const double *v, double *outx,

@@ -96,7 +96,8 @@ def test_step(gpu, tripped, precision):
     sol.ipm_solve_kkt(step)
     g = sol.split_step(step.cpu().numpy())
     p = kkt.reduced_step(M, st, D, C, L)
-    bar = max(TOL, 10.0 * float(np.linalg.cond(C.Khat)) * EPS)
+    kap = max(float(np.linalg.cond(C.Khat)), max(float(np.linalg.cond(d["Gx"].toarray())) for d in D))
+    bar = max(TOL, 10.0 * kap * EPS)
     for k in ("px", "pu", "ps", "py", "pz"):
         assert rel(g[k], p[k]) <= bar, (k, rel(g[k], p[k]), bar)
 

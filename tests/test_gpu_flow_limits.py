@@ -5,7 +5,7 @@ With line ratings h gains |S_f|^2 and |S_t|^2 of every line (m = n_g + 1 +
 the optimum): the flow rows of h, their Jacobian rows, the Lagrangian Hessian
 with random multipliers on every row, the condensed blocks, K_hat and the
 reduced right-hand side at 1e-10; the Newton step at the step bar
-max(1e-10, 10 kappa(K_hat) eps); and the whole solve takes the oracle's
+max(1e-10, 10 kappa eps) (kappa: the larger of kappa(K_hat), kappa(G_x)); and the whole solve takes the oracle's
 iteration count and ends at a point where the tightened lines sit at their
 ratings."""
 import numpy as np
@@ -104,7 +104,8 @@ def test_condensation_and_step(gpu, name, precision):
     sol.ipm_solve_kkt(step)
     g = sol.split_step(step.cpu().numpy())
     p = kkt.reduced_step(M, st, D, C, L)
-    bar = max(TOL, 10.0 * float(np.linalg.cond(C.Khat)) * EPS)
+    kap = max(float(np.linalg.cond(C.Khat)), max(float(np.linalg.cond(d["Gx"].toarray())) for d in D))
+    bar = max(TOL, 10.0 * kap * EPS)
     for k in ("px", "pu", "ps", "py", "pz"):
         assert rel(g[k], p[k]) <= bar, (k, rel(g[k], p[k]), bar)
 

@@ -7,9 +7,10 @@ condensed blocks, Z, K_hat, the reduced right-hand side) meet the FP64 parity
 bar 1e-10.  The Newton step is the solution of a linear system: two
 backward-stable FP64 solves of it (the GPU's static-pivot LU and Cholesky,
 the oracle's SuperLU and LAPACK) each carry a forward error of order
-kappa(K_hat) eps, so its bar is max(1e-10, 10 kappa_2(K_hat) eps) with
-kappa from the oracle's K_hat at that iterate (the measured errors sit at
-0.3 - 3 kappa eps).  Cases span one scenario (30 buses), a ragged small batch
+kappa eps, so its bar is max(1e-10, 10 kappa eps), kappa the larger of
+kappa_2(K_hat) and kappa_2(G_x^i) at that iterate (K_hat alone on the
+64-scenario workload, where the dense condition numbers of 64 G_x would
+dominate the test's time; the measured errors sit at 0.3 - 3 kappa eps).  Cases span one scenario (30 buses), a ragged small batch
 (60 buses, 5 scenarios), and the 1000-bus network with 4 and 64 scenarios."""
 import numpy as np
 import pytest
@@ -23,9 +24,14 @@ TOL = 1e-10
 EPS = float(np.finfo(np.float64).eps)
 
 
-def step_bar(Khat):
-    """Parity bar of a Newton step: max(1e-10, 10 kappa_2(K_hat) eps)."""
-    return max(TOL, 10.0 * float(np.linalg.cond(Khat)) * EPS)
+def step_bar(Khat, D=None):
+    """Parity bar of a Newton step: max(1e-10, 10 kappa eps), kappa the larger
+    condition number of K_hat and of the G_x^i (p_u comes from K_hat, p_x and
+    p_y from solves with G_x and G_x^T)."""
+    kap = float(np.linalg.cond(Khat))
+    if D is not None:
+        kap = max(kap, max(float(np.linalg.cond(d["Gx"].toarray())) for d in D))
+    return max(TOL, 10.0 * kap * EPS)
 
 
 def rel(a, b):
@@ -146,10 +152,11 @@ def test_newton_step_parity(gpu, name, delta, precision):
     C = kkt.condense(M, st, D, st["mu"], delta)
     L = kkt.cholesky_pd(C.Khat)
     p = kkt.reduced_step(M, st, D, C, L)
-    bar = step_bar(C.Khat)
+    bar = step_bar(C.Khat, D)
     for k in ("px", "pu", "ps", "py", "pz"):
         assert rel(g[k], p[k]) <= bar, (k, rel(g[k], p[k]), bar)
-    # the step the library returns was checked on the augmented system eq. (6)
+    # the step the library returns was checked on the augmented system eq. (6):
+    # the direct FP64 solve is backward stable (backward error <= 1e-12)
     info = sol.ipm_get_quantity(gpu.Q_INFO)
     assert info[14] <= 1e-12, info[12:15]
 
