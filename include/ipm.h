@@ -129,6 +129,11 @@ typedef struct {
                             multi-RHS solve with G_x^T instead of the contraction);
                             IPM_REDUCTION_AUTO: the autotuner (autotune = 1) times both at the
                             first condensation and keeps the faster (dense without it) */
+  int big_block;         /* 0 (default): the dense trailing block of the LU of G_x is factored
+                            and solved in shared memory when it has at most 400 states and by
+                            the batched global-memory kernels above that (the block then also
+                            takes the sparse pivots just before it that reach a sixth of it);
+                            1: the global-memory kernels whatever its size */
   double sigma;          /* centring factor of the adaptive rule (0.1) */
 } ipm_options;
 
@@ -302,15 +307,24 @@ ipm_status ipm_selftest_bounded_wait(long long polls, void *stream);
  *     product pointers, columns and slots);
  *   IPM_SYM_TW_*: the products of the sparse pivots into the trailing block
  *     (list lengths; L slot, U slot and flushed entry slot or -1 per product,
- *     product q of list t at q * lists + t).
+ *     product q of list t at q * lists + t);
+ *   IPM_SYM_LU_SLOT: the storage slot of every entry of the CSC pattern (the
+ *     entries outside the trailing block in CSC order, then the trailing
+ *     block column-major with leading dimension nd at dense_base).
+ * IPM_SYM_DIMS then also gives dense_base and 1 if the trailing block is
+ * handled by the large-block (global-memory) kernels.  which |
+ * IPM_SYM_FORCE_BIG builds the structures of that mode whatever nd is (its
+ * dense block also takes the sparse pivots just before it that reach a
+ * sixth of it).
  * Writes min(cap, size) values to out (out may be NULL) and the size to *len.
  * Errors: IPM_ERR_ARG for an invalid network or structure id. */
 enum {
   IPM_SYM_DIMS = 0, IPM_SYM_LU_COLPTR, IPM_SYM_LU_ROW, IPM_SYM_FR_PTR, IPM_SYM_FR_COL, IPM_SYM_FR_LSLOT,
   IPM_SYM_GU_PTR, IPM_SYM_GU_COL, IPM_SYM_ZP_LEV_OFF, IPM_SYM_ZP_LEV_PTR, IPM_SYM_ZP_ROWS, IPM_SYM_ZP_EPTR,
   IPM_SYM_ZP_COL, IPM_SYM_ZP_SLOT, IPM_SYM_ZP_ZPTR, IPM_SYM_ZP_ZROWS, IPM_SYM_ZP_TPTR, IPM_SYM_ZP_TCOL,
-  IPM_SYM_ZP_TSLOT, IPM_SYM_TW_LEN, IPM_SYM_TW_L, IPM_SYM_TW_U, IPM_SYM_TW_E, IPM_SYM_COUNT
+  IPM_SYM_ZP_TSLOT, IPM_SYM_TW_LEN, IPM_SYM_TW_L, IPM_SYM_TW_U, IPM_SYM_TW_E, IPM_SYM_LU_SLOT, IPM_SYM_COUNT
 };
+#define IPM_SYM_FORCE_BIG 0x100
 ipm_status ipm_symbolic_export(const ipm_network *net, int which, int *out, long long cap, long long *len);
 
 /* Replace the scenario loads of a context (same network and N) and reset the

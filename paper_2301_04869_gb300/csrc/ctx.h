@@ -70,6 +70,7 @@ struct ipm_ctx {
   double *dstep = nullptr, *dpx = nullptr, *dpu = nullptr, *dps = nullptr, *dpy = nullptr, *dpz = nullptr;
   double *arh1x = nullptr, *arh2 = nullptr, *arhs = nullptr, *apos2 = nullptr, *bpos2 = nullptr, *vpos2 = nullptr;
   unsigned long long *amax = nullptr, *h_amax = nullptr;
+  double *aupart = nullptr, *aumag = nullptr;  // per-(scenario, u row) terms [N][n_u]
   int aug_steps = 0;
   double aug_res0 = 0.0, aug_res = 0.0;
   double *dz[6] = {};

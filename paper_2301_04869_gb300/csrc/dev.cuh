@@ -12,6 +12,11 @@ constexpr int LU_LISTS = 1024;  // lists of trailing-block products of the LU fa
 struct DevSym {
   int n, L, ng, N, nx, nu, m, nnzA, nnzKB, nnzLU, nlev, nlev_b, nlev_f, t0, nd, nlev_fs, nlev_bs;
   int nflow;  // line-flow rows of h (2 L with ratings, else 0)
+  // large trailing block (global-memory kernels): flag, offset of the block
+  // in each scenario's LU values (column-major, leading dimension nd), and
+  // max |G_x| per scenario (reference of the pivot test) [N]
+  int big, dense_base;
+  double *lu_amax;
   const int *xth, *xv, *uv, *gen_of_bus, *xbus, *xkind;
   const int *lfr, *lto;
   const double *lg, *lb, *lbh;

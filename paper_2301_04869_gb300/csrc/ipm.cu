@@ -101,6 +101,10 @@ ipm_status upload_symbolic(ipm_ctx *c, const HostNet &net, const double *pd, con
   d.nnzA = S.nnzA; d.nnzKB = S.nnzKB; d.nnzLU = S.nnzLU; d.nlev = S.nlev; d.nlev_b = S.nlev_b;
   d.nlev_f = S.nlev_f; d.t0 = S.t0; d.nd = S.nd; d.nlev_fs = S.nlev_fs; d.nlev_bs = S.nlev_bs;
   d.nflow = S.nflow;
+  d.big = S.big ? 1 : 0;
+  d.dense_base = S.dense_base;
+  d.lu_amax = nullptr;
+  if (S.big) TRY(dalloc(c, &d.lu_amax, (size_t)S.N));
   TRY(upload(c, &d.xth, S.xth)); TRY(upload(c, &d.xv, S.xv)); TRY(upload(c, &d.uv, S.uv));
   TRY(upload(c, &d.gen_of_bus, S.gen_of_bus)); TRY(upload(c, &d.xbus, S.xbus)); TRY(upload(c, &d.xkind, S.xkind));
   TRY(upload(c, &d.lfr, S.lfr)); TRY(upload(c, &d.lto, S.lto));
@@ -312,6 +316,7 @@ ipm_status alloc_work(ipm_ctx *c) {
     TRY(dalloc(c, &c->arh1x, N * nx)); TRY(dalloc(c, &c->arh2, nu)); TRY(dalloc(c, &c->arhs, nu));
     TRY(dalloc(c, &c->apos2, N * nx)); TRY(dalloc(c, &c->bpos2, N * nx)); TRY(dalloc(c, &c->vpos2, N * nx));
     TRY(dalloc(c, &c->amax, 2));
+    TRY(dalloc(c, &c->aupart, N * nu)); TRY(dalloc(c, &c->aumag, N * nu));
     CK(cudaMallocHost(&c->h_amax, 2 * sizeof(unsigned long long)));
   }
   TRY(dalloc(c, &c->vpos, N * nx)); TRY(dalloc(c, &c->bpos, N * nx)); TRY(dalloc(c, &c->apos, N * nx));
@@ -946,7 +951,7 @@ ipm_status aug_residual(ipm_ctx *c, double delta, double *rel, cudaStream_t st) 
   launch_kapply(S, D.K, c->vpos, c->pu, c->kpx, c->kpu, st);
   CK(cudaMemsetAsync(c->amax, 0, 2 * sizeof(unsigned long long), st));
   launch_aug_residual(S, D, delta, c->px, c->pu, c->ps, c->py, c->pz, c->kpx, c->kpu, c->diag1, c->Hp, c->atw,
-                      c->ar1x, c->ar1u, c->ar2, c->ar3, c->ar4, c->amax, st);
+                      c->ar1x, c->ar1u, c->ar2, c->ar3, c->ar4, c->aupart, c->aumag, c->amax, st);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->h_amax, c->amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -981,21 +986,34 @@ ipm_status refine_aug(ipm_ctx *c, double delta, cudaStream_t st) {
     launch_lincomb(NM, c->ar4, -1.0, c->ar4, 0.0, nullptr, 0.0, nullptr, st);
     // condensed right-hand side (Prop. 2.1): rhat1 = r1' + H^T (Sigma_s r4' - r2')
     launch_tv(NM, D.Ss, c->ar2, c->ar4, c->atw, st);
-    launch_htv(S, D, c->ar1x, c->ar1u, c->atw, c->arh1x, c->arh2, st);
+    launch_htv(S, D, c->ar1x, c->ar1u, c->atw, c->arh1x, c->arh2, c->aupart, st);
     // eq. (11): b = G_x^{-1} r3', a = G_x^{-T}(rhat1_x - (K_xx + delta) b)
     launch_gather_pos(S.N, S.nx, S.iperm, c->ar3, c->bpos2, 1.0, st);
     launch_solve1(S, D.LU, D.rd, c->bpos2, 0, st);
     launch_kapply(S, D.K, c->bpos2, nullptr, c->kpx, nullptr, st);
     launch_gather_pos(S.N, S.nx, S.iperm, c->arh1x, c->apos2, 1.0, st);
     launch_lincomb(NX, c->apos2, 1.0, c->apos2, -1.0, c->kpx, -delta, c->bpos2, st);
-    launch_solve1(S, D.LU, D.rd, c->apos2, 1, st);
-    launch_rhs_reduced(S, D.J, D.K, c->arh2, c->apos2, c->bpos2, c->dpu, st);
+    const bool zfp64 = !c->mixed || c->exact_iter;  // an FP64 Z is at hand
+    if (zfp64) {
+      // with Z = -G_x^{-1} G_u: G_u^T G_x^{-T} w = -Z^T w, and
+      // G_x^{-1}(r3' + G_u dp_u) = b - Z dp_u (no further forward solve)
+      launch_lincomb(S.nu, c->dpu, -1.0, c->arh2, 0.0, nullptr, 0.0, nullptr, st);
+      launch_zt_apply(S, c->Z, c->apos2, D.K, c->bpos2, -1.0, 1.0, c->dpu, c->cpos, st);
+    } else {
+      launch_solve1(S, D.LU, D.rd, c->apos2, 1, st);
+      launch_rhs_reduced(S, D.J, D.K, c->arh2, c->apos2, c->bpos2, c->dpu, st);
+    }
     launch_chol_solve(S.nu, c->F, c->dpu, st);
     // Prop. 2.3: dp_x = -G_x^{-1}(r3' + G_u dp_u), dp_y = -G_x^{-T}(rhat1_x + (K_xx + delta) dp_x + K_xu dp_u)
-    launch_gather_pos(S.N, S.nx, S.iperm, c->ar3, c->vpos2, 1.0, st);
-    launch_gu_apply(S, D.J, c->dpu, c->vpos2, st);
-    launch_solve1(S, D.LU, D.rd, c->vpos2, 0, st);
-    launch_lincomb(NX, c->vpos2, -1.0, c->vpos2, 0.0, nullptr, 0.0, nullptr, st);
+    if (zfp64) {
+      CK(cudaMemcpyAsync(c->vpos2, c->bpos2, NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      launch_z_apply(S, c->Z, c->dpu, -1.0, c->vpos2, st);
+    } else {
+      launch_gather_pos(S.N, S.nx, S.iperm, c->ar3, c->vpos2, 1.0, st);
+      launch_gu_apply(S, D.J, c->dpu, c->vpos2, st);
+      launch_solve1(S, D.LU, D.rd, c->vpos2, 0, st);
+      launch_lincomb(NX, c->vpos2, -1.0, c->vpos2, 0.0, nullptr, 0.0, nullptr, st);
+    }
     launch_kapply(S, D.K, c->vpos2, c->dpu, c->kpx, c->kpu, st);
     launch_gather_pos(S.N, S.nx, S.iperm, c->arh1x, c->apos2, 1.0, st);
     launch_lincomb(NX, c->apos2, 1.0, c->apos2, 1.0, c->kpx, delta, c->vpos2, st);
@@ -1386,6 +1404,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
        c->opt.precision != IPM_PREC_FP64_TC) || !(c->opt.tol > 0) ||
       c->opt.max_iter < 0 || c->opt.max_refine < 0 || c->opt.aug_refine < 0 || c->opt.aug_refine > 100 ||
       c->opt.reduction < IPM_REDUCTION_DENSE || c->opt.reduction > IPM_REDUCTION_AUTO ||
+      (c->opt.big_block != 0 && c->opt.big_block != 1) ||
       (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
       (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
       (c->opt.poison != 0 && c->opt.poison != 1) || (c->opt.lu_pair != 0 && c->opt.lu_pair != 1) ||
@@ -1401,7 +1420,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
   for (int i = 0; i < h.n; ++i)
     if (!(h.vmin[i] > 0) || !(h.vmax[i] > h.vmin[i]) || !std::isfinite(h.vmax[i])) ok = false;
   std::string err;
-  if (!ok || !build_symbolic(h, n_scen, c->S, err)) {
+  if (!ok || !build_symbolic(h, n_scen, c->S, err, c->opt.big_block)) {
     delete c;
     return IPM_ERR_ARG;
   }
@@ -1830,6 +1849,8 @@ ipm_status ipm_warm_start(ipm_ctx *c, const float *pred, void *stream) {
 long long ipm_kernel_launches(void) { return g_ipm_launches.load(); }
 
 ipm_status ipm_symbolic_export(const ipm_network *net, int which, int *out, long long cap, long long *len) {
+  const int force_big = (which & IPM_SYM_FORCE_BIG) ? 1 : 0;
+  which &= ~IPM_SYM_FORCE_BIG;
   if (!net || !len || which < 0 || which >= IPM_SYM_COUNT || cap < 0 || net->n_bus < 2 || net->n_line < 1 ||
       net->n_gen < 1 || !net->from || !net->to || !net->gen_bus || !net->r || !net->x || !net->b ||
       !net->pmax || !net->qmax || !net->c2 || !net->c1 || !net->vmin || !net->vmax)
@@ -1838,11 +1859,14 @@ ipm_status ipm_symbolic_export(const ipm_network *net, int which, int *out, long
   host_net(net, h);
   Sym S;
   std::string err;
-  if (!build_symbolic(h, 1, S, err)) return IPM_ERR_ARG;
+  if (!build_symbolic(h, 1, S, err, force_big)) return IPM_ERR_ARG;
   std::vector<int> v;
   const std::vector<int> *src = &v;
   switch (which) {
-    case IPM_SYM_DIMS: v = {S.nx, S.nu, S.t0, S.nd, S.nnzLU, S.zp_npan, LU_LISTS}; break;
+    case IPM_SYM_DIMS:
+      v = {S.nx, S.nu, S.t0, S.nd, S.nnzLU, S.zp_npan, LU_LISTS, S.dense_base, S.big ? 1 : 0};
+      break;
+    case IPM_SYM_LU_SLOT: src = &S.lu_slot; break;
     case IPM_SYM_LU_COLPTR: src = &S.lu_colptr; break;
     case IPM_SYM_LU_ROW: src = &S.lu_row; break;
     case IPM_SYM_FR_PTR: src = &S.fr_ptr; break;

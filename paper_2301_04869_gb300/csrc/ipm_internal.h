@@ -56,6 +56,14 @@ struct Sym {
   int nlev_f = 0;          // levels of the sparse (non-tail) pivots
   int t0 = 0, nd = 0;      // dense trailing block: positions [t0, nx), nd = nx - t0
   std::vector<int> tail_slot;  // nd*nd LU slots of the trailing block, row-major
+  // LU storage: the entries outside the trailing block in CSC order by
+  // position (slots 0 ..), then the trailing block column-major with leading
+  // dimension nd at dense_base (a multiple of 4): (t0 + a, t0 + b) at
+  // dense_base + b nd + a.  lu_colptr / lu_row describe the whole pattern,
+  // lu_slot the storage slot of each of its entries.
+  int dense_base = 0;
+  bool big = false;        // trailing block factored and solved by the global-memory kernels
+  std::vector<int> lu_slot;
   int nlev_fs = 0, nlev_bs = 0;  // forward / backward levels of the sparse rows only
   std::vector<int> fs_lev_ptr, fs_rows, bs_lev_ptr, bs_rows;
   std::vector<int> f_lev_ptr, f_piv_ptr, f_piv, f_tgt, f_op_ptr, f_op_l, f_op_u, f_op_k;
@@ -91,4 +99,8 @@ struct Sym {
 
 // Builds the symbolic structures.  Returns false with a message on invalid
 // networks (bad indices, duplicate or self lines, gen_bus[0] != 0, ...).
-bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err);
+// big: 0 = the large-trailing-block kernels only when the dense trailing
+// block exceeds BIG_ND, 1 = always (the same results through the other
+// kernels, for tests on small networks)
+constexpr int BIG_ND = 400;
+bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err, int big = 0);

@@ -47,6 +47,10 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
                      double *Z, double *Y, double *Yu, cudaStream_t st, int threads = 256,
                      const double *g = nullptr, double *b = nullptr, int *ezy = nullptr);
 bool zsolve64_folds_b(const DevSym &S);
+// kernels_big.cu: the large trailing block (S.big) in global memory
+void launch_big_lu_dense(const DevSym &S, double *LU, double *rd, const double *amax, int *flags, cudaStream_t st);
+void launch_big_trsm64(const DevSym &S, const double *LU, const double *rd, double *Z, cudaStream_t st);
+void launch_big_trsm32(const DevSym &S, const double *LU, const double *rd, float *Z, cudaStream_t st);
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
                      float *Z, float *Y, double *Yu, cudaStream_t st, int threads = 256);
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
@@ -133,11 +137,11 @@ void launch_fill_bound_duals(long long n, int period, const double *l, const dou
 void launch_aug_residual(const DevSym &S, const DevWork &D, double delta, const double *px, const double *pu,
                          const double *ps, const double *py, const double *pz, const double *kpx_pos,
                          const double *kpu, const double *diag1, double *Hp, double *tw, double *rho1x,
-                         double *rho1u, double *rho2, double *rho3, double *rho4, unsigned long long *amax,
-                         cudaStream_t st);
+                         double *rho1u, double *rho2, double *rho3, double *rho4, double *upart, double *umag,
+                         unsigned long long *amax, cudaStream_t st);
 // outx = ax + H_x^T v (per scenario), outu = au + sum_i H_u^T v_i
 void launch_htv(const DevSym &S, const DevWork &D, const double *ax, const double *au, const double *v, double *outx,
-                double *outu, cudaStream_t st);
+                double *outu, double *upart, cudaStream_t st);
 // t = Sigma_s r4 - r2
 void launch_tv(long long n, const double *Ss, const double *r2, const double *r4, double *t, cudaStream_t st);
 // pz = Sigma_s (H p_d + r4) - r2, ps = -(r2 + pz) / Sigma_s

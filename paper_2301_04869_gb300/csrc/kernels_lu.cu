@@ -162,6 +162,10 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
   double *r = rd + (size_t)sc * S.nx;
   const double amax = lu_sparse_part<false>(S, nL, J, A, r, flags, piv_tol, sc, sh, 0u);
   const int nd = S.nd, t0 = S.t0;
+  if (S.big) {  // the block is factored by the batched kernels
+    if (tid == 0) S.lu_amax[sc] = amax;
+    return;
+  }
   if (nd == 0) return;
   const int *ts = S.tail_slot;
   // dense trailing block: columns [0, k0) in place through the slot map,
@@ -272,10 +276,14 @@ __global__ void k_lu_factor(DevSym S, int nL, const double *__restrict__ J, doub
 // column by column by the whole CTA, in shared memory when it fits
 // (tail_smem), else in place in Z.  T is the storage/arithmetic type of Z, Y
 // (double on the FP64 path, float on the mixed path); Y_u accumulates in FP64.
+// phase (large trailing block, S.big): 1 = the forward sparse rows and the
+// trailing rows' right-hand sides only (left in Z for the batched block
+// solves), 2 = the backward sparse rows and the products only; 0 = all.
 template <typename T>
 __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, const double *__restrict__ rd,
                             const double *__restrict__ J, const double *__restrict__ K, T *Z, T *Y, double *Yu,
-                            bool tail_smem, T *sh, const double *__restrict__ gvec, T *bvec, int *ezy) {
+                            bool tail_smem, T *sh, const double *__restrict__ gvec, T *bvec, int *ezy,
+                            int phase = 0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, bd = blockDim.x;
   const int nu = S.nu, nx = S.nx, N = S.N;
   // the CTA after the panels of Z (when bvec is given) solves b alone
@@ -304,6 +312,7 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
   // forward, sparse rows: this panel's schedule (rows its columns of G_u
   // reach, products against such rows only); the other rows are zero
   const int pan = blockIdx.x;
+  if (phase != 2) {
   for (int e = S.zp_zptr[pan] + warp; e < S.zp_zptr[pan + 1]; e += nw)
     if (wr) zw[(size_t)S.zp_zrows[e] * zst] = (T)0;
   for (int l = S.zp_lev_off[pan]; l < S.zp_lev_off[pan + 1]; ++l) {
@@ -341,6 +350,7 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
       else if (valid) Zs[(size_t)row * nu + c] = acc;
     }
     __syncthreads();
+    if (phase == 1) return;  // the block is solved by the batched kernels
     const int *ts = S.tail_slot;
     if (tail_smem) {
       // Blocked by 32 in shared memory: one warp solves each 32 x 32
@@ -426,6 +436,8 @@ __device__ void zsolve_body(const DevSym &S, const double *__restrict__ LU, cons
       __syncthreads();
     }
   }
+  }  // phase != 2
+  if (phase == 1) return;
   // backward, sparse rows
   for (int l = 0; l < S.nlev_bs; ++l) {
     for (int e = S.bs_lev_ptr[l] + warp; e < S.bs_lev_ptr[l + 1]; e += nw) {
@@ -484,18 +496,18 @@ __global__ void __launch_bounds__(256, 5) k_zsolve64(DevSym S, const double *__r
                                                   const double *__restrict__ J,
                                                   const double *__restrict__ K, double *Z, double *Y,
                                                   double *Yu, int tail_smem, const double *__restrict__ gvec,
-                                                  double *bvec, int *ezy) {
+                                                  double *bvec, int *ezy, int phase) {
   extern __shared__ double shd[];
-  zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd, gvec, bvec, ezy);
+  zsolve_body<double>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shd, gvec, bvec, ezy, phase);
 }
 
 __global__ void __launch_bounds__(256, 5) k_zsolve32(DevSym S, const double *__restrict__ LU,
                                                   const double *__restrict__ rd,
                                                   const double *__restrict__ J,
                                                   const double *__restrict__ K, float *Z, float *Y,
-                                                  double *Yu, int tail_smem) {
+                                                  double *Yu, int tail_smem, int phase) {
   extern __shared__ float shf[];
-  zsolve_body<float>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shf, nullptr, (float *)nullptr, nullptr);
+  zsolve_body<float>(S, LU, rd, J, K, Z, Y, Yu, tail_smem != 0, shf, nullptr, (float *)nullptr, nullptr, phase);
 }
 
 // In-place solve of G_x v = b (trans = 0) or G_x^T v = b (trans = 1) for every
@@ -827,6 +839,12 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
     if (cudaFuncGetAttributes(&fa, k_lu_factor_pair) != cudaSuccess) return (size_t)0;
     return raise_smem_cap(k_lu_factor_pair) ? (size_t)optin - fa.sharedSizeBytes : (size_t)0;
   }();
+  if (S.big) {
+    // sparse part (one CTA per scenario), then the block by the batched kernels
+    k_lu_factor<<<S.N, 512, 0, st>>>(S, nL, J, LU, rd, flags, 1e-14, 0); ipm_count_launch();
+    launch_big_lu_dense(S, LU, rd, S.lu_amax, flags, st);
+    return;
+  }
   const int np = (S.nd + 15) / 16, ldl = ((np + 1) / 2) * 16;
   const size_t pair_smem = (size_t)S.nd * (ldl + 16) * sizeof(double);
   if (allow_pair && S.nd > 0 && pair_smem <= pair_cap) {
@@ -843,7 +861,7 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
 static int zsolve_smem_ok(const DevSym &S, size_t elem) {
   return (S.nd > 0 && (size_t)S.nd * 32 * elem <= 100 * 1024) ? 1 : 0;
 }
-bool zsolve64_folds_b(const DevSym &S) { return S.nd == 0 || zsolve_smem_ok(S, sizeof(double)); }
+bool zsolve64_folds_b(const DevSym &S) { return !S.big && (S.nd == 0 || zsolve_smem_ok(S, sizeof(double))); }
 
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J,
                      const double *K, double *Z, double *Y, double *Yu, cudaStream_t st, int threads,
@@ -855,7 +873,15 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
   // dynamic plus static shared memory may pass the 48 KB default
   static const bool cap = raise_smem_cap(k_zsolve64);
   (void)cap;
-  k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm, g, b, ezy); ipm_count_launch();
+  if (S.big) {
+    // forward sparse rows and the block's right-hand sides, the block by the
+    // batched triangular solves, then the backward sparse rows and products
+    k_zsolve64<<<grid, threads, 0, st>>>(S, LU, rd, J, K, Z, Y, Yu, 0, g, b, ezy, 1); ipm_count_launch();
+    launch_big_trsm64(S, LU, rd, Z, st);
+    k_zsolve64<<<grid, threads, 0, st>>>(S, LU, rd, J, K, Z, Y, Yu, 0, g, b, ezy, 2); ipm_count_launch();
+    return;
+  }
+  k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm, g, b, ezy, 0); ipm_count_launch();
 }
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
                      const double *K, float *Z, float *Y, double *Yu, cudaStream_t st, int threads) {
@@ -864,7 +890,13 @@ void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const 
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(float) : 0;
   static const bool cap = raise_smem_cap(k_zsolve32);
   (void)cap;
-  k_zsolve32<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm); ipm_count_launch();
+  if (S.big) {
+    k_zsolve32<<<grid, threads, 0, st>>>(S, LU, rd, J, K, Z, Y, Yu, 0, 1); ipm_count_launch();
+    launch_big_trsm32(S, LU, rd, Z, st);
+    k_zsolve32<<<grid, threads, 0, st>>>(S, LU, rd, J, K, Z, Y, Yu, 0, 2); ipm_count_launch();
+    return;
+  }
+  k_zsolve32<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm, 0); ipm_count_launch();
 }
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st) {

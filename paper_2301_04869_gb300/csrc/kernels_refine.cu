@@ -126,13 +126,27 @@ __global__ void k_res_h(DevSym S, DevWork D, const double *px, const double *pu,
 }
 
 // x rows (state order): rho_y = -g - G p_d and
-// rho_1x = -r1x - K p_d - delta p_x - G_x^T p_y - H_x^T tw
+// rho_1x = -r1x - K p_d - delta p_x - G_x^T p_y - H_x^T tw; the threads past
+// the x rows form the per-scenario terms of the u rows, upart[s][j] =
+// kpu_s,j + (G_u^T p_y,s + H_u^T tw_s)_j and the largest magnitude of its
+// terms umag[s][j] (summed over scenarios by k_res_u)
 __global__ void k_res_x(DevSym S, DevWork D, double delta, const double *px, const double *pu, const double *py,
-                        const double *tw, const double *kpx_pos, double *rho1x, double *rho3,
-                        unsigned long long *amax) {
+                        const double *tw, const double *kpx_pos, const double *kpu, double *rho1x, double *rho3,
+                        double *upart, double *umag, unsigned long long *amax) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long NX = (long long)S.N * S.nx;
   double res = 0.0, scl = 0.0;
-  if (t < (long long)S.N * S.nx) {
+  if (t >= NX && t < NX + (long long)S.N * S.nu) {
+    const long long q = t - NX;
+    const int sc = (int)(q / S.nu), j = (int)(q - (long long)sc * S.nu);
+    const double kq = kpu[q];
+    double jt;
+    if (j < S.ng) jt = jt_at(S, D, py, tw, sc, S.hrow_bus[j], 1);   // v at generator j's bus
+    else jt = -row_mult(S, py, tw, sc, S.hrow_bus[j - S.ng + 1], 0);  // Pg: -1 in the P row
+    upart[q] = kq + jt;
+    umag[q] = fmax(fabs(kq), fabs(jt));
+  }
+  if (t < NX) {
     const int sc = (int)(t / S.nx), j = (int)(t - (long long)sc * S.nx);
     const int a = S.xbus[j], kind = S.xkind[j];
     const double gp = jrow(S, D.J, px, pu, sc, a, kind);
@@ -151,26 +165,15 @@ __global__ void k_res_x(DevSym S, DevWork D, double delta, const double *px, con
 
 // u rows (scenarios summed in index order):
 // rho_1u = -r1u - (sum_i kpu_i + diag1 p_u) - delta p_u - sum_i (G_u^T p_y,i + H_u^T tw_i)
-__global__ void k_res_u(DevSym S, DevWork D, double delta, const double *pu, const double *py, const double *tw,
-                        const double *kpu, const double *diag1, double *rho1u, unsigned long long *amax) {
+__global__ void k_res_u(DevSym S, DevWork D, double delta, const double *pu, const double *upart,
+                        const double *umag, const double *diag1, double *rho1u, unsigned long long *amax) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   double res = 0.0, scl = 0.0;
   if (j < S.nu) {
     double acc = 0.0, mag = 0.0;
-    if (j < S.ng) {
-      const int a = S.hrow_bus[j];  // generator j's bus; v there is u_j
-      for (int sc = 0; sc < S.N; ++sc) {
-        const double kq = kpu[(size_t)sc * S.nu + j], jt = jt_at(S, D, py, tw, sc, a, 1);
-        acc += kq + jt;
-        mag = fmax(mag, fmax(fabs(kq), fabs(jt)));
-      }
-    } else {
-      const int k = j - S.ng + 1, a = S.hrow_bus[k];
-      for (int sc = 0; sc < S.N; ++sc) {
-        const double kq = kpu[(size_t)sc * S.nu + j], rm = row_mult(S, py, tw, sc, a, 0);
-        acc += kq - rm;
-        mag = fmax(mag, fmax(fabs(kq), fabs(rm)));
-      }
+    for (int sc = 0; sc < S.N; ++sc) {
+      acc += upart[(size_t)sc * S.nu + j];
+      mag = fmax(mag, umag[(size_t)sc * S.nu + j]);
     }
     const double dp = (diag1[j] + delta) * pu[j];
     const double r1 = -D.r1u[j] - acc - dp;
@@ -189,18 +192,20 @@ __global__ void k_htv_x(DevSym S, DevWork D, const double *a, const double *v, d
   out[t] = a[t] + jt_at(S, D, nullptr, v, sc, S.xbus[j], S.xkind[j]);
 }
 
-// u rows of the same, summed over scenarios: out = a + sum_i H_u^T v_i
-__global__ void k_htv_u(DevSym S, DevWork D, const double *a, const double *v, double *out) {
+// u rows of the same: part[s][j] = (H_u^T v_s)_j (thread per (scenario, u
+// row)), then out = a + sum_s part[s] (scenarios in index order)
+__global__ void k_htv_upart(DevSym S, DevWork D, const double *v, double *part) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)S.N * S.nu) return;
+  const int sc = (int)(q / S.nu), j = (int)(q - (long long)sc * S.nu);
+  part[q] = j < S.ng ? jt_at(S, D, nullptr, v, sc, S.hrow_bus[j], 1)
+                     : -row_mult(S, nullptr, v, sc, S.hrow_bus[j - S.ng + 1], 0);
+}
+__global__ void k_htv_u(DevSym S, const double *a, const double *part, double *out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= S.nu) return;
   double acc = 0.0;
-  if (j < S.ng) {
-    const int bus = S.hrow_bus[j];
-    for (int sc = 0; sc < S.N; ++sc) acc += jt_at(S, D, nullptr, v, sc, bus, 1);
-  } else {
-    const int k = j - S.ng + 1, bus = S.hrow_bus[k];
-    for (int sc = 0; sc < S.N; ++sc) acc -= row_mult(S, nullptr, v, sc, bus, 0);
-  }
+  for (int sc = 0; sc < S.N; ++sc) acc += part[(size_t)sc * S.nu + j];
   out[j] = a[j] + acc;
 }
 
@@ -253,20 +258,23 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 void launch_aug_residual(const DevSym &S, const DevWork &D, double delta, const double *px, const double *pu,
                          const double *ps, const double *py, const double *pz, const double *kpx_pos,
                          const double *kpu, const double *diag1, double *Hp, double *tw, double *rho1x,
-                         double *rho1u, double *rho2, double *rho3, double *rho4, unsigned long long *amax,
-                         cudaStream_t st) {
+                         double *rho1u, double *rho2, double *rho3, double *rho4, double *upart, double *umag,
+                         unsigned long long *amax, cudaStream_t st) {
   const long long NX = (long long)S.N * S.nx, NM = (long long)S.N * S.m;
   k_res_h<<<nblk(NM, 256), 256, 0, st>>>(S, D, px, pu, ps, pz, Hp, rho2, rho4, tw, amax); ipm_count_launch();
-  k_res_x<<<nblk(NX, 256), 256, 0, st>>>(S, D, delta, px, pu, py, tw, kpx_pos, rho1x, rho3, amax);
+  const long long NU = (long long)S.N * S.nu;
+  k_res_x<<<nblk(NX + NU, 256), 256, 0, st>>>(S, D, delta, px, pu, py, tw, kpx_pos, kpu, rho1x, rho3, upart, umag,
+                                               amax);
   ipm_count_launch();
-  k_res_u<<<nblk(S.nu, 128), 128, 0, st>>>(S, D, delta, pu, py, tw, kpu, diag1, rho1u, amax); ipm_count_launch();
+  k_res_u<<<nblk(S.nu, 128), 128, 0, st>>>(S, D, delta, pu, upart, umag, diag1, rho1u, amax); ipm_count_launch();
 }
 
 void launch_htv(const DevSym &S, const DevWork &D, const double *ax, const double *au, const double *v, double *outx,
-                double *outu, cudaStream_t st) {
-  const long long NX = (long long)S.N * S.nx;
+                double *outu, double *upart, cudaStream_t st) {
+  const long long NX = (long long)S.N * S.nx, NU = (long long)S.N * S.nu;
   k_htv_x<<<nblk(NX, 256), 256, 0, st>>>(S, D, ax, v, outx); ipm_count_launch();
-  k_htv_u<<<nblk(S.nu, 128), 128, 0, st>>>(S, D, au, v, outu); ipm_count_launch();
+  k_htv_upart<<<nblk(NU, 256), 256, 0, st>>>(S, D, v, upart); ipm_count_launch();
+  k_htv_u<<<nblk(S.nu, 128), 128, 0, st>>>(S, au, upart, outu); ipm_count_launch();
 }
 
 void launch_tv(long long n, const double *Ss, const double *r2, const double *r4, double *t, cudaStream_t st) {

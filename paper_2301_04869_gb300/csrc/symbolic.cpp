@@ -9,6 +9,7 @@
 // numeric factorization then replays a fixed, level-scheduled list of
 // operations for every scenario.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <limits>
@@ -78,7 +79,7 @@ void min_degree(int nv, std::vector<std::vector<int>> adj, std::vector<int> &ord
 
 }  // namespace
 
-bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
+bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err, int big) {
   const int n = net.n, L = net.L, ng = net.ng;
   if (n < 2 || L < 1 || ng < 1 || N < 1) { err = "bad sizes"; return false; }
   if ((int)net.fr.size() != L || (int)net.to.size() != L || (int)net.gen.size() != ng) {
@@ -296,49 +297,9 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
       pat[pth] = rows;
     }
   }
-  // ---- LU storage (CSC by position): U part, diagonal, L part ----
-  std::vector<std::vector<int>> ucols(nx);  // rows r < c with U(r,c) != 0
-  for (int r = 0; r < nx; ++r)
-    for (int c : pat[r]) ucols[c].push_back(r);
-  S.lu_colptr.assign(nx + 1, 0);
-  S.lu_diag.assign(nx, -1);
-  for (int c = 0; c < nx; ++c) {
-    for (int r : ucols[c]) S.lu_row.push_back(r);
-    S.lu_diag[c] = (int)S.lu_row.size();
-    S.lu_row.push_back(c);
-    for (int r : pat[c]) S.lu_row.push_back(r);
-    S.lu_colptr[c + 1] = (int)S.lu_row.size();
-  }
-  S.nnzLU = (int)S.lu_row.size();
-  auto luslot = [&](int r, int c) -> int {
-    auto b = S.lu_row.begin() + S.lu_colptr[c];
-    auto e = S.lu_row.begin() + S.lu_colptr[c + 1];
-    // U part sorted, then diag, then L part sorted; rows < c precede c
-    if (r < c) {
-      auto ee = S.lu_row.begin() + S.lu_diag[c];
-      auto it = std::lower_bound(b, ee, r);
-      if (it == ee || *it != r) return -1;
-      return (int)(it - S.lu_row.begin());
-    }
-    if (r == c) return S.lu_diag[c];
-    auto bb = S.lu_row.begin() + S.lu_diag[c] + 1;
-    auto it = std::lower_bound(bb, e, r);
-    if (it == e || *it != r) return -1;
-    return (int)(it - S.lu_row.begin());
-  };
-  // initial values: G_x entry = J[aslot(bus_r, bus_c)][kind_r*2 + kind_c]
-  S.lu_init.assign(S.nnzLU, -1);
-  for (int c = 0; c < nx; ++c) {
-    int xc = S.iperm[c];
-    int bc = S.xbus[xc], kc = S.xkind[xc];
-    for (int p = S.lu_colptr[c]; p < S.lu_colptr[c + 1]; ++p) {
-      int xr = S.iperm[S.lu_row[p]];
-      int br = S.xbus[xr], kr = S.xkind[xr];
-      int a = aslot(br, bc);
-      if (a >= 0) S.lu_init[p] = a * 4 + kr * 2 + kc;
-    }
-  }
   // ---- levels: lev(p) = 1 + max over pivots k with p in pat(k) ----
+  // (computed on the minimum-degree pattern; a widened trailing block below
+  // only adds fill inside itself, which the dense kernels handle)
   std::vector<int> lev(nx, 0), blev(nx, 0);
   for (int k = 0; k < nx; ++k)
     for (int p : pat[k]) lev[p] = std::max(lev[p], lev[k] + 1);
@@ -351,8 +312,93 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   int t0 = nx;
   while (t0 > 0 && (int)pat[t0 - 1].size() == nx - t0) --t0;
   if (nx - t0 < 2) t0 = nx;  // nothing worth a dense phase
+  // A large trailing block goes to the global-memory kernels.  The sparse
+  // pivots just before it that reach a sizable part of it (a few hundred on
+  // the 10,000-bus networks, each coupled to most of the block) then join it:
+  // their products into the block become part of its dense factorization
+  // instead of millions of gather operations.
+  S.big = (nx - t0) > 0 && (big != 0 || nx - t0 > BIG_ND);
+  if (S.big) {
+    const int nd0 = nx - t0, thr = std::max(8, nd0 / 6);
+    int tp = t0;
+    for (int k = 0; k < t0; ++k) {
+      int ck = 0;
+      for (int i : pat[k]) ck += i >= t0;
+      if (ck >= thr) { tp = k; break; }
+    }
+    for (int k = tp; k < nx; ++k) {
+      pat[k].clear();
+      for (int i = k + 1; i < nx; ++i) pat[k].push_back(i);
+    }
+    t0 = tp;
+  }
   S.t0 = t0;
   S.nd = nx - t0;
+  const int nd = S.nd;
+  // ---- LU pattern (CSC by position): U part, diagonal, L part ----
+  std::vector<std::vector<int>> ucols(nx);  // rows r < c with U(r,c) != 0
+  for (int r = 0; r < nx; ++r)
+    for (int c : pat[r]) ucols[c].push_back(r);
+  S.lu_colptr.assign(nx + 1, 0);
+  std::vector<int> diag_at(nx, -1);
+  for (int c = 0; c < nx; ++c) {
+    for (int r : ucols[c]) S.lu_row.push_back(r);
+    diag_at[c] = (int)S.lu_row.size();
+    S.lu_row.push_back(c);
+    for (int r : pat[c]) S.lu_row.push_back(r);
+    S.lu_colptr[c + 1] = (int)S.lu_row.size();
+  }
+  // storage slots: entries outside the trailing block first, then the block
+  S.lu_slot.assign(S.lu_row.size(), -1);
+  {
+    int q = 0;
+    for (int c = 0; c < nx; ++c)
+      for (int p = S.lu_colptr[c]; p < S.lu_colptr[c + 1]; ++p)
+        if (!(c >= t0 && S.lu_row[p] >= t0)) S.lu_slot[p] = q++;
+    S.dense_base = (q + 3) / 4 * 4;
+    for (int c = t0; c < nx; ++c)
+      for (int p = S.lu_colptr[c]; p < S.lu_colptr[c + 1]; ++p)
+        if (S.lu_row[p] >= t0) S.lu_slot[p] = S.dense_base + (c - t0) * nd + (S.lu_row[p] - t0);
+    S.nnzLU = (int)(((long long)S.dense_base + (long long)nd * nd + 3) / 4 * 4);
+  }
+  S.lu_diag.assign(nx, -1);
+  for (int c = 0; c < nx; ++c) S.lu_diag[c] = S.lu_slot[diag_at[c]];
+  auto luslot = [&](int r, int c) -> int {
+    if (r >= t0 && c >= t0) return S.dense_base + (c - t0) * nd + (r - t0);
+    auto b = S.lu_row.begin() + S.lu_colptr[c];
+    auto e = S.lu_row.begin() + S.lu_colptr[c + 1];
+    // U part sorted, then diag, then L part sorted; rows < c precede c
+    if (r < c) {
+      auto ee = S.lu_row.begin() + diag_at[c];
+      auto it = std::lower_bound(b, ee, r);
+      if (it == ee || *it != r) return -1;
+      return S.lu_slot[it - S.lu_row.begin()];
+    }
+    if (r == c) return S.lu_diag[c];
+    auto bb = S.lu_row.begin() + diag_at[c] + 1;
+    auto it = std::lower_bound(bb, e, r);
+    if (it == e || *it != r) return -1;
+    return S.lu_slot[it - S.lu_row.begin()];
+  };
+  // row and column of every slot (-1 for padding)
+  std::vector<int> slot_row(S.nnzLU, -1), slot_col(S.nnzLU, -1);
+  for (int c = 0; c < nx; ++c)
+    for (int p = S.lu_colptr[c]; p < S.lu_colptr[c + 1]; ++p) {
+      slot_row[S.lu_slot[p]] = S.lu_row[p];
+      slot_col[S.lu_slot[p]] = c;
+    }
+  // initial values: G_x entry = J[aslot(bus_r, bus_c)][kind_r*2 + kind_c]
+  S.lu_init.assign(S.nnzLU, -1);
+  for (int c = 0; c < nx; ++c) {
+    int xc = S.iperm[c];
+    int bc = S.xbus[xc], kc = S.xkind[xc];
+    for (int p = S.lu_colptr[c]; p < S.lu_colptr[c + 1]; ++p) {
+      int xr = S.iperm[S.lu_row[p]];
+      int br = S.xbus[xr], kr = S.xkind[xr];
+      int a = aslot(br, bc);
+      if (a >= 0) S.lu_init[S.lu_slot[p]] = a * 4 + kr * 2 + kc;
+    }
+  }
   S.tail_slot.assign((size_t)S.nd * S.nd, -1);
   for (int a = 0; a < S.nd; ++a)
     for (int b = 0; b < S.nd; ++b) S.tail_slot[(size_t)a * S.nd + b] = luslot(t0 + a, t0 + b);
@@ -373,31 +419,25 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   // updates of the dense trailing block by the sparse pivots (L(i,k) U(k,j),
   // i, j >= t0, k < t0) are kept out of the level lists: per trailing-block
   // entry, all its products, applied after the sparse phase (see below)
-  std::map<int, std::vector<std::pair<int, int>>> tail_ops;  // slot -> (L slot, U slot)
+  struct TailOp { int t, k, l, u; };
+  std::vector<TailOp> tail_ops;
+  std::vector<std::pair<int, int>> tk;  // (target slot, pivot) of one level
   for (int l = 0; l < nlevf; ++l) {
-    std::unordered_map<int, std::vector<int>> tg;  // target slot -> pivots
-    std::vector<int> tslots;
+    tk.clear();
     for (int k : piv_of_lev[l])
       for (int i : pat[k])
         for (int j : pat[k]) {
-          int t = luslot(i, j);
+          const int t = luslot(i, j);
           if (t < 0) { err = "internal: fill pattern not closed"; return false; }
-          auto &v = tg[t];
-          if (v.empty()) tslots.push_back(t);
-          v.push_back(k);
+          if (i >= t0 && j >= t0) tail_ops.push_back({t, k, luslot(i, k), luslot(k, j)});
+          else tk.push_back({t, k});
         }
-    std::sort(tslots.begin(), tslots.end());
-    for (int t : tslots) {
-      int i = S.lu_row[t];
-      // column of slot t
-      int j = (int)(std::upper_bound(S.lu_colptr.begin(), S.lu_colptr.end(), t) - S.lu_colptr.begin()) - 1;
-      if (i >= t0 && j >= t0) {
-        auto &v = tail_ops[t];
-        for (int k : tg[t]) v.push_back({luslot(i, k), luslot(k, j)});
-        continue;
-      }
+    std::sort(tk.begin(), tk.end());
+    for (size_t e = 0; e < tk.size();) {
+      const int t = tk[e].first, i = slot_row[t], j = slot_col[t];
       S.f_tgt.push_back(t);
-      for (int k : tg[t]) {
+      for (; e < tk.size() && tk[e].first == t; ++e) {
+        const int k = tk[e].second;
         S.f_op_l.push_back(luslot(i, k));
         S.f_op_u.push_back(luslot(k, j));
         S.f_op_k.push_back(k);
@@ -414,41 +454,51 @@ bool build_symbolic(const HostNet &net, int N, Sym &S, std::string &err) {
   // op s of list t at s * LU_LISTS + t (coalesced); tw_e names the entry
   // slot after its last product, else -1.
   {
-    std::vector<std::pair<int, int>> ents;  // (op count, slot)
-    for (auto &kv : tail_ops) ents.push_back({(int)kv.second.size(), kv.first});
-    std::sort(ents.begin(), ents.end(), [](const std::pair<int, int> &a, const std::pair<int, int> &b) {
-      return a.first != b.first ? a.first > b.first : a.second < b.second;
-    });
-    std::vector<std::vector<int>> own(LU_LISTS);
-    std::vector<long long> load(LU_LISTS, 0);
-    for (auto &e : ents) {
-      int best = 0;
-      for (int q = 1; q < LU_LISTS; ++q)
-        if (load[q] < load[best]) best = q;
-      own[best].push_back(e.second);
-      load[best] += e.first;
+    std::sort(tail_ops.begin(), tail_ops.end(),
+              [](const TailOp &a, const TailOp &b) { return a.t != b.t ? a.t < b.t : a.k < b.k; });
+    std::vector<std::array<int, 3>> ents;  // (op count, slot, first op)
+    for (size_t e = 0; e < tail_ops.size();) {
+      size_t f = e;
+      while (f < tail_ops.size() && tail_ops[f].t == tail_ops[e].t) ++f;
+      ents.push_back({(int)(f - e), tail_ops[e].t, (int)e});
+      e = f;
     }
-    int M = 0;
-    for (int q = 0; q < LU_LISTS; ++q) M = std::max(M, (int)load[q]);
+    std::sort(ents.begin(), ents.end(), [](const std::array<int, 3> &a, const std::array<int, 3> &b) {
+      return a[0] != b[0] ? a[0] > b[0] : a[1] < b[1];
+    });
+    std::vector<std::vector<int>> own(LU_LISTS);  // entries (index into ents) per list
+    std::vector<long long> load(LU_LISTS, 0);
+    // least-loaded list first (ties: the lower list)
+    std::set<std::pair<long long, int>> heap;
+    for (int q = 0; q < LU_LISTS; ++q) heap.insert({0LL, q});
+    for (size_t e = 0; e < ents.size(); ++e) {
+      const auto top = *heap.begin();
+      heap.erase(heap.begin());
+      own[top.second].push_back((int)e);
+      heap.insert({top.first + ents[e][0], top.second});
+      load[top.second] += ents[e][0];
+    }
+    long long M = 0;
+    for (int q = 0; q < LU_LISTS; ++q) M = std::max(M, load[q]);
     S.tw_len.assign(LU_LISTS, 0);
     S.tw_l.assign((size_t)M * LU_LISTS, 0);
     S.tw_u.assign((size_t)M * LU_LISTS, 0);
     S.tw_e.assign((size_t)M * LU_LISTS, -1);
     for (int q = 0; q < LU_LISTS; ++q) {
       int s_ = 0;
-      for (int slot : own[q]) {
-        const auto &v = tail_ops[slot];
-        for (size_t o = 0; o < v.size(); ++o, ++s_) {
+      for (int ei : own[q]) {
+        const auto &en = ents[ei];
+        for (int o = 0; o < en[0]; ++o, ++s_) {
           const size_t at = (size_t)s_ * LU_LISTS + q;
-          S.tw_l[at] = v[o].first;
-          S.tw_u[at] = v[o].second;
-          if (o + 1 == v.size()) S.tw_e[at] = slot;
+          const TailOp &op = tail_ops[(size_t)en[2] + o];
+          S.tw_l[at] = op.l;
+          S.tw_u[at] = op.u;
+          if (o + 1 == en[0]) S.tw_e[at] = en[1];
         }
       }
       S.tw_len[q] = s_;
     }
-    S.n_tail_ops = 0;
-    for (auto &kv : tail_ops) S.n_tail_ops += (long long)kv.second.size();
+    S.n_tail_ops = (long long)tail_ops.size();
   }
   // forward rows (L rows, k < i) with the matching U(k,i) slots
   {

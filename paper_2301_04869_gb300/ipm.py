@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("solve_threads", ctypes.c_int), ("barrier_rule", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
-                ("lu_pair", ctypes.c_int), ("aug_refine", ctypes.c_int), ("reduction", ctypes.c_int),
+                ("lu_pair", ctypes.c_int), ("aug_refine", ctypes.c_int), ("reduction", ctypes.c_int), ("big_block", ctypes.c_int),
                 ("sigma", ctypes.c_double)]
 
 
@@ -140,15 +140,17 @@ def kernel_launches():
 
 SYM_NAMES = ["dims", "lu_colptr", "lu_row", "fr_ptr", "fr_col", "fr_lslot", "gu_ptr", "gu_col", "zp_lev_off",
              "zp_lev_ptr", "zp_rows", "zp_eptr", "zp_col", "zp_slot", "zp_zptr", "zp_zrows", "zp_tptr", "zp_tcol",
-             "zp_tslot", "tw_len", "tw_l", "tw_u", "tw_e"]
+             "zp_tslot", "tw_len", "tw_l", "tw_u", "tw_e", "lu_slot"]
+SYM_FORCE_BIG = 0x100
 
 
-def symbolic_export(net, name):
+def symbolic_export(net, name, force_big=False):
     """One integer structure of the host-side symbolic analysis of `net`
-    (ipm_symbolic_export; no GPU needed) as an int32 array."""
+    (ipm_symbolic_export; no GPU needed) as an int32 array; force_big builds
+    the structures of the large-trailing-block mode."""
     lib = load()
     keep, cnet = _cnet(net)
-    which = SYM_NAMES.index(name)
+    which = SYM_NAMES.index(name) | (SYM_FORCE_BIG if force_big else 0)
     n = ctypes.c_longlong(0)
     st = lib.ipm_symbolic_export(ctypes.byref(cnet), which, None, 0, ctypes.byref(n))
     if st != IPM_OK:
@@ -201,7 +203,7 @@ def _cnet(net):
 
 def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, barrier_rule=None, sigma=None,
                  graphs=False, autotune=False, solve_threads=0, poison=False, lu_pair=True, aug_refine=None,
-                 reduction=None):
+                 reduction=None, big_block=False):
     lib = load()
     opt = Options()
     lib.ipm_default_options(ctypes.byref(opt))
@@ -222,6 +224,7 @@ def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, bar
         opt.aug_refine = int(aug_refine)
     if reduction is not None:
         opt.reduction = int(reduction)
+    opt.big_block = int(bool(big_block))
     return opt
 
 
@@ -230,14 +233,14 @@ class Solver:
 
     def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
                  barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0, poison=False,
-                 lu_pair=True, aug_refine=None, reduction=None):
+                 lu_pair=True, aug_refine=None, reduction=None, big_block=False):
         lib = load()
         self._lib = lib
         self._keep, cnet = _cnet(net)
         opt = make_options(precision=precision, tol=tol, max_iter=max_iter, max_refine=max_refine,
                            barrier_rule=barrier_rule, sigma=sigma, graphs=graphs, autotune=autotune,
                            solve_threads=solve_threads, poison=poison, lu_pair=lu_pair,
-                           aug_refine=aug_refine, reduction=reduction)
+                           aug_refine=aug_refine, reduction=reduction, big_block=big_block)
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]

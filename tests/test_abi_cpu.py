@@ -70,7 +70,7 @@ def test_symbolic_export_rejects_bad_ids(lib):
     assert lib.ipm_symbolic_export(ctypes.byref(cnet), -1, None, 0, ctypes.byref(n)) == 1
     assert lib.ipm_symbolic_export(ctypes.byref(cnet), len(ipm.SYM_NAMES), None, 0, ctypes.byref(n)) == 1
     assert lib.ipm_symbolic_export(None, 0, None, 0, ctypes.byref(n)) == 1
-    assert lib.ipm_symbolic_export(ctypes.byref(cnet), 0, None, 0, ctypes.byref(n)) == 0 and n.value == 7
+    assert lib.ipm_symbolic_export(ctypes.byref(cnet), 0, None, 0, ctypes.byref(n)) == 0 and n.value == 9
 
 
 def _create(lib, net, pd, qd):

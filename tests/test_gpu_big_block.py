@@ -1,0 +1,123 @@
+"""The large-trailing-block kernels (batched global-memory LU of the dense
+block and batched triangular solves of the multi-RHS solve) against the
+oracle (needs a GPU).
+
+They take over when the minimum-degree order leaves a dense trailing block
+of more than 400 states (the 10,000-bus networks: about 1,800 with the
+widening to the pivots just before it).  Forced on smaller networks
+(big_block = 1), every path must give the oracle's results at the same bars
+as the shared-memory kernels; on the 10,000-bus network itself (one and two
+scenarios) K_hat, Z and the reduced right-hand side match the oracle at
+1e-10 on the FP64 path and at the mixed path's bars."""
+import numpy as np
+import pytest
+
+from bars import step_bars
+from oracle import ipm as oipm
+from oracle import kkt, opf
+from paper_2301_04869_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2301_04869_gb300 import ipm
+    ipm.load()
+    return ipm
+
+
+CASES = {"60bus_N5": (60, 9, 5, 0.05, 4), "1000bus_N4": (1000, 150, 4, 0.05, 5)}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        n, ng, N, sigma, iters = CASES[name]
+        net = synth.make_network(n, ng, seed=0)
+        pd, qd = synth.make_scenarios(net, N, sigma, seed=1)
+        M = opf.Model(net, pd, qd)
+        st = oipm.initial_state(M)
+        for _ in range(iters):
+            oipm.iterate(M, st)
+        _cache[name] = (net, pd, qd, M, st)
+    return _cache[name]
+
+
+PRECS = {"fp64": 0, "fp64_tc": 2, "mixed": 1}
+
+
+@pytest.mark.parametrize("precision", list(PRECS))
+@pytest.mark.parametrize("name", list(CASES))
+def test_forced_big_block(gpu, name, precision):
+    import torch
+    net, pd, qd, M, st = case(name)
+    sol = gpu.Solver(net, pd, qd, precision=PRECS[precision], big_block=True)
+    sol.ipm_set_state(sol.pack_state(st))
+    sol.ipm_eval_derivatives()
+    sol.ipm_condense_scenarios()
+    D = kkt.eval_all(M, st)
+    C0 = kkt.condense(M, st, D, st["mu"], 0.0)
+    nx, nu = sol.dims.n_x, sol.dims.n_u
+    zbar, kbar = (1e-5, 1e-5) if precision == "mixed" else (TOL, TOL)
+    assert rel(sol.ipm_get_quantity(gpu.Q_KHAT).reshape(nu, nu), C0.Khat) <= kbar
+    assert rel(sol.ipm_get_quantity(gpu.Q_RHS_U), C0.rhs_u) <= TOL
+    for i in sorted({0, M.N - 1}):
+        assert rel(sol.ipm_get_quantity(gpu.Q_Z, i).reshape(nx, nu), C0.Z[i]) <= zbar
+    C, L, delta = oipm.factor_with_inertia_correction(M, dict(st), D, st["mu"])
+    assert sol.ipm_factor_schur(delta)
+    step = torch.empty(sol.dims.step_len, dtype=torch.float64, device="cuda")
+    sol.ipm_solve_kkt(step)
+    g = sol.split_step(step.cpu().numpy())
+    p = kkt.reduced_step(M, st, D, C, L)
+    bars = step_bars(M, st, D, C, p)
+    for k in ("px", "pu", "ps", "py", "pz"):
+        assert rel(g[k], p[k]) <= bars[k], (k, rel(g[k], p[k]), bars[k])
+
+
+def test_forced_big_block_solve(gpu):
+    net, pd, qd = synth.workload("opf1000_n64", n_scen=4)
+    M = opf.Model(net, pd, qd)
+    _, k_o, _ = oipm.solve(M)
+    sol = gpu.Solver(net, pd, qd, big_block=True)
+    k_g, e_g = sol.ipm_solve()
+    assert k_g == k_o and e_g <= 1e-8
+
+
+@pytest.fixture(scope="module")
+def net10k():
+    net, pd, qd = synth.workload("opf10000_n256", n_scen=2)
+    M = opf.Model(net, pd, qd)
+    st = oipm.initial_state(M)
+    D = kkt.eval_all(M, st)
+    C = kkt.condense(M, st, D, st["mu"], 0.0)
+    return net, pd, qd, M, st, C
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_10000_bus_condensation(gpu, net10k, precision):
+    """The 10,000-bus, 1,000-generator network of the mixed-precision
+    workload (n_x = 18,999, n_u = 1,999), two of its scenarios, at the cold
+    start: the dense trailing block takes the global-memory kernels."""
+    net, pd, qd, M, st, C = net10k
+    sol = gpu.Solver(net, pd, qd, precision=PRECS[precision])
+    sol.ipm_set_state(sol.pack_state(st))
+    sol.ipm_eval_derivatives()
+    sol.ipm_condense_scenarios()
+    nx, nu = sol.dims.n_x, sol.dims.n_u
+    assert (nx, nu) == (18999, 1999)
+    zbar, kbar = (1e-5, 1e-5) if precision == "mixed" else (TOL, TOL)
+    assert rel(sol.ipm_get_quantity(gpu.Q_KHAT).reshape(nu, nu), C.Khat) <= kbar
+    assert rel(sol.ipm_get_quantity(gpu.Q_RHS_U), C.rhs_u) <= TOL
+    for i in range(M.N):
+        assert rel(sol.ipm_get_quantity(gpu.Q_Z, i).reshape(nx, nu), C.Z[i]) <= zbar

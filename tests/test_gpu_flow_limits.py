@@ -11,6 +11,7 @@ ratings."""
 import numpy as np
 import pytest
 
+from bars import step_bars
 from oracle import ipm as oipm
 from oracle import kkt, opf
 from ratings import end_flows, rated
@@ -104,10 +105,9 @@ def test_condensation_and_step(gpu, name, precision):
     sol.ipm_solve_kkt(step)
     g = sol.split_step(step.cpu().numpy())
     p = kkt.reduced_step(M, st, D, C, L)
-    kap = max(float(np.linalg.cond(C.Khat)), max(float(np.linalg.cond(d["Gx"].toarray())) for d in D))
-    bar = max(TOL, 10.0 * kap * EPS)
+    bars = step_bars(M, st, D, C, p)
     for k in ("px", "pu", "ps", "py", "pz"):
-        assert rel(g[k], p[k]) <= bar, (k, rel(g[k], p[k]), bar)
+        assert rel(g[k], p[k]) <= bars[k], (k, rel(g[k], p[k]), bars[k])
 
 
 @pytest.mark.parametrize("name", list(CASES))

@@ -18,23 +18,26 @@ import pytest
 from paper_2301_04869_gb300 import ipm, synth
 
 
-@pytest.fixture(scope="module", params=[(118, 19, 3), (1000, 150, 0)])
+@pytest.fixture(scope="module", params=[(118, 19, 3, False), (1000, 150, 0, False), (1000, 150, 0, True)])
 def sym(request):
-    n, ng, seed = request.param
+    """The structures of a 118-bus and a 1000-bus network, and of the 1000-bus
+    network in the large-trailing-block mode (widened dense block)."""
+    n, ng, seed, big = request.param
     net = synth.make_network(n, ng, seed=seed)
-    return {k: ipm.symbolic_export(net, k) for k in ipm.SYM_NAMES}
+    return {k: ipm.symbolic_export(net, k, force_big=big) for k in ipm.SYM_NAMES}
 
 
 def slot_rc(S):
-    """(row, col) of every LU slot from the CSC pattern by position."""
+    """(row, col, slot) of every LU pattern entry from the CSC pattern by
+    position and the slot map."""
     cp, rw = S["lu_colptr"], S["lu_row"]
     col = np.repeat(np.arange(len(cp) - 1), np.diff(cp))
-    return rw, col
+    return rw, col, S["lu_slot"]
 
 
 def test_panel_schedules_are_the_reach_of_each_panel(sym):
     S = sym
-    nx, nu, t0, nd, nnz, npan, nlists = S["dims"]
+    nx, nu, t0, nd, nnz, npan, nlists = S["dims"][:7]
     fr_ptr, fr_col, fr_lslot = S["fr_ptr"], S["fr_col"], S["fr_lslot"]
     gu_ptr, gu_col = S["gu_ptr"], S["gu_col"]
     lev_off, lev_ptr, rows, eptr = S["zp_lev_off"], S["zp_lev_ptr"], S["zp_rows"], S["zp_eptr"]
@@ -73,8 +76,8 @@ def test_panel_schedules_are_the_reach_of_each_panel(sym):
 
 def test_trailing_block_products(sym):
     S = sym
-    nx, nu, t0, nd, nnz, npan, nlists = S["dims"]
-    row, col = slot_rc(S)
+    nx, nu, t0, nd, nnz, npan, nlists = S["dims"][:7]
+    row, col, sl = slot_rc(S)
     lens, tl, tu, te = S["tw_len"], S["tw_l"], S["tw_u"], S["tw_e"]
     assert len(lens) == nlists
     # products per flushed entry, list by list
@@ -91,7 +94,7 @@ def test_trailing_block_products(sym):
                 pending = []
         assert not pending  # every list ends with a flush
     # brute force: entries (i, j) of the trailing block, k < t0 with L(i,k) and U(k,j) in the pattern
-    slot = {(int(r), int(c)): s for s, (r, c) in enumerate(zip(row, col))}
+    slot = {(int(r), int(c)): int(s) for r, c, s in zip(row, col, sl)}
     want = {}
     for (i, j), s in slot.items():
         if i >= t0 and j >= t0:
@@ -101,3 +104,18 @@ def test_trailing_block_products(sym):
     assert set(got) == set(want)
     for s in want:
         assert sorted(got[s]) == want[s]
+
+
+def test_slot_layout(sym):
+    """Every pattern entry has its own slot; the trailing block is stored
+    column-major with leading dimension nd at dense_base (a multiple of 4)
+    after every other entry, and it is fully dense."""
+    S = sym
+    nx, nu, t0, nd, nnz, npan, nlists, dense_base, big = S["dims"]
+    row, col, sl = slot_rc(S)
+    assert len(set(sl.tolist())) == len(sl) and sl.min() >= 0 and sl.max() < nnz
+    assert dense_base % 4 == 0 and nnz % 4 == 0 and nnz >= dense_base + nd * nd
+    inb = (row >= t0) & (col >= t0)
+    assert np.array_equal(sl[inb], dense_base + (col[inb] - t0) * nd + (row[inb] - t0))
+    assert np.all(sl[~inb] < dense_base)
+    assert inb.sum() == nd * nd  # the block is full
