@@ -2,16 +2,17 @@
 
 Metric: scenario condensations per second (one scenario condensed and reduced
 at one interior-point iteration = one condensation) and seconds per IPM
-iteration, on the 1000-bus / 64-scenario two-stage OPF workload.  A step is
-one full IPM iteration (evaluation, condensation, reduction, Cholesky with
-inertia correction, step recovery, line search) over all scenarios; the
-states cycle through complete solves from the cold start (re-initialised,
-untimed, whenever a solve converges).
-
-The headline path is --precision (default fp64_tc: FP64 results, the K_hat
-contraction emulated on the BF16 tensor cores); the other two paths (fp64 on
-the FP64 units, mixed BF16x3 with FP64 refinement) are timed too and reported
-under "paths" unless --no-compare.
+iteration.  Default workload: the mixed-precision configuration, a 10,000-bus
+network with 1,000 generators and 256 scenarios (n_x = 18,999, n_u = 1,999),
+on the mixed path (FP32 multi-RHS solves, BF16x3 tensor-core contraction,
+FP64 LU, Cholesky and refinement); the plain FP64 path is timed on the same
+iterates for comparison (a few steps: about 20 s each).  --workload
+opf1000_n64 --precision fp64_tc gives the 1,000-bus / 64-scenario workload
+on the FP64_TC path.  A step is one full IPM iteration (evaluation,
+condensation, reduction, Cholesky with inertia correction, step recovery
+with refinement, line search) over all scenarios; the states cycle through
+complete solves from the cold start (re-initialised, untimed, whenever a
+solve converges).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -46,6 +47,7 @@ TRAFFIC = {"k_gemm_tn64": 590.125568e6 + 25.997568e6,   # DRAM read + write, one
            "k_zsolve64": 1.691865e9 + 865.253632e6,
            "k_emu_schur": 1.137726e9 + 3.871488e6}
 UNIT = "scenario condensations/s"
+REF_BUDGET_S = 150.0  # timed host seconds of the reference arm on the 10,000-bus workload
 
 
 def load_peaks():
@@ -157,19 +159,30 @@ def roofline(phases, dims, peaks, peak_kind, precision):
             "frac": ach / peaks["hbm_gbs"], "traffic": None}
 
 
-def cpu_baseline(workload, n_sample=8, min_s=10.0, max_iters=40):
+def oracle_sample(workload):
+    """Scenarios per oracle sample: all of the 1000-bus workload's 64 (one
+    IPM iteration ~5-10 s on the host), one of the 10,000-bus workload's 256
+    (one iteration on one scenario ~30-40 s)."""
+    n_bus, _, N, _, _ = synth.CONFIGS[workload]
+    return N if n_bus <= 2000 else 1
+
+
+def cpu_baseline(workload, min_s=10.0, max_iters=40):
     """The oracle, as it stands, on a bounded sample: IPM iterations from the
-    cold start on the first `n_sample` scenarios of the workload, until about
-    `min_s` seconds of CPU work (at least 2, at most `max_iters` iterations;
-    a converged solve restarts from the cold start)."""
+    cold start on the first oracle_sample(workload) scenarios of the
+    workload, until about `min_s` seconds of CPU work (at least 2 iterations
+    on the 1000-bus workload, 1 on the 10,000-bus one; at most `max_iters`; a
+    converged solve restarts from the cold start)."""
     from oracle import ipm as oipm
     from oracle import opf
+    n_sample = oracle_sample(workload)
     net, pd, qd = synth.workload(workload, n_scen=n_sample)
     M = opf.Model(net, pd, qd)
     st = oipm.initial_state(M)
     iters = 0
+    min_it = 2 if synth.CONFIGS[workload][0] <= 2000 else 1
     t0 = time.perf_counter()
-    while iters < max_iters and (iters < 2 or time.perf_counter() - t0 < min_s):
+    while iters < max_iters and (iters < min_it or time.perf_counter() - t0 < min_s):
         conv, _ = oipm.iterate(M, st)
         iters += 1
         if conv:
@@ -182,16 +195,23 @@ def cpu_baseline(workload, n_sample=8, min_s=10.0, max_iters=40):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step one oracle IPM iteration on
+    the sample of oracle_sample(workload) scenarios (from the cold start; a
+    converged solve restarts).  On the 10,000-bus workload a step takes about
+    30-40 s of host time, so the run stops after REF_BUDGET_S seconds of timed
+    steps (at least one) and skips the warm-up (CPU code needs none); the line
+    reports the steps it timed."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import ipm as oipm
     from oracle import opf
-    n_sample = 8
+    n_sample = oracle_sample(args.workload)
+    big = synth.CONFIGS[args.workload][0] > 2000
     net, pd, qd = synth.workload(args.workload, n_scen=n_sample)
     M = opf.Model(net, pd, qd)
     st = oipm.initial_state(M)
-    for _ in range(args.warmup):
+    for _ in range(0 if big else args.warmup):
         conv, _ = oipm.iterate(M, st)
         if conv:
             st = oipm.initial_state(M)
@@ -202,15 +222,18 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
         if conv:
             st = oipm.initial_state(M)
+        if big and sum(times) > REF_BUDGET_S:
+            break
     tot = sum(times)
-    val = n_sample * args.steps / tot
-    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+    val = n_sample * len(times) / tot
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
+            "warmup": 0 if big else args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "scenarios_timed": n_sample, "path": "oracle FP64 (CPU)"},
+            "config": {"workload": args.workload, "scenarios_timed": n_sample, "path": "oracle FP64 (CPU)",
+                       "steps_requested": args.steps},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"each step = one IPM iteration on {n_sample} scenarios"},
+                             "sample": f"each step = one IPM iteration on {n_sample} of the workload's scenarios"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -222,7 +245,7 @@ def fallback_count(sol):
     return int(sol.ipm_get_quantity(ipm.Q_INFO)[10])
 
 
-def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush, want_e2e=True):
+def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush, want_e2e=True, want_phases=True):
     """Time `steps` IPM iterations of one precision path (device events per step,
     L2 flushed between steps; graphs and autotuned launch shapes on), then the
     same number again with the phase timers on, and the end-to-end variant."""
@@ -277,7 +300,7 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
         # phase breakdown (events between phases; graphs are off while profiling)
         sol.ipm_set_state(ck, stream=stream)
         sol.ipm_set_profiling(2)
-        for k in range(steps):
+        for k in range(steps if want_phases else 0):
             flush.fill_(float(k))
             step()
         torch.cuda.synchronize()
@@ -307,7 +330,7 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
                     sol.ipm_init_state(stream=stream)
                     sol.ipm_get_state(hnp, stream=stream)
             e2e_val = world * N * len(e2e) / sum(e2e)
-    per = {p: phases[p][0] / steps for p in phases}
+    per = {p: phases[p][0] / steps for p in phases} if want_phases else {p: 0.0 for p in phases}
     # the reduced right-hand side runs on a side stream beside the split on
     # the FP64 paths (its phase time overlaps); on the mixed path it follows
     # the contraction
@@ -316,7 +339,7 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
     return dict(sol=sol, dims=dims, N=N, tot_ms=tot_ms, value=world * N * steps / (tot_ms / 1e3),
                 fallbacks=fallbacks,
                 ms_per_step=tot_ms / steps, phases=phases, phases_ms_per_step=per,
-                condense_only=N / (cond_ms / 1e3) if cond_ms > 0 else None,
+                condense_only=N * world / (cond_ms / 1e3) if cond_ms > 0 else None,
                 launches=launches1 - launches0, clocks=clk.summary(), e2e=e2e_val)
 
 
@@ -332,19 +355,36 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     net, pd, qd = synth.workload(args.workload)
+    big = synth.CONFIGS[args.workload][0] > 2000
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     main = measure_path(ipm, net, pd, qd, args.precision, args.steps, args.warmup, world, local, flush)
+    # free the headline context before the others (the 10,000-bus one holds ~210 GB)
+    main["sol"].close()
+    del main["sol"]
+    torch.cuda.empty_cache()
     others = {}
     if not args.no_compare:
         for p in ("fp64", "fp64_tc", "mixed"):
-            if p != args.precision:
-                r = measure_path(ipm, net, pd, qd, p, max(5, args.steps // 2), args.warmup, world, local, flush,
-                                 want_e2e=False)
-                others[p] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
-                             "condense_only": r["condense_only"], "fp64_fallback_iterations": r["fallbacks"],
-                             "phases_ms_per_step": {k: round(v, 3) for k, v in r["phases_ms_per_step"].items()},
-                             "clocks": r["clocks"]}
-                del r
+            if p == args.precision:
+                continue
+            # the 10,000-bus FP64 iteration takes ~20 s: two timed steps after one warm-up
+            csteps, cwarm = (2, 1) if big else (max(5, args.steps // 2), args.warmup)
+            try:
+                r = measure_path(ipm, net, pd, qd, p, csteps, cwarm, world, local, flush, want_e2e=False,
+                                 want_phases=not big)
+            except ipm.IPMError as e:
+                others[p] = {"unavailable": f"{e.kind}: this path's operands do not fit on one GPU at this size"
+                             if e.kind == "IPM_ERR_OOM" else str(e)}
+                torch.cuda.empty_cache()
+                continue
+            others[p] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"], "steps": csteps,
+                         "warmup": cwarm, "condense_only": r["condense_only"],
+                         "fp64_fallback_iterations": r["fallbacks"],
+                         "phases_ms_per_step": {k: round(v, 3) for k, v in r["phases_ms_per_step"].items()},
+                         "clocks": r["clocks"]}
+            r["sol"].close()
+            del r
+            torch.cuda.empty_cache()
     if rank != 0:
         return
     dims, N = main["dims"], main["N"]
@@ -442,18 +482,21 @@ def run_batch(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="opf1000_n64", choices=list(synth.CONFIGS) + ["batch_uneven"])
+    ap.add_argument("--workload", default="opf10000_n256", choices=list(synth.CONFIGS) + ["batch_uneven"])
     ap.add_argument("--instances", type=int, default=64, help="batch_uneven: number of instances")
     ap.add_argument("--max-iter", type=int, default=150, help="batch_uneven: IPM iteration limit")
-    ap.add_argument("--precision", default="fp64_tc", choices=["fp64", "mixed", "fp64_tc"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "fp64_tc"],
+                    help="headline path (default: mixed on the 10,000-bus workload, fp64_tc otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision paths")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.precision is None:
+        args.precision = "mixed" if args.workload == "opf10000_n256" else "fp64_tc"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch_uneven":

@@ -151,6 +151,10 @@ typedef struct {
   int lu_levels;         /* level-schedule depth of the LU / triangular solves */
   int nnz_kx, nnz_ku;    /* entries of the rows of [K_xx K_xu] and [K_ux] per scenario (the
                             products Y = K_x [Z; I], Y_u = K_u [Z; I]) */
+  int nd;                /* states in the dense trailing block of the LU of G_x */
+  int big_block;         /* 1 if that block is handled by the global-memory kernels */
+  long long lu_sparse_ops; /* multiply-adds of the sparse pivots per scenario (level lists and
+                              products into the trailing block) */
 } ipm_dims;
 
 ipm_status ipm_default_options(ipm_options *opt);

@@ -1467,6 +1467,9 @@ ipm_status ipm_get_dims(const ipm_ctx *c, ipm_dims *o) {
   o->lu_levels = c->S.nlev;
   o->nnz_kx = (int)c->S.kx_col.size();
   o->nnz_ku = (int)c->S.ku_col.size();
+  o->nd = c->S.nd;
+  o->big_block = c->S.big ? 1 : 0;
+  o->lu_sparse_ops = c->S.n_ops + c->S.n_tail_ops;
   return IPM_OK;
 }
 

@@ -61,7 +61,8 @@ class Dims(ctypes.Structure):
                 ("n_scen", ctypes.c_int), ("n_x", ctypes.c_int), ("n_u", ctypes.c_int), ("m", ctypes.c_int),
                 ("state_len", ctypes.c_longlong), ("step_len", ctypes.c_longlong),
                 ("nnz_lu", ctypes.c_longlong), ("lu_levels", ctypes.c_int),
-                ("nnz_kx", ctypes.c_int), ("nnz_ku", ctypes.c_int)]
+                ("nnz_kx", ctypes.c_int), ("nnz_ku", ctypes.c_int), ("nd", ctypes.c_int),
+                ("big_block", ctypes.c_int), ("lu_sparse_ops", ctypes.c_longlong)]
 
 
 _lib = None
