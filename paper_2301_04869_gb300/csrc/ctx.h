@@ -36,6 +36,11 @@ struct ipm_ctx {
   double *rhs_corr = nullptr, *cpos = nullptr;  // d(rhs_u)/d(delta); scratch [N][max(nx,nu)]
   double *gLu = nullptr, *HTt_u = nullptr;
   double *pg_curv = nullptr, *pmax_d = nullptr;
+  // large-block LU: trailing updates on the tensor cores at FP64 grade
+  // (mixed and FP64_TC paths), turned off for good if it ever gives a
+  // non-finite value
+  bool emu_lu_on = false;
+  EmuLuPlan emu_lu;
   // the paper's adjoint-solve reduction (IPM_REDUCTION_ADJOINT / _AUTO):
   // the columns of L_x as vectors [N][n_u][n_x], solved in place with G_x^T
   bool adjoint = false;

@@ -192,6 +192,17 @@ ipm_status alloc_work(ipm_ctx *c) {
   TRY(dalloc(c, &D.r4, N * m)); TRY(dalloc(c, &D.rh1x, N * nx)); TRY(dalloc(c, &D.rh2, nu));
   TRY(dalloc(c, &D.tv, N * m));
   TRY(dalloc(c, &D.LU, (long long)S.nnzLU * N)); TRY(dalloc(c, &D.rd, N * nx));
+  if (S.big && (c->opt.precision == IPM_PREC_MIXED || c->opt.precision == IPM_PREC_FP64_TC)) {
+    const size_t pb = emu_lu_planes_bytes((int)N, S.nd);
+    const long long rows = N * (long long)((S.nd + 127) / 128 * 128);
+    unsigned char *pa = nullptr, *pbp = nullptr;
+    int *ea = nullptr, *eb = nullptr;
+    TRY(dalloc(c, &pa, pb)); TRY(dalloc(c, &pbp, pb));
+    TRY(dalloc(c, &ea, rows)); TRY(dalloc(c, &eb, rows));
+    if (!emu_lu_plan(c->emu_lu, (int)N, S.nd, pa, pbp, ea, eb))
+      return fail(c, IPM_ERR_CUDA, "tensor maps of the large-block LU update");
+    c->emu_lu_on = true;
+  }
   TRY(dalloc(c, &D.flags, FLAG_COUNT));
   CK(cudaMemset(D.flags, 0, FLAG_COUNT * sizeof(int)));
   c->mixed = c->opt.precision == IPM_PREC_MIXED;
@@ -726,7 +737,7 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     ph_end(c, PH_COND, st);
     cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st);
     ph_begin(c, PH_LU, st);
-    launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st, c->opt.lu_pair != 0);
+    launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st, c->opt.lu_pair != 0, c->emu_lu_on ? &c->emu_lu : nullptr);
     ph_end(c, PH_LU, st);
     // first-stage diagonal of K_hat: Sigma_u + 2 c2_k on the non-slack Pg entries
     launch_lincomb(S.nu, c->diag1, 1.0, D.Su, 1.0, c->pg_curv, 0.0, nullptr, st);
@@ -806,6 +817,18 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
   ph_collect(c);
   if (c->h_flags[FLAG_SINGULAR]) return fail(c, IPM_ERR_SINGULAR_GX, "singular pivot in the LU of G_x");
   if (c->h_flags[FLAG_TIMEOUT]) return fail(c, IPM_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (c->emu_lu_on && c->h_flags[FLAG_NONFINITE]) {
+    // a non-finite value from the tensor-core LU update (or the contraction):
+    // factor on the FP64 units from now on and condense again
+    c->emu_lu_on = false;
+    for (int b = 0; b < 2; ++b) {
+      if (c->gx_pre[b]) cudaGraphExecDestroy(c->gx_pre[b]);
+      if (c->gx_post[b]) cudaGraphExecDestroy(c->gx_post[b]);
+      c->gx_pre[b] = c->gx_post[b] = nullptr;
+    }
+    CK(cudaMemsetAsync(D.flags, 0, FLAG_COUNT * sizeof(int), st));
+    return do_condense(c, st);
+  }
   if (fp64 && c->emu && !c->adjoint && c->h_flags[FLAG_NONFINITE]) {
     // the emulated contraction gave a non-finite value: redo it on the FP64 units
     ++c->n_emu_fallback;

@@ -38,9 +38,11 @@ void launch_condense(const DevSym &S, DevWork &D, cudaStream_t st);
 void launch_rhs(const DevSym &S, DevWork &D, const double *mu, double *gLu, double *HTt_u, cudaStream_t st);
 void launch_ugrad(const DevSym &S, DevWork &D, double *gLu, cudaStream_t st);
 
-// kernels_lu.cu
+struct EmuLuPlan;
+// kernels_lu.cu (emu_lu: the large-block LU's trailing updates on the tensor
+// cores at FP64 grade; null: on the FP64 units)
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
-                      cudaStream_t st, bool allow_pair = true);
+                      cudaStream_t st, bool allow_pair = true, const EmuLuPlan *emu_lu = nullptr);
 // g, b (optional, [N][n_x]): also b = G_x^{-1} g in position order (g in
 // state order), in an extra right-hand-side lane, when zsolve64_folds_b
 void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
@@ -48,7 +50,8 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
                      const double *g = nullptr, double *b = nullptr, int *ezy = nullptr);
 bool zsolve64_folds_b(const DevSym &S);
 // kernels_big.cu: the large trailing block (S.big) in global memory
-void launch_big_lu_dense(const DevSym &S, double *LU, double *rd, const double *amax, int *flags, cudaStream_t st);
+void launch_big_lu_dense(const DevSym &S, double *LU, double *rd, const double *amax, int *flags, cudaStream_t st,
+                         const EmuLuPlan *emu_lu = nullptr);
 void launch_big_trsm64(const DevSym &S, const double *LU, const double *rd, double *Z, cudaStream_t st);
 void launch_big_trsm32(const DevSym &S, const double *LU, const double *rd, float *Z, cudaStream_t st);
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
@@ -204,6 +207,19 @@ void launch_emu_split_pair(const EmuPlan &P, const double *Z, const double *Y, c
 void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st);
 void launch_emu_assemble(const EmuPlan &P, int N, const double *partial, const double *Yu, const double *diag,
                          double *Khat, cudaStream_t st);
+// the large-block LU's trailing update A22 -= L21 U12 at FP64 grade on the
+// tensor cores: slices of the N scenarios' L21 rows and U12 columns stacked
+// with stride Mp (nd rounded up to 128), planes [8][N Mp][64] each
+struct EmuLuPlan {
+  int N = 0, nd = 0, Mp = 0;
+  void *a_planes = nullptr, *b_planes = nullptr;
+  int *exp_a = nullptr, *exp_b = nullptr;
+  alignas(64) unsigned char maps[16 * 128];
+};
+size_t emu_lu_planes_bytes(int N, int nd);
+bool emu_lu_plan(EmuLuPlan &P, int N, int nd, void *a_planes, void *b_planes, int *exp_a, int *exp_b);
+void launch_emu_lu_update(const EmuLuPlan &P, double *LU, long long nnzlu, int dense_base, int kb, int ke, int *flags,
+                          cudaStream_t st);
 bool tc_set_operands(TcPlan &P, const void *a_planes, const void *b_planes);
 void launch_split_t(long long krows, int nu, long long kpad, const float *src, void *planes, cudaStream_t st);
 void launch_tc_schur(const TcPlan &P, double *partial, int *flags, cudaStream_t st);

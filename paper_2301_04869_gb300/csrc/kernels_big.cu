@@ -271,7 +271,8 @@ void btrsm(const DevSym &S, const double *LU, const double *rd, T *Z, cudaStream
 
 }  // namespace
 
-void launch_big_lu_dense(const DevSym &S, double *LU, double *rd, const double *amax, int *flags, cudaStream_t st) {
+void launch_big_lu_dense(const DevSym &S, double *LU, double *rd, const double *amax, int *flags, cudaStream_t st,
+                         const EmuLuPlan *emu_lu) {
   static const bool cap = cudaFuncSetAttribute(k_blu_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)gemm_smem()) == cudaSuccess;
   (void)cap;
@@ -283,9 +284,14 @@ void launch_big_lu_dense(const DevSym &S, double *LU, double *rd, const double *
     if (ke >= nd) break;
     k_blu_trsm<<<dim3((nd - ke + 7) / 8, S.N), 256, 0, st>>>(nd, S.nnzLU, S.dense_base, LU, kb, ke);
     ipm_count_launch();
-    const int nt = (nd - ke + TT - 1) / TT;
-    k_blu_gemm<<<dim3(nt * nt, S.N), 256, gemm_smem(), st>>>(nd, S.nnzLU, S.dense_base, LU, kb, ke, nt);
-    ipm_count_launch();
+    if (emu_lu) {
+      // FP64-grade on the tensor cores (exact 7-bit slices of L21, U12)
+      launch_emu_lu_update(*emu_lu, LU, S.nnzLU, S.dense_base, kb, ke, flags, st);
+    } else {
+      const int nt = (nd - ke + TT - 1) / TT;
+      k_blu_gemm<<<dim3(nt * nt, S.N), 256, gemm_smem(), st>>>(nd, S.nnzLU, S.dense_base, LU, kb, ke, nt);
+      ipm_count_launch();
+    }
   }
 }
 

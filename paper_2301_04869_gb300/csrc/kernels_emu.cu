@@ -275,10 +275,22 @@ __device__ __forceinline__ void tile_of_index(const int2 *tiles, int t, int &ti,
   tj = v.y;
 }
 
-__global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Maps maps, const int2 *tiles,
-                                                      int nu, int kb_total, int kb_per_group,
-                                                      const int *__restrict__ expA, const int *__restrict__ expB,
-                                                      double *partial, int *flags) {
+// The trailing update of the large-block LU (LU_OUT): the operands are the
+// scenarios' L21 (A side) and U12^T (B side) rows stacked with a fixed
+// stride Mp (a multiple of 128) per scenario, the contraction is the panel
+// width (KPG = 2: one group of 64), and the epilogue subtracts the tile
+// from the scenario's dense block instead of writing a partial tile.
+struct LuOut {
+  double *LU;
+  long long nnzlu;
+  int dense_base, nd, ke, Mp, na, nb;
+};
+
+template <int KPG, bool LU_OUT>
+__global__ void __launch_bounds__(320, 1) k_emu_mma(const __grid_constant__ Maps maps, const int2 *tiles,
+                                                    int nu, int kb_total, int kb_per_group,
+                                                    const int *__restrict__ expA, const int *__restrict__ expB,
+                                                    double *partial, int *flags, LuOut lo) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE_BYTES);  // [NSTAGE]
@@ -288,12 +300,19 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int ti, tj;
-  tile_of_index(tiles, blockIdx.x, ti, tj);
+  int ti, tj, lsc = 0;
+  if (LU_OUT) {
+    const int per = lo.na * lo.nb, r = blockIdx.x % per;
+    lsc = blockIdx.x / per;
+    ti = lsc * (lo.Mp / BM) + r / lo.nb;
+    tj = lsc * (lo.Mp / BN) + r % lo.nb;
+  } else {
+    tile_of_index(tiles, blockIdx.x, ti, tj);
+  }
   const int kb0 = blockIdx.y * kb_per_group;
   const int kb1 = min(kb_total, kb0 + kb_per_group);
-  const int nkb = kb1 - kb0;               // a multiple of KB_PER_GROUP
-  const int ngr = nkb / KB_PER_GROUP;
+  const int nkb = kb1 - kb0;               // a multiple of KPG
+  const int ngr = nkb / KPG;
   if (threadIdx.x == 0) {
     for (int q = 0; q < NSTAGE; ++q) {
       mbar_init(full + q, 1);
@@ -335,7 +354,7 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % NSTAGE;
-      const int d = i / KB_PER_GROUP, kbi = i % KB_PER_GROUP;
+      const int d = i / KPG, kbi = i % KPG;
       if (kbi == 0 && d >= 1 && !mbar_wait(acc_empty, (d - 1) & 1)) {
         flags[FLAG_TIMEOUT] = 1;
         *abort_flag = 1;
@@ -366,7 +385,7 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
         }
       }
       mma_commit(empty + s);
-      if (kbi == KB_PER_GROUP - 1) mma_commit(acc_full);
+      if (kbi == KPG - 1) mma_commit(acc_full);
     }
   } else if (warp >= 2) {
     // eight epilogue warps: lane quarter q (the TMEM lanes a warp may read)
@@ -386,7 +405,7 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const long long g = (kb0 / KB_PER_GROUP) + d;
+      const long long g = (kb0 / KPG) + d;
       const int ea = gi < nu ? expA[g * nu + gi] : 0;
 #pragma unroll
       for (int c0 = 0; c0 < HC; c0 += 16) {
@@ -431,11 +450,25 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty)) : "memory");
     }
-    double *out = partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * BM * BN + (size_t)row * BN + h * HC;
+    if (LU_OUT) {
+      // C -= tile on the valid rows and columns (a lane's row: consecutive
+      // lanes write consecutive rows of each column)
+      const int M = lo.nd - lo.ke, m = ti * BM - lsc * lo.Mp + row, n0 = tj * BN - lsc * lo.Mp + h * HC;
+      double *C = lo.LU + (size_t)lsc * lo.nnzlu + lo.dense_base;
+      if (m < M)
 #pragma unroll
-    for (int c = 0; c < HC; ++c) {
-      bad |= !isfinite(acc[c]);
-      out[c] = acc[c];
+        for (int c = 0; c < HC; ++c)
+          if (n0 + c < M) {
+            bad |= !isfinite(acc[c]);
+            C[(size_t)(lo.ke + n0 + c) * lo.nd + lo.ke + m] -= acc[c];
+          }
+    } else {
+      double *out = partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * BM * BN + (size_t)row * BN + h * HC;
+#pragma unroll
+      for (int c = 0; c < HC; ++c) {
+        bad |= !isfinite(acc[c]);
+        out[c] = acc[c];
+      }
     }
     if (bad) flags[FLAG_NONFINITE] = 1;
   }
@@ -447,6 +480,64 @@ __global__ void __launch_bounds__(320, 1) k_emu_schur(const __grid_constant__ Ma
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// Slices of the trailing update's operands for one panel [kb, ke) of the
+// large-block LU: stacked row r = s Mp + m (m < M = nd - ke) is row m of
+// L21 (side 0: L(ke + m, kb + k)) or column m of U12 (side 1:
+// U(kb + k, ke + m)), k = 0 .. ke - kb - 1 (at most 64); a warp per row: its
+// exponent e = ilogb(max |x|) + 2 and eight 7-bit digits per entry as in
+// k_emu_split, planes [NS][N Mp][64] (K-major); rows m >= M are zero.
+__global__ void __launch_bounds__(256) k_emu_lu_split(const double *__restrict__ LU, long long nnzlu, int dense_base,
+                                                      int nd, int kb, int ke, int Mp, int N,
+                                                      __nv_bfloat16 *pa, __nv_bfloat16 *pb, int *ea, int *eb) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, side = blockIdx.y;
+  if (r >= (long long)N * Mp) return;
+  const int sc = (int)(r / Mp), m = (int)(r - (long long)sc * Mp), M = nd - ke, pbw = ke - kb;
+  const double *A = LU + (size_t)sc * nnzlu + dense_base;
+  double x[2] = {0.0, 0.0};
+  if (m < M)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      if (k < pbw) x[h] = side == 0 ? A[(size_t)(kb + k) * nd + ke + m] : A[(size_t)(ke + m) * nd + kb + k];
+    }
+  unsigned long long key = 0;
+  int E[2];
+  long long mt[2];
+  bool neg[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    dsplit_bits(x[h], E[h], mt[h], neg[h]);
+    if (mt[h]) key = max(key, ((unsigned long long)E[h] << 53) | (unsigned long long)mt[h]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+    key = max(key, ok);
+  }
+  const int e = key > 0 ? (int)(key >> 53) - 1023 + 2 : 0;
+  __nv_bfloat16 *planes = side == 0 ? pa : pb;
+  if (lane == 0) (side == 0 ? ea : eb)[r] = e;
+  const size_t plane = (size_t)N * Mp * 64;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const long long X = mt[h] ? fixed56(E[h], mt[h], neg[h], e) : 0;
+    const unsigned long long Y = (unsigned long long)(X + DIGIT_OFFSET);
+    const uint32_t lo = (uint32_t)Y, hi = (uint32_t)(Y >> 32);
+    uint32_t d[NS];
+    d[0] = digit_bf16((int)hi >> 17);
+    d[1] = digit_bf16((int)((hi >> 10) & 127) - 64);
+    d[2] = digit_bf16((int)((hi >> 3) & 127) - 64);
+    d[3] = digit_bf16((int)(__funnelshift_r(lo, hi, 28) & 127) - 64);
+    d[4] = digit_bf16((int)((lo >> 21) & 127) - 64);
+    d[5] = digit_bf16((int)((lo >> 14) & 127) - 64);
+    d[6] = digit_bf16((int)((lo >> 7) & 127) - 64);
+    d[7] = digit_bf16((int)(lo & 127) - 64);
+    uint16_t *dst = reinterpret_cast<uint16_t *>(planes) + (size_t)r * 64 + lane + 32 * h;
+#pragma unroll
+    for (int t = 0; t < NS; ++t) dst[t * plane] = (uint16_t)d[t];
   }
 }
 
@@ -566,14 +657,15 @@ void launch_emu_split_pair(const EmuPlan &P, const double *Z, const double *Y, c
 }
 
 void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st) {
-  static const bool attr = cudaFuncSetAttribute(emu::k_emu_schur, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                emu::SMEM_BYTES) == cudaSuccess;
+  auto kern = emu::k_emu_mma<emu::KB_PER_GROUP, false>;
+  static const bool attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES) == cudaSuccess;
   (void)attr;
   emu::Maps m;
   memcpy(&m, P.maps, sizeof(m));
   dim3 grid(P.ntiles, P.ngroups);
-  emu::k_emu_schur<<<grid, 320, emu::SMEM_BYTES, st>>>(m, P.tiles, P.nu, P.kb_total, P.kb_per_group, P.exp_a,
-                                                      P.exp_b, partial, flags);
+  kern<<<grid, 320, emu::SMEM_BYTES, st>>>(m, P.tiles, P.nu, P.kb_total, P.kb_per_group, P.exp_a, P.exp_b, partial,
+                                           flags, emu::LuOut{});
   ipm_count_launch();
 }
 
@@ -681,4 +773,57 @@ done:
   for (void *p : {pa, pbp, part, (void *)ea, (void *)eb, (void *)tof, (void *)flags, (void *)tiles, (void *)rsd})
     if (p) cudaFree(p);
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// The trailing update A22 -= L21 U12 of the large-block LU at FP64 grade on
+// the tensor cores (the emulated product above with one 64-row group).
+bool emu_lu_plan(EmuLuPlan &P, int N, int nd, void *a_planes, void *b_planes, int *exp_a, int *exp_b) {
+  P.N = N;
+  P.nd = nd;
+  P.Mp = (nd + emu::BM - 1) / emu::BM * emu::BM;
+  P.a_planes = a_planes;
+  P.b_planes = b_planes;
+  P.exp_a = exp_a;
+  P.exp_b = exp_b;
+  const long long rows = (long long)N * P.Mp;
+  if (rows > 0x7fffffffLL) return false;
+  emu::Maps m;
+  const size_t plane = (size_t)rows * 64 * 2;
+  for (int p = 0; p < emu::NS; ++p) {
+    if (!tc_make_kmajor_map_box(&m.a[p], (const char *)a_planes + p * plane, (int)rows, 64, emu::BM, emu::BK))
+      return false;
+    if (!tc_make_kmajor_map_box(&m.b[p], (const char *)b_planes + p * plane, (int)rows, 64, emu::BN, emu::BK))
+      return false;
+  }
+  static_assert(sizeof(emu::Maps) <= sizeof(P.maps), "map storage");
+  memcpy(P.maps, &m, sizeof(m));
+  return true;
+}
+
+size_t emu_lu_planes_bytes(int N, int nd) {
+  const long long Mp = (nd + emu::BM - 1) / emu::BM * emu::BM;
+  return (size_t)emu::NS * N * Mp * 64 * 2;
+}
+
+void launch_emu_lu_update(const EmuLuPlan &P, double *LU, long long nnzlu, int dense_base, int kb, int ke, int *flags,
+                          cudaStream_t st) {
+  const int M = P.nd - ke;
+  if (M <= 0) return;
+  const long long rows = (long long)P.N * P.Mp;
+  emu::k_emu_lu_split<<<dim3((unsigned)((rows * 32 + 255) / 256), 2), 256, 0, st>>>(
+      LU, nnzlu, dense_base, P.nd, kb, ke, P.Mp, P.N, (__nv_bfloat16 *)P.a_planes, (__nv_bfloat16 *)P.b_planes,
+      P.exp_a, P.exp_b);
+  ipm_count_launch();
+  auto kern = emu::k_emu_mma<2, true>;
+  static const bool attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES) == cudaSuccess;
+  (void)attr;
+  emu::Maps m;
+  memcpy(&m, P.maps, sizeof(m));
+  emu::LuOut lo{LU, nnzlu, dense_base, P.nd, ke, P.Mp, (M + emu::BM - 1) / emu::BM, (M + emu::BN - 1) / emu::BN};
+  const long long grid = (long long)P.N * lo.na * lo.nb;
+  kern<<<dim3((unsigned)grid, 1), 320, emu::SMEM_BYTES, st>>>(m, nullptr, (int)rows, 2, 2, P.exp_a, P.exp_b, nullptr,
+                                                             flags, lo);
+  ipm_count_launch();
 }

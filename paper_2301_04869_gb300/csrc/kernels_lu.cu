@@ -816,7 +816,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
 }  // namespace
 
 void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, double *rd, int *flags,
-                      cudaStream_t st, bool allow_pair) {
+                      cudaStream_t st, bool allow_pair, const EmuLuPlan *emu_lu) {
   // trailing sub-block held in shared memory: as large as fits next to the
   // kernel's static shared memory (170 x 170 doubles on GB300)
   static const int ns_max = [] {
@@ -842,7 +842,7 @@ void launch_lu_factor(const DevSym &S, int nL, const double *J, double *LU, doub
   if (S.big) {
     // sparse part (one CTA per scenario), then the block by the batched kernels
     k_lu_factor<<<S.N, 512, 0, st>>>(S, nL, J, LU, rd, flags, 1e-14, 0); ipm_count_launch();
-    launch_big_lu_dense(S, LU, rd, S.lu_amax, flags, st);
+    launch_big_lu_dense(S, LU, rd, S.lu_amax, flags, st, emu_lu);
     return;
   }
   const int np = (S.nd + 15) / 16, ldl = ((np + 1) / 2) * 16;
