@@ -163,7 +163,7 @@ def oracle_sample(workload):
     """Scenarios per oracle sample: all of the 1000-bus workload's 64 (one
     IPM iteration ~5-10 s on the host), one of the 10,000-bus workload's 256
     (one iteration on one scenario ~30-40 s)."""
-    n_bus, _, N, _, _ = synth.CONFIGS[workload]
+    n_bus, _, N = synth.CONFIGS[workload][:3]
     return N if n_bus <= 2000 else 1
 
 

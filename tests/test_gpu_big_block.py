@@ -121,3 +121,28 @@ def test_10000_bus_condensation(gpu, net10k, precision):
     assert rel(sol.ipm_get_quantity(gpu.Q_RHS_U), C.rhs_u) <= TOL
     for i in range(M.N):
         assert rel(sol.ipm_get_quantity(gpu.Q_Z, i).reshape(nx, nu), C.Z[i]) <= zbar
+
+
+@pytest.mark.slow
+def test_10000_bus_load_scale(gpu):
+    """Why the 10,000-bus workload scales its loads by 0.2, not the 0.3 of the
+    1000-bus one: at 0.3 the interior-point method's primal residual stalls
+    above 0.1 pu while its multipliers grow (infeasible); at 0.2 the same
+    network solves to 1e-8."""
+    out = {}
+    for scale, iters in ((0.3, 80), (0.2, 120)):
+        net = synth.make_network(10000, 1000, seed=0, load_scale=scale)
+        pd, qd = synth.make_scenarios(net, 1, 0.05, seed=1)
+        sol = gpu.Solver(net, pd, qd, precision=PRECS["mixed"])
+        conv = False
+        for _ in range(iters):
+            conv, e = sol.ipm_step()
+            if conv:
+                break
+        out[scale] = (conv, sol.ipm_get_quantity(gpu.Q_ERRS))
+        sol.close()
+    conv3, errs3 = out[0.3]
+    assert not conv3 and errs3[1] >= 0.1 and errs3[0] >= 1e3, errs3
+    conv2, errs2 = out[0.2]
+    assert conv2
+    assert synth.CONFIGS["opf10000_n256"][5] == 0.2
