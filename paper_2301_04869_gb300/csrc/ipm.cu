@@ -1184,12 +1184,11 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
     TRY(read_red(c, 1, st));
     const double dmax = c->h_red[0];
     for (double f = 1e-8; f <= 1e-5 * 1.0001 && !pd; f *= 10.0) TRY(do_factor(c, 0.0, &pd, st, f * dmax));
-    if (!pd) {
-      c->exact_iter = true;
-      ++c->n_fallback;
-      TRY(do_condense(c, st));
-      TRY(do_factor(c, 0.0, &pd, st));
-    }
+    // Still not positive definite: the reduced matrix is indefinite by more
+    // than the BF16x3 error, so the delta_w rule below corrects the inertia
+    // on it (the refinement on the exact operator at that delta_w checks the
+    // decision: non-positive curvature there still sends the iteration to
+    // the FP64 condensation).
   }
   double delta = 0.0;
   if (!pd) {

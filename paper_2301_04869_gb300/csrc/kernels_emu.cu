@@ -275,22 +275,26 @@ __device__ __forceinline__ void tile_of_index(const int2 *tiles, int t, int &ti,
   tj = v.y;
 }
 
-// The trailing update of the large-block LU (LU_OUT): the operands are the
-// scenarios' L21 (A side) and U12^T (B side) rows stacked with a fixed
-// stride Mp (a multiple of 128) per scenario, the contraction is the panel
-// width (KPG = 2: one group of 64), and the epilogue subtracts the tile
-// from the scenario's dense block instead of writing a partial tile.
-struct LuOut {
-  double *LU;
-  long long nnzlu;
-  int dense_base, nd, ke, Mp, na, nb;
+// Batched updates C -= A B (MODE 1, 2): the operands are the scenarios' A
+// rows and B columns stacked with fixed strides mpa, mpb (multiples of 128)
+// per scenario, the contraction is one 64-wide block (KPG = 2: one group),
+// and the epilogue subtracts the tile from the scenario's output instead of
+// writing a partial tile: MODE 1 a column-major FP64 block (the large-block
+// LU's trailing update), MODE 2 a row-major FP32 block (the multi-RHS
+// solve's block updates on the mixed path).  Rows m < M and columns n < ncol
+// of a scenario are written, at out + s stride + (roff + m) rs + (coff + n) cs.
+struct TileOut {
+  void *out;
+  long long stride;
+  long long rs, cs;
+  int roff, coff, M, ncol, mpa, mpb, na, nb;
 };
 
-template <int KPG, bool LU_OUT>
+template <int KPG, int MODE>
 __global__ void __launch_bounds__(320, 1) k_emu_mma(const __grid_constant__ Maps maps, const int2 *tiles,
                                                     int nu, int kb_total, int kb_per_group,
                                                     const int *__restrict__ expA, const int *__restrict__ expB,
-                                                    double *partial, int *flags, LuOut lo) {
+                                                    double *partial, int *flags, TileOut lo) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE_BYTES);  // [NSTAGE]
@@ -301,11 +305,11 @@ __global__ void __launch_bounds__(320, 1) k_emu_mma(const __grid_constant__ Maps
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int ti, tj, lsc = 0;
-  if (LU_OUT) {
+  if (MODE != 0) {
     const int per = lo.na * lo.nb, r = blockIdx.x % per;
     lsc = blockIdx.x / per;
-    ti = lsc * (lo.Mp / BM) + r / lo.nb;
-    tj = lsc * (lo.Mp / BN) + r % lo.nb;
+    ti = lsc * (lo.mpa / BM) + r / lo.nb;
+    tj = lsc * (lo.mpb / BN) + r % lo.nb;
   } else {
     tile_of_index(tiles, blockIdx.x, ti, tj);
   }
@@ -450,18 +454,20 @@ __global__ void __launch_bounds__(320, 1) k_emu_mma(const __grid_constant__ Maps
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty)) : "memory");
     }
-    if (LU_OUT) {
-      // C -= tile on the valid rows and columns (a lane's row: consecutive
-      // lanes write consecutive rows of each column)
-      const int M = lo.nd - lo.ke, m = ti * BM - lsc * lo.Mp + row, n0 = tj * BN - lsc * lo.Mp + h * HC;
-      double *C = lo.LU + (size_t)lsc * lo.nnzlu + lo.dense_base;
-      if (m < M)
+    if (MODE != 0) {
+      // out -= tile on the valid rows and columns
+      const int m = ti * BM - lsc * lo.mpa + row, n0 = tj * BN - lsc * lo.mpb + h * HC;
+      if (m < lo.M) {
+        const size_t rbase = (size_t)lsc * lo.stride + (size_t)(lo.roff + m) * lo.rs;
 #pragma unroll
         for (int c = 0; c < HC; ++c)
-          if (n0 + c < M) {
+          if (n0 + c < lo.ncol) {
             bad |= !isfinite(acc[c]);
-            C[(size_t)(lo.ke + n0 + c) * lo.nd + lo.ke + m] -= acc[c];
+            const size_t at = rbase + (size_t)(lo.coff + n0 + c) * lo.cs;
+            if (MODE == 1) static_cast<double *>(lo.out)[at] -= acc[c];
+            else static_cast<float *>(lo.out)[at] -= (float)acc[c];
           }
+      }
     } else {
       double *out = partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * BM * BN + (size_t)row * BN + h * HC;
 #pragma unroll
@@ -657,7 +663,7 @@ void launch_emu_split_pair(const EmuPlan &P, const double *Z, const double *Y, c
 }
 
 void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_t st) {
-  auto kern = emu::k_emu_mma<emu::KB_PER_GROUP, false>;
+  auto kern = emu::k_emu_mma<emu::KB_PER_GROUP, 0>;
   static const bool attr =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES) == cudaSuccess;
   (void)attr;
@@ -665,7 +671,7 @@ void launch_emu_schur(const EmuPlan &P, double *partial, int *flags, cudaStream_
   memcpy(&m, P.maps, sizeof(m));
   dim3 grid(P.ntiles, P.ngroups);
   kern<<<grid, 320, emu::SMEM_BYTES, st>>>(m, P.tiles, P.nu, P.kb_total, P.kb_per_group, P.exp_a, P.exp_b, partial,
-                                           flags, emu::LuOut{});
+                                           flags, emu::TileOut{});
   ipm_count_launch();
 }
 
@@ -815,13 +821,15 @@ void launch_emu_lu_update(const EmuLuPlan &P, double *LU, long long nnzlu, int d
       LU, nnzlu, dense_base, P.nd, kb, ke, P.Mp, P.N, (__nv_bfloat16 *)P.a_planes, (__nv_bfloat16 *)P.b_planes,
       P.exp_a, P.exp_b);
   ipm_count_launch();
-  auto kern = emu::k_emu_mma<2, true>;
+  auto kern = emu::k_emu_mma<2, 1>;
   static const bool attr =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES) == cudaSuccess;
   (void)attr;
   emu::Maps m;
   memcpy(&m, P.maps, sizeof(m));
-  emu::LuOut lo{LU, nnzlu, dense_base, P.nd, ke, P.Mp, (M + emu::BM - 1) / emu::BM, (M + emu::BN - 1) / emu::BN};
+  // C = the dense block, column-major: (ke + m, ke + n) at dense_base + (ke + n) nd + ke + m
+  emu::TileOut lo{LU + dense_base, nnzlu, 1, P.nd, ke, ke, M, M, P.Mp, P.Mp,
+                  (M + emu::BM - 1) / emu::BM, (M + emu::BN - 1) / emu::BN};
   const long long grid = (long long)P.N * lo.na * lo.nb;
   kern<<<dim3((unsigned)grid, 1), 320, emu::SMEM_BYTES, st>>>(m, nullptr, (int)rows, 2, 2, P.exp_a, P.exp_b, nullptr,
                                                              flags, lo);
