@@ -41,6 +41,8 @@ METRIC = "scenario condensations/s & s per IPM iter (mixed vs FP64 path, 1e-8 KK
 # FP64 arithmetic peak of a GB300: 2 FP64 FMA per clock per SM x 152 SMs x 2.07 GHz = 1.259 TFLOP/s,
 # the 1.25 TFLOP/s FP64 figure of the profiling recipe (a cuBLAS DGEMM measured 1.10 TFLOP/s here).
 FP64_PEAK_TFLOPS = 1.25
+# FP32 (SIMT) arithmetic peak: 128 FP32 FMA per clock per SM x 152 SMs x 2.07 GHz = 80.5 TFLOP/s.
+FP32_PEAK_TFLOPS = 80.5
 # DRAM bytes per launch from one ncu capture of the kernel as it stands (profiles/); None once the
 # kernel changes until it is captured again.
 TRAFFIC = {"k_gemm_tn64": 590.125568e6 + 25.997568e6,   # DRAM read + write, one launch, 1000 buses x 64
@@ -110,7 +112,8 @@ def emu_issued_flops(nu, krows):
 
 def roofline(phases, dims, peaks, peak_kind, precision):
     """Roofline entry for the dominant kernel phase (device time share)."""
-    name = max(phases, key=lambda k: phases[k][0])
+    # the fallback phase (a mixed iteration condensed again in FP64) spans many kernels
+    name = max((k for k in phases if k != "fallback"), key=lambda k: phases[k][0])
     ms, calls = phases[name]
     N, nx, nu = dims.n_scen, dims.n_x, dims.n_u
     per_call_s = ms / 1e3 / max(calls, 1)
@@ -139,19 +142,32 @@ def roofline(phases, dims, peaks, peak_kind, precision):
                 "traffic": TRAFFIC.get("k_gemm_tn64"),
                 "algorithmic": f"{kflops:.4g} flop/launch"}
     if name == "zsolve":
-        # the solves with n_u + 1 dense right-hand sides (the columns of G_u and g) and the
-        # products Y = K_x [Z; I], Y_u = K_u [Z; I]
-        solve = 2.0 * dims.nnz_lu * (nu + 1) * N
+        # the solves with the n_u (+ 1 on the FP64 paths) dense right-hand sides (the columns of
+        # G_u and g) and the products Y = K_x [Z; I], Y_u = K_u [Z; I]
+        nrhs = nu if precision == "mixed" else nu + 1
+        solve = 2.0 * dims.nnz_lu * nrhs * N
         prod = 2.0 * (dims.nnz_kx + dims.nnz_ku) * nu * N
         flops = solve + prod
         ach = flops / per_call_s / 1e12
-        return {"kernel": "k_zsolve64 (FP64 multi-RHS solves + products with K)", "bound": "alu", "achieved": ach,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": TRAFFIC.get("k_zsolve64"),
+        if precision == "mixed":
+            kern = ("k_zsolve32 + k_btrsm_diag/update (FP32 multi-RHS solves, the dense trailing block by "
+                    "batched blocked triangular solves, products with K)")
+            pk = FP32_PEAK_TFLOPS
+        else:
+            kern = "k_zsolve64 (FP64 multi-RHS solves + products with K)"
+            pk = fp64_peak
+        return {"kernel": kern, "bound": "alu", "achieved": ach,
+                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": TRAFFIC.get("k_zsolve64") if precision != "mixed" else None,
                 "algorithmic": f"{flops:.4g} flop/launch ({solve:.4g} solves + {prod:.4g} products with K)"}
     if name == "lu":
-        return {"kernel": "k_lu_factor", "bound": "alu", "achieved": None, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": None, "traffic": None}
+        # sparse eliminations (one FMA each) and, with a dense trailing block, its LU (2/3 nd^3)
+        flops = (2.0 * dims.lu_sparse_ops + (2.0 / 3.0) * dims.nd ** 3) * N
+        ach = flops / per_call_s / 1e12
+        return {"kernel": "k_lu_factor + trailing-block LU (k_blu_*; FP64-grade tensor-core updates on the "
+                          "mixed and FP64_TC paths)" if dims.big_block else "k_lu_factor_pair",
+                "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": None, "algorithmic": f"{flops:.4g} FP64 flop/launch"}
     # bandwidth-type phases: bytes of Z and Y touched
     byt = 8.0 * nx * nu * N * 2
     ach = byt / per_call_s / 1e9
@@ -245,10 +261,19 @@ def fallback_count(sol):
     return int(sol.ipm_get_quantity(ipm.Q_INFO)[10])
 
 
-def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush, want_e2e=True, want_phases=True):
+def raise_count(sol):
+    """Times a mixed-precision context raised delta_w after CG met non-positive
+    curvature of the exact reduced operator (IPM_Q_INFO; 0 on the FP64 paths)."""
+    from paper_2301_04869_gb300 import ipm
+    return int(sol.ipm_get_quantity(ipm.Q_INFO)[18])
+
+
+def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush, want_e2e=True, want_phases=True,
+                 phase_steps=None):
     """Time `steps` IPM iterations of one precision path (device events per step,
     L2 flushed between steps; graphs and autotuned launch shapes on), then the
-    same number again with the phase timers on, and the end-to-end variant."""
+    first `phase_steps` (default all) of the same iterates again with the phase
+    timers on, and the same iterates end to end."""
     import torch
     prec = {"fp64": ipm.PREC_FP64, "mixed": ipm.PREC_MIXED, "fp64_tc": ipm.PREC_FP64_TC}[precision]
     stream = torch.cuda.Stream()
@@ -269,7 +294,7 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
         # so all three passes time the same iterates
         ck = torch.empty(dims.state_len, dtype=torch.float64, device="cuda")
         sol.ipm_get_state(ck, stream=stream)
-        fb0 = fallback_count(sol)
+        fb0, rc0 = fallback_count(sol), raise_count(sol)
         _, launches0 = sol.timers()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
@@ -291,7 +316,7 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
         if world > 1:
             torch.distributed.barrier()
         _, launches1 = sol.timers()
-        fallbacks = fallback_count(sol) - fb0
+        fallbacks, raises = fallback_count(sol) - fb0, raise_count(sol) - rc0
         tot_ms = sum(a.elapsed_time(b) for a, b in ev)
         if world > 1:
             t = torch.tensor([tot_ms], device="cuda")
@@ -300,7 +325,8 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
         # phase breakdown (events between phases; graphs are off while profiling)
         sol.ipm_set_state(ck, stream=stream)
         sol.ipm_set_profiling(2)
-        for k in range(steps if want_phases else 0):
+        n_ph = (phase_steps or steps) if want_phases else 0
+        for k in range(n_ph):
             flush.fill_(float(k))
             step()
         torch.cuda.synchronize()
@@ -330,14 +356,14 @@ def measure_path(ipm, net, pd, qd, precision, steps, warmup, world, local, flush
                     sol.ipm_init_state(stream=stream)
                     sol.ipm_get_state(hnp, stream=stream)
             e2e_val = world * N * len(e2e) / sum(e2e)
-    per = {p: phases[p][0] / steps for p in phases} if want_phases else {p: 0.0 for p in phases}
+    per = {p: phases[p][0] / n_ph for p in phases} if n_ph else {p: 0.0 for p in phases}
     # the reduced right-hand side runs on a side stream beside the split on
     # the FP64 paths (its phase time overlaps); on the mixed path it follows
     # the contraction
     cond = ("condense_K", "lu", "zsolve", "split", "gemm") + (("reduced_rhs",) if precision == "mixed" else ())
     cond_ms = sum(per[p] for p in cond)
     return dict(sol=sol, dims=dims, N=N, tot_ms=tot_ms, value=world * N * steps / (tot_ms / 1e3),
-                fallbacks=fallbacks,
+                fallbacks=fallbacks, raises=raises,
                 ms_per_step=tot_ms / steps, phases=phases, phases_ms_per_step=per,
                 condense_only=N * world / (cond_ms / 1e3) if cond_ms > 0 else None,
                 launches=launches1 - launches0, clocks=clk.summary(), e2e=e2e_val)
@@ -354,10 +380,12 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    net, pd, qd = synth.workload(args.workload)
+    net, pd, qd = synth.workload(args.workload, n_scen=args.scenarios)
     big = synth.CONFIGS[args.workload][0] > 2000
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    main = measure_path(ipm, net, pd, qd, args.precision, args.steps, args.warmup, world, local, flush)
+    # the 10,000-bus phase breakdown takes the first 4 of the timed iterates
+    main = measure_path(ipm, net, pd, qd, args.precision, args.steps, args.warmup, world, local, flush,
+                        phase_steps=min(args.steps, 4) if big else None)
     # free the headline context before the others (the 10,000-bus one holds ~210 GB)
     main["sol"].close()
     del main["sol"]
@@ -379,7 +407,7 @@ def run_ours(args):
                 continue
             others[p] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"], "steps": csteps,
                          "warmup": cwarm, "condense_only": r["condense_only"],
-                         "fp64_fallback_iterations": r["fallbacks"],
+                         "fp64_fallback_iterations": r["fallbacks"], "curvature_raises": r["raises"],
                          "phases_ms_per_step": {k: round(v, 3) for k, v in r["phases_ms_per_step"].items()},
                          "clocks": r["clocks"]}
             r["sol"].close()
@@ -396,7 +424,8 @@ def run_ours(args):
     cb = cpu_baseline(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
     paths = {args.precision: {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"],
                               "condense_only": main["condense_only"],
-                              "fp64_fallback_iterations": main["fallbacks"]}}
+                              "fp64_fallback_iterations": main["fallbacks"],
+                              "curvature_raises": main["raises"]}}
     paths.update(others)
     line = {
         "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -404,7 +433,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "bf16x3+f64", "fp64_tc": "f64 (bf16 slices)"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_bus": dims.n_bus, "n_scen": N, "n_x": dims.n_x, "n_u": dims.n_u,
+        "config": {"workload": args.workload + (f" (first {N} scenarios)" if args.scenarios else ""),
+                   "n_bus": dims.n_bus, "n_scen": N, "n_x": dims.n_x, "n_u": dims.n_u,
                    "path": args.precision, "l2": "flushed between steps (256 MB write)",
                    "graphs": True, "autotune": True,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -482,7 +512,8 @@ def run_batch(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed IPM iterations (default 10; 6 on the 10,000-bus workload)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="opf10000_n256", choices=list(synth.CONFIGS) + ["batch_uneven"])
@@ -490,6 +521,9 @@ def main():
     ap.add_argument("--max-iter", type=int, default=150, help="batch_uneven: IPM iteration limit")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "fp64_tc"],
                     help="headline path (default: mixed on the 10,000-bus workload, fp64_tc otherwise)")
+    ap.add_argument("--scenarios", type=int, default=None,
+                    help="scenarios of the workload's network (default: the workload's own count); a smaller "
+                         "count is for profiling captures, and the line's config then names it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision paths")
     args = ap.parse_args()
@@ -497,6 +531,8 @@ def main():
         args.warmup = 3
     if args.precision is None:
         args.precision = "mixed" if args.workload == "opf10000_n256" else "fp64_tc"
+    if args.steps is None:
+        args.steps = 6 if args.workload in synth.CONFIGS and synth.CONFIGS[args.workload][0] > 2000 else 10
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch_uneven":

@@ -99,7 +99,9 @@ typedef struct {
   double tol;            /* KKT residual E_0 target (1e-8) */
   int max_iter;          /* 200 */
   int precision;         /* IPM_PREC_FP64, IPM_PREC_MIXED or IPM_PREC_FP64_TC */
-  int max_refine;        /* iterative-refinement sweeps of the KKT solve (mixed) */
+  int max_refine;        /* mixed path: conjugate-gradient iterations on the exact reduced
+                            operator, preconditioned by the BF16x3 factor (default 60); an
+                            iteration whose CG does not reach 1e-10 is condensed again in FP64 */
   int solve_threads;     /* threads per CTA of the multi-RHS solves: 128 or 256 (0 = 256,
                             or the autotuner's choice) */
   int barrier_rule;      /* IPM_BARRIER_ADAPTIVE (default): mu = max(tol/10, sigma * mean
@@ -135,6 +137,10 @@ typedef struct {
                             takes the sparse pivots just before it that reach a sixth of it);
                             1: the global-memory kernels whatever its size */
   double sigma;          /* centring factor of the adaptive rule (0.1) */
+  int tc_solve;          /* mixed path with a dense trailing block too large for shared memory
+                            (big_block): 1 (default) the block updates of the multi-RHS solve as
+                            BF16x3 products on the tensor cores (FP32 accumulation), 0 FP32 on
+                            the SIMT units */
 } ipm_options;
 
 /* Sizes of a context.  state_len = 4 N n_x + 4 N m + 3 n_u + 3; the state
@@ -264,7 +270,10 @@ ipm_status ipm_solve(ipm_ctx *ctx, int *iters, double *kkt_err, void *stream);
  *        FP64 units, for the last solve the refinement steps on the
  *        augmented system eq. (6), its relative residual before and after
  *        them, then 1 if K_hat is formed by the adjoint-solve reduction, and
- *        the autotuner's times (ms) of the dense and the adjoint reduction),
+ *        the autotuner's times (ms) of the dense and the adjoint reduction,
+ *        and the number of times since ipm_create that the mixed path raised
+ *        delta_w because CG met non-positive curvature of the exact
+ *        operator),
  *        IPM_Q_TIMERS (2*IPM_N_PHASES doubles: accumulated device milliseconds
  *        and call counts per phase, see ipm_set_profiling; a further double,
  *        if cap allows, is the total number of kernels the library launched).
@@ -276,11 +285,15 @@ ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
 
 /* Phase timers (tracing).  When on, CUDA events are recorded on the call's
  * stream around each phase of the path and the elapsed device time is
- * accumulated; on = 2 also resets the accumulators.  Phases, in order:
+ * accumulated (a phase met several times in one iteration counts each
+ * time); on = 2 also resets the accumulators.  Phases, in order:
  * eval, condense_K (Sigma, K, right-hand sides), lu, zsolve (Z and Y),
  * gemm (Z^T Y + scenario sum), reduced_rhs, cholesky, recover, linesearch,
- * split (the tensor-core operands of Z and Y: BF16 slices or planes). */
-enum { IPM_N_PHASES = 10 };
+ * split (the tensor-core operands of Z and Y: BF16 slices or planes),
+ * fallback (mixed path: the whole FP64 condensation and solve of an
+ * iteration condensed again; its inner phases are not added to the others).
+ * Profiling serialises the host with the device at phase boundaries. */
+enum { IPM_N_PHASES = 11 };
 ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
 
 /* Kernels this library has launched in the process so far (all contexts;

@@ -41,6 +41,8 @@ struct ipm_ctx {
   // non-finite value
   bool emu_lu_on = false;
   EmuLuPlan emu_lu;
+  bool tcs_on = false;  // mixed, large trailing block: its solve updates on the tensor cores
+  TcsPlan tcs;
   // the paper's adjoint-solve reduction (IPM_REDUCTION_ADJOINT / _AUTO):
   // the columns of L_x as vectors [N][n_u][n_x], solved in place with G_x^T
   bool adjoint = false;
@@ -65,8 +67,10 @@ struct ipm_ctx {
   int refine_iters = 0;
   double refine_res = 0.0;
   bool neg_curv = false;     // CG met p^T A p <= 0
+  double curv_q = 0.0;       // and the Rayleigh quotient p^T A p / p^T p there
   bool exact_iter = false;   // this iteration runs the FP64 condensation (mixed fallback)
   long long n_fallback = 0;  // mixed-path iterations that needed the FP64 condensation
+  long long n_curv_raise = 0;  // mixed path: delta_w raised after CG met non-positive curvature
   double *step = nullptr, *px = nullptr, *pu = nullptr, *ps = nullptr, *py = nullptr, *pz = nullptr;
   // iterative refinement on the residual of the augmented system eq. (6):
   // residual blocks (reused as the correction's right-hand side), the

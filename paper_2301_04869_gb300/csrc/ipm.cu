@@ -263,6 +263,17 @@ ipm_status alloc_work(ipm_ctx *c) {
       c->tc_max_groups = std::max(big.ngroups, c->planZY.ngroups);
     }
     TRY(dalloc(c, &c->tcpart, (long long)c->tc_max_groups * c->planZY.ntiles * 128 * 128));
+    if (S.big && c->opt.tc_solve) {
+      // BF16x3 planes of the trailing factor block and of the finished rows
+      // of Z_d for the tensor-core block updates; padding stays zero
+      const size_t tb = tcs_planes_bytes((int)N, S.nd, (int)nu);
+      unsigned char *tp = nullptr;
+      TRY(dalloc(c, &tp, (tb + 255) / 256 * 256));
+      CK(cudaMemset(tp, 0, tb));
+      if (!tcs_plan(c->tcs, (int)N, S.nd, (int)nu, tp))
+        return fail(c, IPM_ERR_CUDA, "tensor maps of the tensor-core block solve");
+      c->tcs_on = true;
+    }
     TRY(dalloc(c, &c->pcg_b, nu)); TRY(dalloc(c, &c->pcg_r, nu)); TRY(dalloc(c, &c->pcg_z, nu));
     TRY(dalloc(c, &c->pcg_p, nu)); TRY(dalloc(c, &c->pcg_Ap, nu));
   }
@@ -359,29 +370,40 @@ ipm_status read_red(ipm_ctx *c, int nv, cudaStream_t st) {
 }
 
 
-enum { PH_EVAL = 0, PH_COND, PH_LU, PH_ZSOLVE, PH_GEMM, PH_RRHS, PH_CHOL, PH_RECOVER, PH_LS, PH_SPLIT };
+// the tensor-core block-solve plan of a mixed context, or null
+inline const TcsPlan *tcs_of(const ipm_ctx *c) { return c->tcs_on ? &c->tcs : nullptr; }
 
+enum { PH_EVAL = 0, PH_COND, PH_LU, PH_ZSOLVE, PH_GEMM, PH_RRHS, PH_CHOL, PH_RECOVER, PH_LS, PH_SPLIT,
+       PH_FALLBACK };
+
+// accumulate one finished phase (waits for its end event)
+void ph_take(ipm_ctx *c, int p) {
+  if (!c->ev_pending[p]) return;
+  float ms = 0.f;
+  cudaEventSynchronize(c->ev[2 * p + 1]);
+  if (cudaEventElapsedTime(&ms, c->ev[2 * p], c->ev[2 * p + 1]) == cudaSuccess) {
+    c->t_ms[p] += ms;
+    c->t_cnt[p] += 1;
+  }
+  c->ev_pending[p] = false;
+}
+// A mixed-path iteration condensed again in FP64 is timed as one phase of its
+// own (fallback); its inner phases are not added to the mixed path's.
+inline bool ph_skip(const ipm_ctx *c, int p) { return !c->prof || (c->mixed && c->exact_iter && p != PH_FALLBACK); }
 inline void ph_begin(ipm_ctx *c, int p, cudaStream_t st) {
-  if (c->prof) cudaEventRecord(c->ev[2 * p], st);
+  if (ph_skip(c, p)) return;
+  ph_take(c, p);  // a phase met again in the same iteration (inertia trials, solves)
+  cudaEventRecord(c->ev[2 * p], st);
 }
 inline void ph_end(ipm_ctx *c, int p, cudaStream_t st) {
-  if (c->prof) {
-    cudaEventRecord(c->ev[2 * p + 1], st);
-    c->ev_pending[p] = true;
-  }
+  if (ph_skip(c, p)) return;
+  cudaEventRecord(c->ev[2 * p + 1], st);
+  c->ev_pending[p] = true;
 }
 // accumulate finished phases (call after a stream synchronisation)
 void ph_collect(ipm_ctx *c) {
   if (!c->prof) return;
-  for (int p = 0; p < IPM_N_PHASES; ++p)
-    if (c->ev_pending[p]) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, c->ev[2 * p], c->ev[2 * p + 1]) == cudaSuccess) {
-        c->t_ms[p] += ms;
-        c->t_cnt[p] += 1;
-      }
-      c->ev_pending[p] = false;
-    }
+  for (int p = 0; p < IPM_N_PHASES; ++p) ph_take(c, p);
 }
 
 ipm_status read_flags(ipm_ctx *c, cudaStream_t st) {
@@ -583,7 +605,7 @@ ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
   int best_thr = 256;
   for (int thr : {128, 256}) {
     const double ms = fp64 ? time_ms([&] { launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, thr); }, st)
-                           : time_ms([&] { launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, thr); }, st);
+                           : time_ms([&] { launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, thr, tcs_of(c), D.flags); }, st);
     c->tune_ms[thr == 128 ? 0 : 1] = ms;
     if (ms < best) best = ms, best_thr = thr;
   }
@@ -593,7 +615,7 @@ ipm_status autotune(ipm_ctx *c, cudaStream_t st) {
   if (fp64) {
     launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, best_thr);
   } else {
-    launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, best_thr);
+    launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, best_thr, tcs_of(c), D.flags);
     launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Z32, c->zpl, st);
     launch_split_t((long long)S.N * S.nx, S.nu, c->planZY.kpad, c->Y32, c->ypl, st);
   }
@@ -748,7 +770,7 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
     if (fp64)
       launch_zsolve64(S, D.LU, D.rd, D.J, D.K, c->Z, c->Y, c->Yu, st, c->zs_threads, D.g, c->bpos,
                       c->emu ? c->emu_rs : nullptr);
-    else launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads);
+    else launch_zsolve32(S, D.LU, D.rd, D.J, D.K, c->Z32, c->Y32, c->Yu, st, c->zs_threads, tcs_of(c), D.flags);
     ph_end(c, PH_ZSOLVE, st);
     if (fp64) {
       // the reduced right-hand side needs Z and b only: on the side stream,
@@ -938,11 +960,12 @@ ipm_status pcg_reduced(ipm_ctx *c, double delta, cudaStream_t st) {
   int it = 0;
   for (; it < c->opt.max_refine && res > 1e-13 && rz > 0.0; ++it) {
     TRY(reduced_apply(c, p, Ap, delta, st));
-    launch_dot2(nu, p, Ap, nullptr, nullptr, c->red_out, st);
-    TRY(read_red(c, 1, st));
+    launch_dot2(nu, p, Ap, p, p, c->red_out, st);
+    TRY(read_red(c, 2, st));
     const double pAp = c->h_red[0];
     if (!(pAp > 0.0)) {
       c->neg_curv = true;
+      c->curv_q = c->h_red[1] > 0.0 ? pAp / c->h_red[1] : 0.0;
       break;
     }
     const double alpha = rz / pAp;
@@ -1187,8 +1210,7 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
     // Still not positive definite: the reduced matrix is indefinite by more
     // than the BF16x3 error, so the delta_w rule below corrects the inertia
     // on it (the refinement on the exact operator at that delta_w checks the
-    // decision: non-positive curvature there still sends the iteration to
-    // the FP64 condensation).
+    // decision: non-positive curvature there raises delta_w further).
   }
   double delta = 0.0;
   if (!pd) {
@@ -1205,6 +1227,25 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
     }
   }
   TRY(do_solve(c, st, true));
+  // Mixed path: CG met non-positive curvature of the exact operator at this
+  // delta_w, so the BF16x3 matrix passed a Cholesky test that the exact one
+  // fails.  The Rayleigh quotient q = p^T A p / p^T p <= 0 of the direction
+  // CG found bounds the smallest eigenvalue of the exact operator from
+  // above, so delta_w must grow by at least |q|: take delta + 2 |q| (at
+  // least twice delta, at least the rule's first trial) and solve again, a
+  // few times at most; the inertia is then decided on the exact operator.
+  for (int raise = 0; c->mixed && !c->exact_iter && c->opt.max_refine > 0 && c->neg_curv && raise < 6; ++raise) {
+    const double dl = c->delta_last;
+    const double first = dl == 0.0 ? DELTA0 : std::max(DELTA_MIN, KW_MINUS * dl);
+    delta = std::max({first, 2.0 * delta, delta + 2.0 * std::fabs(c->curv_q)});
+    if (delta > DELTA_MAX) break;
+    ++c->n_curv_raise;
+    join_py(c, st);
+    TRY(do_factor(c, delta, &pd, st));
+    if (!pd) continue;
+    c->delta_last = delta;
+    TRY(do_solve(c, st, true));
+  }
   // the mixed-precision step is kept when CG (if run) converged without
   // meeting non-positive curvature and, with refinement on eq. (6), its
   // augmented residual reached 1e-10
@@ -1215,6 +1256,7 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
     // CG met non-positive curvature or did not converge: redo in FP64
     c->exact_iter = true;
     ++c->n_fallback;
+    ph_begin(c, PH_FALLBACK, st);
     TRY(do_condense(c, st));
     pd = 0;
     TRY(do_factor(c, 0.0, &pd, st));
@@ -1233,6 +1275,7 @@ ipm_status do_step(ipm_ctx *c, int *converged, double *kkt_err, cudaStream_t st)
       }
     }
     TRY(do_solve(c, st, true));
+    ph_end(c, PH_FALLBACK, st);
   }
   // every exit from here on waits for the p_y solve on the side stream
   struct JoinPy {
@@ -1395,7 +1438,7 @@ ipm_status ipm_default_options(ipm_options *opt) {
   opt->tol = 1e-8;
   opt->max_iter = 200;
   opt->precision = IPM_PREC_FP64;
-  opt->max_refine = 25;
+  opt->max_refine = 60;
   opt->solve_threads = 0;
   opt->graphs = 0;
   opt->autotune = 0;
@@ -1403,6 +1446,7 @@ ipm_status ipm_default_options(ipm_options *opt) {
   opt->aug_refine = 10;
   opt->barrier_rule = IPM_BARRIER_ADAPTIVE;
   opt->sigma = 0.1;
+  opt->tc_solve = 1;
   return IPM_OK;
 }
 
@@ -1430,6 +1474,7 @@ ipm_status ipm_create(const ipm_network *net, int n_scen, const double *pd, cons
       (c->opt.solve_threads != 0 && c->opt.solve_threads != 128 && c->opt.solve_threads != 256) ||
       (c->opt.graphs != 0 && c->opt.graphs != 1) || (c->opt.autotune != 0 && c->opt.autotune != 1) ||
       (c->opt.poison != 0 && c->opt.poison != 1) || (c->opt.lu_pair != 0 && c->opt.lu_pair != 1) ||
+      (c->opt.tc_solve != 0 && c->opt.tc_solve != 1) ||
       (c->opt.barrier_rule == IPM_BARRIER_ADAPTIVE && !(c->opt.sigma > 0 && c->opt.sigma < 1))) {
     delete c;
     return IPM_ERR_ARG;
@@ -1620,6 +1665,7 @@ ipm_status ipm_get_quantity(ipm_ctx *c, int which, int scen, double *out, long l
     if (cap >= 16) out[15] = c->adjoint ? 1.0 : 0.0;       // K_hat by the adjoint-solve reduction
     if (cap >= 17) out[16] = c->tune_ms[6];                // autotuner: dense reduction (ms)
     if (cap >= 18) out[17] = c->tune_ms[7];                // autotuner: adjoint reduction (ms)
+    if (cap >= 19) out[18] = (double)c->n_curv_raise;      // mixed: delta_w raises after CG curvature
     return IPM_OK;
   }
   if (scen < 0 || scen >= N) return IPM_ERR_ARG;

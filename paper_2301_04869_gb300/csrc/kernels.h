@@ -53,9 +53,16 @@ bool zsolve64_folds_b(const DevSym &S);
 void launch_big_lu_dense(const DevSym &S, double *LU, double *rd, const double *amax, int *flags, cudaStream_t st,
                          const EmuLuPlan *emu_lu = nullptr);
 void launch_big_trsm64(const DevSym &S, const double *LU, const double *rd, double *Z, cudaStream_t st);
-void launch_big_trsm32(const DevSym &S, const double *LU, const double *rd, float *Z, cudaStream_t st);
+// one vector per scenario (v: [N][n_x], positions) through the block: forward
+// then backward, with G_x (trans 0) or G_x^T (trans 1)
+void launch_big_trsv(const DevSym &S, const double *LU, const double *rd, double *v, int trans, cudaStream_t st);
+struct TcsPlan;
+// tcs: the tensor-core variant of the block updates (mixed path), or null
+void launch_big_trsm32(const DevSym &S, const double *LU, const double *rd, float *Z, cudaStream_t st,
+                       const TcsPlan *tcs = nullptr, int *flags = nullptr);
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J, const double *K,
-                     float *Z, float *Y, double *Yu, cudaStream_t st, int threads = 256);
+                     float *Z, float *Y, double *Yu, cudaStream_t st, int threads = 256,
+                     const TcsPlan *tcs = nullptr, int *flags = nullptr);
 void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *v, int trans,
                    cudaStream_t st);
 // vps vectors per scenario: v [N * vps][n_x] (position order), one CTA of
@@ -220,6 +227,23 @@ size_t emu_lu_planes_bytes(int N, int nd);
 bool emu_lu_plan(EmuLuPlan &P, int N, int nd, void *a_planes, void *b_planes, int *exp_a, int *exp_b);
 void launch_emu_lu_update(const EmuLuPlan &P, double *LU, long long nnzlu, int dense_base, int kb, int ke, int *flags,
                           cudaStream_t st);
+// kernels_tcsolve.cu: the mixed path's solve through the large trailing
+// block with its updates as BF16x3 products on the tensor cores; planes of
+// the factor block [3][N ndp][kpl] then of the finished rows [3][N nup][kpl]
+// (ndp = kpl = nd, nup = nu, rounded up to 128), zero-filled once
+struct TcsPlan {
+  int N = 0, nd = 0, nu = 0, ndp = 0, nup = 0;
+  long long kpl = 0;
+  void *fpl = nullptr, *xpl = nullptr;
+  alignas(64) unsigned char maps[6 * 128];
+};
+size_t tcs_planes_bytes(int N, int nd, int nu, size_t *f_bytes = nullptr);
+bool tcs_plan(TcsPlan &P, int N, int nd, int nu, void *planes);
+void launch_tcs_split_f(const TcsPlan &P, const double *LU, long long nnzlu, int dense_base, cudaStream_t st);
+void launch_tcs_split_x(const TcsPlan &P, int nx, int t0, const float *Z, int r0, int r1, cudaStream_t st);
+// Z_d rows [r0, r1) -= F(rows, [k0, k1)) Z_d([k0, k1), :) (k0 a multiple of 64)
+void launch_tcs_update(const TcsPlan &P, int nx, int t0, float *Z, int r0, int r1, int k0, int k1, int *flags,
+                       cudaStream_t st);
 bool tc_set_operands(TcPlan &P, const void *a_planes, const void *b_planes);
 void launch_split_t(long long krows, int nu, long long kpad, const float *src, void *planes, cudaStream_t st);
 void launch_tc_schur(const TcPlan &P, double *partial, int *flags, cudaStream_t st);

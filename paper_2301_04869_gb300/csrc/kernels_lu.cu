@@ -553,8 +553,12 @@ __device__ __forceinline__ void solve_level(const int4 *__restrict__ rows, int e
 
 // One CTA per vector: vector b of v ([N * vps][n_x], position order) belongs
 // to scenario b / vps (vps vectors per scenario share its factors).
+// phase (large trailing block, S.big): 1 = the forward sparse rows and the
+// sparse part of the trailing rows only, 2 = the backward sparse rows only
+// (the dense block between them by the batched kernels of kernels_big.cu);
+// 0 = all.
 __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
-                                                double *v, int trans, int in_smem, int vps) {
+                                                double *v, int trans, int in_smem, int vps, int phase) {
   extern __shared__ double xsm[];
   __shared__ double blk[32][33];
   const int sc = blockIdx.x / vps, tid = threadIdx.x, bd = blockDim.x;
@@ -570,11 +574,11 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
     __syncthreads();
   }
   // forward sparse rows (few entries each): four lanes per row
-  for (int l = 0; l < S.nlev_fs; ++l) {
+  for (int l = 0; l < (phase == 2 ? 0 : S.nlev_fs); ++l) {
     solve_level<4>(S.fs4, S.fs_lev_ptr[l], S.fs_lev_ptr[l + 1], S.fr4, trans != 0, A, r, trans != 0, x);
     __syncthreads();
   }
-  if (nd > 0) {
+  if (nd > 0 && phase != 2) {
     const int *ts = S.tail_slot;
     double *tv = x + t0;
     // sparse part of the trailing rows (their columns < t0), eight lanes per row
@@ -595,6 +599,11 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
       }
     }
     __syncthreads();
+    if (phase == 1) {
+      if (in_smem)
+        for (int i = tid; i < nx; i += bd) vs[i] = x[i];
+      return;
+    }
     // Dense trailing block, blocked by 32: one warp per 32 x 32 diagonal
     // block (lane = row, shuffles), all threads for the off-diagonal updates
     // (four partial sums).  Column c of the block is contiguous in LU
@@ -688,6 +697,11 @@ __global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restri
       }
       __syncthreads();
     }
+  }
+  if (phase == 1) {  // (no trailing block)
+    if (in_smem)
+      for (int i = tid; i < nx; i += bd) vs[i] = x[i];
+    return;
   }
   // backward sparse rows: eight lanes per row
   for (int l = 0; l < S.nlev_bs; ++l) {
@@ -884,7 +898,8 @@ void launch_zsolve64(const DevSym &S, const double *LU, const double *rd, const 
   k_zsolve64<<<grid, threads, bytes, st>>>(S, LU, rd, J, K, Z, Y, Yu, sm, g, b, ezy, 0); ipm_count_launch();
 }
 void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const double *J,
-                     const double *K, float *Z, float *Y, double *Yu, cudaStream_t st, int threads) {
+                     const double *K, float *Z, float *Y, double *Yu, cudaStream_t st, int threads,
+                     const TcsPlan *tcs, int *flags) {
   dim3 grid((S.nu + 31) / 32, S.N);
   const int sm = zsolve_smem_ok(S, sizeof(float));
   const size_t bytes = sm ? (size_t)S.nd * 32 * sizeof(float) : 0;
@@ -892,7 +907,7 @@ void launch_zsolve32(const DevSym &S, const double *LU, const double *rd, const 
   (void)cap;
   if (S.big) {
     k_zsolve32<<<grid, threads, 0, st>>>(S, LU, rd, J, K, Z, Y, Yu, 0, 1); ipm_count_launch();
-    launch_big_trsm32(S, LU, rd, Z, st);
+    launch_big_trsm32(S, LU, rd, Z, st, tcs, flags);
     k_zsolve32<<<grid, threads, 0, st>>>(S, LU, rd, J, K, Z, Y, Yu, 0, 2); ipm_count_launch();
     return;
   }
@@ -912,7 +927,15 @@ void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *
   }();
   const int sm = (size_t)S.nx * sizeof(double) <= cap ? 1 : 0;
   const size_t bytes = sm ? (size_t)S.nx * sizeof(double) : 0;
-  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1); ipm_count_launch();
+  if (S.big) {
+    // sparse rows in one CTA per scenario; the dense block by the batched
+    // single-vector kernels (many CTAs per scenario)
+    k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 1); ipm_count_launch();
+    launch_big_trsv(S, LU, rd, v, trans, st);
+    k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 2); ipm_count_launch();
+    return;
+  }
+  k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 0); ipm_count_launch();
 }
 
 void launch_solve1_batched(const DevSym &S, const double *LU, const double *rd, double *v, int trans, int vps,
@@ -928,5 +951,5 @@ void launch_solve1_batched(const DevSym &S, const double *LU, const double *rd, 
   const int sm = (size_t)S.nx * sizeof(double) <= cap ? 1 : 0;
   const size_t bytes = sm ? (size_t)S.nx * sizeof(double) : 0;
   const long long nb = (long long)S.N * vps;
-  k_solve1<<<(unsigned)nb, threads, bytes, st>>>(S, LU, rd, v, trans, sm, vps); ipm_count_launch();
+  k_solve1<<<(unsigned)nb, threads, bytes, st>>>(S, LU, rd, v, trans, sm, vps, 0); ipm_count_launch();
 }

@@ -21,8 +21,9 @@ STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_CUDA", 3: "IPM_ERR_OOM",
           7: "IPM_ERR_MAXITER", 8: "IPM_ERR_TIMEOUT", 9: "IPM_ERR_STATE"}
 PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 Q_KHAT, Q_RHS_U, Q_Z, Q_FGH, Q_JAC, Q_HESS, Q_ERRS, Q_INFO, Q_TIMERS, Q_ZTZ = range(10)
-N_PHASES = 10
-PHASES = ("eval", "condense_K", "lu", "zsolve", "gemm", "reduced_rhs", "cholesky", "recover", "linesearch", "split")
+N_PHASES = 11
+PHASES = ("eval", "condense_K", "lu", "zsolve", "gemm", "reduced_rhs", "cholesky", "recover", "linesearch", "split",
+          "fallback")
 
 
 class IPMError(RuntimeError):
@@ -53,7 +54,7 @@ class Options(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("solve_threads", ctypes.c_int), ("barrier_rule", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
                 ("lu_pair", ctypes.c_int), ("aug_refine", ctypes.c_int), ("reduction", ctypes.c_int), ("big_block", ctypes.c_int),
-                ("sigma", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("tc_solve", ctypes.c_int)]
 
 
 class Dims(ctypes.Structure):
@@ -202,9 +203,9 @@ def _cnet(net):
     return keep, cnet
 
 
-def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, barrier_rule=None, sigma=None,
+def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=60, barrier_rule=None, sigma=None,
                  graphs=False, autotune=False, solve_threads=0, poison=False, lu_pair=True, aug_refine=None,
-                 reduction=None, big_block=False):
+                 reduction=None, big_block=False, tc_solve=True):
     lib = load()
     opt = Options()
     lib.ipm_default_options(ctypes.byref(opt))
@@ -226,22 +227,24 @@ def make_options(precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25, bar
     if reduction is not None:
         opt.reduction = int(reduction)
     opt.big_block = int(bool(big_block))
+    opt.tc_solve = int(bool(tc_solve))
     return opt
 
 
 class Solver:
     """One context: a network with N load scenarios on the current GPU."""
 
-    def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=25,
+    def __init__(self, net, pd, qd, precision=PREC_FP64, tol=1e-8, max_iter=200, max_refine=60,
                  barrier_rule=None, sigma=None, graphs=False, autotune=False, solve_threads=0, poison=False,
-                 lu_pair=True, aug_refine=None, reduction=None, big_block=False):
+                 lu_pair=True, aug_refine=None, reduction=None, big_block=False, tc_solve=True):
         lib = load()
         self._lib = lib
         self._keep, cnet = _cnet(net)
         opt = make_options(precision=precision, tol=tol, max_iter=max_iter, max_refine=max_refine,
                            barrier_rule=barrier_rule, sigma=sigma, graphs=graphs, autotune=autotune,
                            solve_threads=solve_threads, poison=poison, lu_pair=lu_pair,
-                           aug_refine=aug_refine, reduction=reduction, big_block=big_block)
+                           aug_refine=aug_refine, reduction=reduction, big_block=big_block,
+                           tc_solve=tc_solve)
         pd = np.ascontiguousarray(np.atleast_2d(pd), dtype=np.float64)
         qd = np.ascontiguousarray(np.atleast_2d(qd), dtype=np.float64)
         self.N = pd.shape[0]
@@ -343,7 +346,7 @@ class Solver:
         d = self.dims
         sizes = {Q_KHAT: d.n_u * d.n_u, Q_RHS_U: d.n_u, Q_Z: d.n_x * d.n_u, Q_FGH: 1 + d.n_x + d.m,
                  Q_JAC: d.n_x * d.n_x + d.n_x * d.n_u + d.m * d.n_x + d.m * d.n_u,
-                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 18,
+                 Q_HESS: d.n_x * d.n_x + d.n_x * d.n_u + d.n_u * d.n_u, Q_ERRS: 6, Q_INFO: 19,
                  Q_TIMERS: 2 * N_PHASES + 1, Q_ZTZ: d.n_u * d.n_u}
         out = np.empty(sizes[which])
         self._check(self._lib.ipm_get_quantity(self._h, which, scen, _ptr(out, ctypes.c_double), out.size,

@@ -43,10 +43,12 @@ def test_default_options(lib):
     assert lib.ipm_default_options(ctypes.byref(o)) == 0
     assert o.tol == 1e-8 and o.max_iter == 200 and o.precision == ipm.PREC_FP64
     assert o.lu_pair == 1 and o.graphs == 0 and o.autotune == 0 and o.poison == 0
+    assert o.tc_solve == 1
 
 
 @pytest.mark.parametrize("field,value", [("precision", 3), ("solve_threads", 64), ("graphs", 2), ("autotune", -1),
-                                         ("poison", 2), ("lu_pair", 2), ("tol", 0.0), ("max_iter", -1)])
+                                         ("poison", 2), ("lu_pair", 2), ("tol", 0.0), ("max_iter", -1),
+                                         ("tc_solve", 2)])
 def test_rejects_bad_options(lib, field, value):
     """Invalid options are rejected before the device is touched."""
     net = synth.make_network(30, 6, seed=0)

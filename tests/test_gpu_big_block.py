@@ -146,3 +146,27 @@ def test_10000_bus_load_scale(gpu):
     conv2, errs2 = out[0.2]
     assert conv2
     assert synth.CONFIGS["opf10000_n256"][5] == 0.2
+
+
+def test_tc_block_solve_matches_simt(gpu):
+    """Mixed path, large-block mode forced on the 1000-bus network (two row
+    blocks of the trailing block, so both tensor-core products run): the
+    block updates as BF16x3 tensor-core products (tc_solve = 1) and as FP32
+    SIMT products (tc_solve = 0) give the same Z to FP32 grade, and both the
+    oracle's Z at the mixed path's bar."""
+    net, pd, qd, M, st = case("1000bus_N4")
+    D = kkt.eval_all(M, st)
+    C0 = kkt.condense(M, st, D, st["mu"], 0.0)
+    Z = {}
+    for tc in (True, False):
+        sol = gpu.Solver(net, pd, qd, precision=PRECS["mixed"], big_block=True, tc_solve=tc)
+        assert sol.dims.nd > 128
+        sol.ipm_set_state(sol.pack_state(st))
+        sol.ipm_eval_derivatives()
+        sol.ipm_condense_scenarios()
+        nx, nu = sol.dims.n_x, sol.dims.n_u
+        Z[tc] = [sol.ipm_get_quantity(gpu.Q_Z, i).reshape(nx, nu) for i in range(M.N)]
+        sol.close()
+    for i in range(M.N):
+        assert rel(Z[True][i], Z[False][i]) <= 1e-5
+        assert rel(Z[True][i], C0.Z[i]) <= 1e-5
