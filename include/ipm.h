@@ -291,9 +291,11 @@ ipm_status ipm_get_quantity(ipm_ctx *ctx, int which, int scen, double *host_out,
  * gemm (Z^T Y + scenario sum), reduced_rhs, cholesky, recover, linesearch,
  * split (the tensor-core operands of Z and Y: BF16 slices or planes),
  * fallback (mixed path: the whole FP64 condensation and solve of an
- * iteration condensed again; its inner phases are not added to the others).
+ * iteration condensed again; its inner phases are not added to the others),
+ * solve1 (every solve of one vector per scenario with G_x or G_x^T on the
+ * call's stream, counted each time; nested in the phases above).
  * Profiling serialises the host with the device at phase boundaries. */
-enum { IPM_N_PHASES = 11 };
+enum { IPM_N_PHASES = 12 };
 ipm_status ipm_set_profiling(ipm_ctx *ctx, int on);
 
 /* Kernels this library has launched in the process so far (all contexts;

@@ -374,7 +374,7 @@ ipm_status read_red(ipm_ctx *c, int nv, cudaStream_t st) {
 inline const TcsPlan *tcs_of(const ipm_ctx *c) { return c->tcs_on ? &c->tcs : nullptr; }
 
 enum { PH_EVAL = 0, PH_COND, PH_LU, PH_ZSOLVE, PH_GEMM, PH_RRHS, PH_CHOL, PH_RECOVER, PH_LS, PH_SPLIT,
-       PH_FALLBACK };
+       PH_FALLBACK, PH_SOLVE1 };
 
 // accumulate one finished phase (waits for its end event)
 void ph_take(ipm_ctx *c, int p) {
@@ -404,6 +404,14 @@ inline void ph_end(ipm_ctx *c, int p, cudaStream_t st) {
 void ph_collect(ipm_ctx *c) {
   if (!c->prof) return;
   for (int p = 0; p < IPM_N_PHASES; ++p) ph_take(c, p);
+}
+
+// one vector per scenario through G_x (trans 0) or G_x^T (trans 1) on the
+// main stream, timed as the solve1 phase (nested in the phase it serves)
+void solve1(ipm_ctx *c, double *v, int trans, cudaStream_t st) {
+  ph_begin(c, PH_SOLVE1, st);
+  launch_solve1(c->ds, c->dw.LU, c->dw.rd, v, trans, st);
+  ph_end(c, PH_SOLVE1, st);
 }
 
 ipm_status read_flags(ipm_ctx *c, cudaStream_t st) {
@@ -813,11 +821,11 @@ ipm_status do_condense(ipm_ctx *c, cudaStream_t st) {
       ph_begin(c, PH_RRHS, st);
       // eq. (11) with FP64 solves: b = G_x^{-1} r3, a = G_x^{-T}(rhat1 - K_xx b)
       launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->bpos, 1.0, st);
-      launch_solve1(S, D.LU, D.rd, c->bpos, 0, st);
+      solve1(c, c->bpos, 0, st);
       launch_kapply(S, D.K, c->bpos, nullptr, c->kpx, nullptr, st);
       launch_gather_pos(S.N, S.nx, S.iperm, D.rh1x, c->apos, 1.0, st);
       launch_lincomb((long long)S.N * S.nx, c->apos, 1.0, c->apos, -1.0, c->kpx, 0.0, nullptr, st);
-      launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+      solve1(c, c->apos, 1, st);
       launch_rhs_reduced(S, D.J, D.K, D.rh2, c->apos, c->bpos, c->rhs_u, st);
       ph_end(c, PH_RRHS, st);
     }
@@ -898,7 +906,7 @@ ipm_status do_factor(ipm_ctx *c, double delta, int *is_pd, cudaStream_t st, doub
       launch_tc_schur(c->planZZ, c->tcpart, c->dw.flags, st);
       launch_tc_assemble(c->planZZ, S.N, c->tcpart, nullptr, nullptr, c->M, st);
       CK(cudaMemcpyAsync(c->cpos, c->bpos, (size_t)S.N * S.nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      launch_solve1(S, c->dw.LU, c->dw.rd, c->cpos, 1, st);
+      solve1(c, c->cpos, 1, st);
       launch_gut_sum(S, c->dw.J, c->cpos, -1.0, c->rhs_corr, st);
     }
     c->M_valid = true;
@@ -926,11 +934,11 @@ ipm_status reduced_apply(ipm_ctx *c, const double *v, double *out, double delta,
   const long long NX = (long long)S.N * S.nx;
   CK(cudaMemsetAsync(c->vpos, 0, NX * sizeof(double), st));
   launch_gu_apply(S, D.J, v, c->vpos, st);
-  launch_solve1(S, D.LU, D.rd, c->vpos, 0, st);
+  solve1(c, c->vpos, 0, st);
   launch_lincomb(NX, c->vpos, -1.0, c->vpos, 0.0, nullptr, 0.0, nullptr, st);
   launch_kapply(S, D.K, c->vpos, v, c->kpx, c->kpu, st);
   launch_lincomb(NX, c->apos, 1.0, c->kpx, delta, c->vpos, 0.0, nullptr, st);
-  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+  solve1(c, c->apos, 1, st);
   launch_gut_sum(S, D.J, c->apos, -1.0, out, st);
   launch_apply_finish(S, c->kpu, c->diag1, delta, v, out, st);
   return IPM_OK;
@@ -1035,7 +1043,7 @@ ipm_status refine_aug(ipm_ctx *c, double delta, cudaStream_t st) {
     launch_htv(S, D, c->ar1x, c->ar1u, c->atw, c->arh1x, c->arh2, c->aupart, st);
     // eq. (11): b = G_x^{-1} r3', a = G_x^{-T}(rhat1_x - (K_xx + delta) b)
     launch_gather_pos(S.N, S.nx, S.iperm, c->ar3, c->bpos2, 1.0, st);
-    launch_solve1(S, D.LU, D.rd, c->bpos2, 0, st);
+    solve1(c, c->bpos2, 0, st);
     launch_kapply(S, D.K, c->bpos2, nullptr, c->kpx, nullptr, st);
     launch_gather_pos(S.N, S.nx, S.iperm, c->arh1x, c->apos2, 1.0, st);
     launch_lincomb(NX, c->apos2, 1.0, c->apos2, -1.0, c->kpx, -delta, c->bpos2, st);
@@ -1046,7 +1054,7 @@ ipm_status refine_aug(ipm_ctx *c, double delta, cudaStream_t st) {
       launch_lincomb(S.nu, c->dpu, -1.0, c->arh2, 0.0, nullptr, 0.0, nullptr, st);
       launch_zt_apply(S, c->Z, c->apos2, D.K, c->bpos2, -1.0, 1.0, c->dpu, c->cpos, st);
     } else {
-      launch_solve1(S, D.LU, D.rd, c->apos2, 1, st);
+      solve1(c, c->apos2, 1, st);
       launch_rhs_reduced(S, D.J, D.K, c->arh2, c->apos2, c->bpos2, c->dpu, st);
     }
     launch_chol_solve(S.nu, c->F, c->dpu, st);
@@ -1057,13 +1065,13 @@ ipm_status refine_aug(ipm_ctx *c, double delta, cudaStream_t st) {
     } else {
       launch_gather_pos(S.N, S.nx, S.iperm, c->ar3, c->vpos2, 1.0, st);
       launch_gu_apply(S, D.J, c->dpu, c->vpos2, st);
-      launch_solve1(S, D.LU, D.rd, c->vpos2, 0, st);
+      solve1(c, c->vpos2, 0, st);
       launch_lincomb(NX, c->vpos2, -1.0, c->vpos2, 0.0, nullptr, 0.0, nullptr, st);
     }
     launch_kapply(S, D.K, c->vpos2, c->dpu, c->kpx, c->kpu, st);
     launch_gather_pos(S.N, S.nx, S.iperm, c->arh1x, c->apos2, 1.0, st);
     launch_lincomb(NX, c->apos2, 1.0, c->apos2, 1.0, c->kpx, delta, c->vpos2, st);
-    launch_solve1(S, D.LU, D.rd, c->apos2, 1, st);
+    solve1(c, c->apos2, 1, st);
     launch_scatter_pos(S.N, S.nx, S.iperm, c->apos2, c->dpy, -1.0, st);
     launch_scatter_pos(S.N, S.nx, S.iperm, c->vpos2, c->dpx, 1.0, st);
     // Prop. 2.1: dp_z, dp_s
@@ -1116,7 +1124,7 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st, bool defer_py = false) {
     // p_x = -G_x^{-1} (r3 + G_u p_u) with FP64 solves
     launch_gather_pos(S.N, S.nx, S.iperm, D.g, c->vpos, 1.0, st);
     launch_gu_apply(S, D.J, c->pu, c->vpos, st);
-    launch_solve1(S, D.LU, D.rd, c->vpos, 0, st);
+    solve1(c, c->vpos, 0, st);
     launch_lincomb(NX, c->vpos, -1.0, c->vpos, 0.0, nullptr, 0.0, nullptr, st);
   }
   launch_scatter_pos(S.N, S.nx, S.iperm, c->vpos, c->px, 1.0, st);
@@ -1134,7 +1142,7 @@ ipm_status do_solve(ipm_ctx *c, cudaStream_t st, bool defer_py = false) {
     CK(cudaEventRecord(c->ev_join, c->side));
     c->py_pending = true;
   } else {
-    launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+    solve1(c, c->apos, 1, st);
     launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, c->py, -1.0, st);
   }
   launch_pz_ps(S, D, c->px, c->pu, c->Hp, c->pz, c->ps, st);
@@ -1395,7 +1403,7 @@ ipm_status do_warm_start(ipm_ctx *c, const float *pred, cudaStream_t st) {
   launch_lu_factor(S, c->nL, D.J, D.LU, D.rd, D.flags, st, c->opt.lu_pair != 0);
   launch_warm_yrhs(S, D, c->kpx, st);
   launch_gather_pos(S.N, S.nx, S.iperm, c->kpx, c->apos, 1.0, st);
-  launch_solve1(S, D.LU, D.rd, c->apos, 1, st);
+  solve1(c, c->apos, 1, st);
   launch_scatter_pos(S.N, S.nx, S.iperm, c->apos, D.y, -1.0, st);
   CK(cudaGetLastError());
   TRY(read_flags(c, st));

@@ -21,9 +21,9 @@ STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_CUDA", 3: "IPM_ERR_OOM",
           7: "IPM_ERR_MAXITER", 8: "IPM_ERR_TIMEOUT", 9: "IPM_ERR_STATE"}
 PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 Q_KHAT, Q_RHS_U, Q_Z, Q_FGH, Q_JAC, Q_HESS, Q_ERRS, Q_INFO, Q_TIMERS, Q_ZTZ = range(10)
-N_PHASES = 11
+N_PHASES = 12
 PHASES = ("eval", "condense_K", "lu", "zsolve", "gemm", "reduced_rhs", "cholesky", "recover", "linesearch", "split",
-          "fallback")
+          "fallback", "solve1")
 
 
 class IPMError(RuntimeError):
