@@ -557,7 +557,7 @@ __device__ __forceinline__ void solve_level(const int4 *__restrict__ rows, int e
 // sparse part of the trailing rows only, 2 = the backward sparse rows only
 // (the dense block between them by the batched kernels of kernels_big.cu);
 // 0 = all.
-__global__ void __launch_bounds__(512) k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
+__global__ void __launch_bounds__(1024) k_solve1(DevSym S, const double *__restrict__ LU, const double *__restrict__ rd,
                                                 double *v, int trans, int in_smem, int vps, int phase) {
   extern __shared__ double xsm[];
   __shared__ double blk[32][33];
@@ -928,11 +928,12 @@ void launch_solve1(const DevSym &S, const double *LU, const double *rd, double *
   const int sm = (size_t)S.nx * sizeof(double) <= cap ? 1 : 0;
   const size_t bytes = sm ? (size_t)S.nx * sizeof(double) : 0;
   if (S.big) {
-    // sparse rows in one CTA per scenario; the dense block by the batched
-    // single-vector kernels (many CTAs per scenario)
-    k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 1); ipm_count_launch();
+    // sparse rows in one CTA of 1,024 threads per scenario (the level sweeps
+    // of the large networks are long: more rows in flight per round); the
+    // dense block by the batched single-vector kernels (many CTAs per scenario)
+    k_solve1<<<S.N, 1024, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 1); ipm_count_launch();
     launch_big_trsv(S, LU, rd, v, trans, st);
-    k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 2); ipm_count_launch();
+    k_solve1<<<S.N, 1024, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 2); ipm_count_launch();
     return;
   }
   k_solve1<<<S.N, 512, bytes, st>>>(S, LU, rd, v, trans, sm, 1, 0); ipm_count_launch();
