@@ -148,13 +148,11 @@ __global__ void __launch_bounds__(192, 1) k_tcs_update(const __grid_constant__ M
     float acc[BN];
 #pragma unroll
     for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
-    bool ok = true;
     for (int i = 0; i < nkb; ++i) {
       const int b = i & 1;
       if (!mbar_wait(&acc_full[b], (i >> 1) & 1)) {
         flags[FLAG_TIMEOUT] = 1;
         *abort_flag = 1;
-        ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -175,7 +173,6 @@ __global__ void __launch_bounds__(192, 1) k_tcs_update(const __grid_constant__ M
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
     }
-    (void)ok;
     // the stage buffers are idle once the last accumulator has been drained:
     // the tile goes through shared memory so that the subtraction from Z_d
     // reads and writes whole rows (a warp per row, lanes along the columns)
