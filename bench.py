@@ -471,7 +471,7 @@ def run_ours(args):
 
 def run_batch(args):
     """The multi-instance runner on uneven instances (bus counts log-uniform in
-    [100, 1000], generators at 10 % of buses, 8..128 scenarios each): create,
+    [100, nmax], generators at 10 % of buses, 8..128 scenarios each): create,
     solve from the cold start and destroy every instance under a device-memory
     budget.  Metric: scenario condensations (scenarios x IPM iterations,
     summed over instances) per second of wall time for the whole job, context
@@ -483,7 +483,7 @@ def run_batch(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    insts = synth.uneven_batch(n_inst=args.instances, seed=4, nmin=100, nmax=1000, smin=8, smax=128)
+    insts = synth.uneven_batch(n_inst=args.instances, seed=4, nmin=100, nmax=args.nmax, smin=8, smax=128)
     nets, pds, qds = [t[0] for t in insts], [t[1] for t in insts], [t[2] for t in insts]
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.7 * free)
@@ -510,7 +510,7 @@ def run_batch(args):
         "metric": METRIC, "value": g["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": 1e3 * g["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batch_uneven", "instances": args.instances, "n_bus": "log-uniform 100..1000",
+        "config": {"workload": "batch_uneven", "instances": args.instances, "n_bus": f"log-uniform 100..{args.nmax}",
                    "generators": "10% of buses", "scenarios": "uniform 8..128",
                    "total_scenarios": int(sum(p.shape[0] for p in pds)), "max_iter": args.max_iter,
                    "mem_budget_bytes": budget, "timing": "wall clock of the whole job (host), device synchronised"},
@@ -533,6 +533,9 @@ def main():
     ap.add_argument("--workload", default="opf10000_n256", choices=list(synth.CONFIGS) + ["batch_uneven"])
     ap.add_argument("--instances", type=int, default=64, help="batch_uneven: number of instances")
     ap.add_argument("--max-iter", type=int, default=150, help="batch_uneven: IPM iteration limit")
+    ap.add_argument("--nmax", type=int, default=1000,
+                    help="batch_uneven: largest bus count (the many-instance configuration: --instances 512 "
+                         "--nmax 5000)")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "fp64_tc"],
                     help="headline path (default: mixed on the 10,000-bus workload, fp64_tc otherwise)")
     ap.add_argument("--scenarios", type=int, default=None,
